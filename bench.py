@@ -1,0 +1,386 @@
+"""Benchmark of the metric-based importance-sampling hot path on GB300.
+
+Workload (N = 1): the aligned-spin BNS population -- H1+L1, 20-1024 Hz at 1/128 Hz
+(128,513 bins, complex64 data, FP64 PSD), coloured Gaussian noise, SNR 10-30; per event
+2^20 proposal samples over (Mc, q, chi1, chi2, t_c) from a Gaussian in the Fisher metric
+at the trigger; phase and distance marginalised.  One step = one event's batch:
+draw (Philox) -> fused waveform/projection/inner-product/marginalisation -> two-pass
+weight reduction.  Steps cycle over resident events; an L2 flush (256 MB write) runs
+between steps inside the timed region.
+
+JSON line (rank 0): value = likelihood evaluations / s over all ranks (weak scaling:
+every rank runs its own events), e2e = the same through the C ABI from host buffers
+(create + set_metric + draw + loglike + reduce + destroy per step, host->device data
+and device->host summary inside the timed region), roofline of the fused likelihood
+kernel against the SFU ceiling (two MUFU transcendentals per bin), cpu_baseline = the
+FP64 oracle on the host cores on a bounded sample.
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+from workloads import MC, Q, CHI1, CHI2, RA, DEC, PSI, IOTA, DL, TC, PHIC  # noqa: E402
+
+METRIC = "likelihood evals/sec and seconds to 1e4 effective samples per event"
+UNIT = "likelihood evals/s"
+SFU_PER_SM_PER_CLK = 16        # MUFU results per SM per clock (Blackwell)
+SFU_PER_BIN = 2                # one sine and one cosine per (sample, bin)
+N_SM = 152
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------------- clock sampling
+class ClockSampler:
+    def __init__(self):
+        self.samples, self.proc, self.thread = [], None, None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if not self.samples:
+            return None
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------------- event set-up
+def event_setup(m, w, spec, dets_np):
+    """Synthetic data and proposal for one event through the library's own helpers:
+    injection + noise (mbis_inject), Fisher matrix (mbis_fisher), Gaussian proposal."""
+    n = w.n_bins
+    psd1 = m.mbis_psd_aligo(w.f_lo, w.df, n)
+    psd = np.tile(psd1, (w.n_det, 1))
+    dets = m.make_detectors(*dets_np)
+    th = np.zeros(11)
+    mc = (spec.m1 * spec.m2) ** 0.6 / (spec.m1 + spec.m2) ** 0.2
+    th[MC], th[Q] = mc, spec.m1 / spec.m2
+    for k, v in spec.params.items():
+        th[workloads.PARAM_NAMES.index(k)] = v
+    th[DL] = 1.0
+    _, snr2 = m.mbis_inject(w.f_lo, w.df, n, dets, psd, spec.gmst, th)
+    th[DL] = math.sqrt(snr2) / spec.snr
+    strain, _ = m.mbis_inject(w.f_lo, w.df, n, dets, psd, spec.gmst, th, spec.noise_seed or 0,
+                              spec.noise_seed is not None)
+    strain = strain.astype(np.complex64)
+    ctx = m.mbis_create(strain, psd, dets, w.f_lo, w.df, th, gmst=spec.gmst, precision=m.FP64, marg=w.marg,
+                        dmin=w.dmin, dmax=w.dmax)
+    sampled = list(w.sampled)
+    ids = sampled + [PHIC, DL]
+    steps = np.array([{MC: 1e-6 * th[MC], Q: 1e-6, CHI1: 1e-5, CHI2: 1e-5, TC: 1e-7, PHIC: 1e-6, DL: 1e-5 * th[DL]}[i]
+                      for i in ids])
+    G = m.mbis_fisher(ctx, th, ids, steps)
+    m.mbis_destroy(ctx)
+    P = len(sampled)
+    A, B, Cm = G[:P, :P], G[:P, P:], G[P:, P:]
+    G = A - B @ np.linalg.solve(Cm, B.T)
+    width = {Q: 2.0, CHI1: 2 * w.chi_max, CHI2: 2 * w.chi_max}
+    for p, i in enumerate(sampled):
+        if i in width:
+            G[p, p] += 12.0 / width[i] ** 2
+    cov = np.linalg.inv(G)
+    cov = 0.5 * (cov + cov.T)
+    L = np.linalg.cholesky(cov)
+    sig = np.sqrt(np.diag(cov)) * w.scale
+    mean = np.array([th[i] for i in sampled])
+    lo, hi = mean - w.box_sigmas * sig, mean + w.box_sigmas * sig
+    for p, i in enumerate(sampled):
+        if i in (CHI1, CHI2):
+            lo[p], hi[p] = -w.chi_max, w.chi_max
+        if i == Q:
+            lo[p] = max(1.0, lo[p])
+    prop = dict(ids=np.array(sampled, dtype=np.int32), mean=mean, chol=L, scale=w.scale, lo=lo, hi=hi,
+                flags=w.prior_flags)
+    return dict(spec=spec, th=th, strain=strain, psd=psd, dets=dets, prop=prop)
+
+
+def make_ctx(m, w, ev, precision):
+    ctx = m.mbis_create(ev["strain"], ev["psd"], ev["dets"], w.f_lo, w.df, ev["th"], gmst=ev["spec"].gmst,
+                        precision=precision, marg=w.marg, dmin=w.dmin, dmax=w.dmax)
+    p = ev["prop"]
+    m.mbis_set_metric(ctx, p["ids"], p["mean"], p["chol"], p["scale"], p["lo"], p["hi"], p["flags"])
+    return ctx
+
+
+# ------------------------------------------------------------------------- CPU oracle timing
+class OracleLeg:
+    """The FP64 oracle on the host cores, on events of the same workload that the oracle
+    builds itself (injection, noise, Fisher proposal): no input comes from the GPU path."""
+
+    def __init__(self, w, specs):
+        import oracle
+        from oracle import events as oev
+        oracle.build()
+        self.oracle, self.w = oracle, w
+        self.events = []
+        for spec in specs:
+            ev, th, _ = oev.make_event(w, spec)
+            s = (ev.strain[..., 0] + 1j * ev.strain[..., 1]).astype(np.complex64)   # the data the GPU holds
+            ev.set_strain(np.stack([s.real.astype(np.float64), s.imag.astype(np.float64)], axis=-1))
+            self.events.append((spec, ev, th, oev.make_proposal(ev, w, th)))
+        self.cores = os.cpu_count() or 1
+
+    def batch(self, i, n):
+        """draw -> likelihood -> weights for n samples of event i; returns seconds."""
+        o = self.oracle
+        spec, ev, th, p = self.events[i % len(self.events)]
+        t0 = time.perf_counter()
+        theta, lq = o.draw(spec.draw_seed, (i // len(self.events)) * n, n, p["ids"], p["mean"], p["chol"],
+                           p["scale"])
+        ll = o.loglike_batch(ev, o.full_params(p["ids"], theta, th))
+        lp = o.log_prior(p["ids"], p["lo"], p["hi"], p["flags"], theta)
+        o.reduce(ll, lp, lq)
+        return time.perf_counter() - t0
+
+    def rate(self, budget_s):
+        n = max(4, 2 * self.cores)
+        evals, used, i = 0, 0.0, 0
+        while used < budget_s:
+            used += self.batch(i, n)
+            evals += n
+            i += 1
+        return evals / used, evals, used
+
+
+# ------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2410_05190_gb300 as m
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workloads.bns_population(n_events=max(args.events * world, 1), n_samples=args.samples)
+    my_events = w.events[rank::world][: args.events]
+    dets_np = workloads.network(w.detectors)
+    t_setup = time.time()
+    evs = [event_setup(m, w, spec, dets_np) for spec in my_events]
+    ctxs = [make_ctx(m, w, ev, m.MIXED) for ev in evs]
+    setup_s = time.time() - t_setup
+    n, P = w.n_samples, len(w.sampled)
+    stream = torch.cuda.current_stream()
+    theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+    lq, lp, ll = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    launches_per_step = 4  # draw, fused likelihood, reduce max, reduce sums
+    like_events = []
+
+    def step(i, timed):
+        ctx = ctxs[i % len(ctxs)]
+        spec = evs[i % len(evs)]["spec"]
+        flush.zero_()
+        m.mbis_draw(ctx, spec.draw_seed, (i // len(ctxs)) * n, n, theta, lq, lp, stream)
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        m.mbis_loglike(ctx, n, theta, ll, stream)
+        if timed:
+            e1.record(stream)
+            like_events.append((e0, e1))
+        return m.mbis_reduce(ctx, n, ll, lp, lq, None, 0, stream)
+
+    summaries = []
+    for i in range(args.warmup):
+        step(i, False)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler()
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        summaries.append(step(args.warmup + i, True))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    like_ms = [a.elapsed_time(b) for a, b in like_events]
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    evals = args.steps * n * world
+    value = evals / elapsed
+
+    # end to end through the C ABI from host buffers (create .. destroy per step)
+    e2e = None
+    if args.e2e_steps > 0:
+        th_bytes = 0
+        hbuf = torch.empty(4, dtype=torch.float64)
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            ev = evs[i % len(evs)]
+            ctx = make_ctx(m, w, ev, m.MIXED)
+            m.mbis_draw(ctx, ev["spec"].draw_seed, 0, n, theta, lq, lp, stream)
+            m.mbis_loglike(ctx, n, theta, ll, stream)
+            s = m.mbis_reduce(ctx, n, ll, lp, lq, None, 0, stream)
+            m.mbis_destroy(ctx)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        ev = evs[0]
+        h2d = ev["strain"].nbytes + ev["psd"].nbytes + 8 * (ev["prop"]["chol"].size + 4 * P + 11)
+        d2h = 4 * 8 + 4
+        e2e = {"value": args.e2e_steps * n / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    out = None
+    if rank == 0:
+        pk = peaks()
+        clock_mhz = pk.get("sm_max_mhz", 2070.0)
+        bins_per_launch = n * w.n_bins
+        avg_s = statistics.mean(like_ms) / 1e3
+        achieved = bins_per_launch / avg_s / 1e9
+        peak = N_SM * SFU_PER_SM_PER_CLK * clock_mhz * 1e6 / SFU_PER_BIN / 1e9
+        ess = [s["ess"] for s in summaries]
+        eff = [s["ess"] / n for s in summaries]
+        per_event_s = [1e4 / max(e * value / world, 1e-30) for e in eff]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "bns_population: one event x 2^20 proposal samples per step, 128513 bins "
+                                   "(20-1024 Hz, df=1/128), H1+L1, complex64 data, phase+distance marginalised",
+                       "events_per_rank": len(evs), "n_samples": n, "n_bins": w.n_bins, "sampled": "Mc,q,chi1,chi2,tc",
+                       "precision": "f32 per bin; f64 anchors, overlap sums, marginalisation, weights",
+                       "l2": "flushed between steps (256 MB write inside the timed region)",
+                       "parallelism": f"replicas x{world} (events sharded, no collective on the data path)",
+                       "setup_s": round(setup_s, 2)},
+            "seconds_to_1e4_ess": {"median": statistics.median(per_event_s), "max": max(per_event_s),
+                                   "efficiency_median": statistics.median(eff), "ess_median": statistics.median(ess)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbin/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "loglike_mixed_fold_kernel", "launch_ms": statistics.mean(like_ms),
+                         "note": "peak = 152 SM x 16 MUFU/clk x sm_max_mhz / 2 MUFU per (sample, bin)"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        if e2e:
+            out["e2e"] = e2e
+    for c in ctxs:
+        m.mbis_destroy(c)
+    return out, w, evs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--events", type=int, default=4, help="resident events per rank")
+    ap.add_argument("--samples", type=int, default=1 << 20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+    out, w, evs = run_gpu(args, rank, world)
+    if rank == 0:
+        if world == 1 and args.cpu_budget > 0:
+            leg = OracleLeg(w, w.events[:1])
+            rate, evals, secs = leg.rate(args.cpu_budget)
+            out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": leg.cores, "kind": "oracle",
+                                   "sample": f"{evals} likelihoods of the first event ({secs:.1f} s of FP64 oracle "
+                                             f"work, OpenMP over samples)"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload, as the reference arm: each step a bounded
+    sample of likelihoods of one event (draw -> likelihood -> weights)."""
+    w = workloads.bns_population(n_events=max(args.events, 1), n_samples=args.samples)
+    leg = OracleLeg(w, w.events[: min(args.events, 2)])
+    pilot = leg.batch(0, max(4, leg.cores))
+    per_step = max(leg.cores, int(4.0 * max(4, leg.cores) / max(pilot, 1e-3)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = leg.batch(i, per_step)
+        if i >= args.warmup:
+            times.append(t)
+    tot_t, tot_n = sum(times), per_step * args.steps
+    value = tot_n / tot_t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "bns_population: 128513 bins (20-1024 Hz, df=1/128), H1+L1, complex64 data, "
+                               f"phase+distance marginalised; each step a bounded sample of {per_step} likelihoods",
+                   "n_bins": w.n_bins},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": leg.cores, "kind": "oracle",
+                         "sample": f"{tot_n} likelihoods over {args.steps} steps ({tot_t:.1f} s)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * mbis.h -- C ABI of the GB300 (sm_103a) implementation of metric-based importance
+ * sampling for compact-binary parameter estimation (Nitz, "Robust, Rapid, and Simple
+ * Gravitational-wave Parameter Estimation").
+ *
+ * One call sequence per event:
+ *   mbis_create      event data, PSD, detectors, frequency grid, options -> context
+ *   mbis_set_metric  Gaussian proposal in the Fisher metric + prior box
+ *   mbis_draw        proposal samples theta ~ g, log g, log prior         (Eq. 5: g, pi)
+ *   mbis_loglike     log L(d | theta) for every sample                    (Eqs. 1-3)
+ *   mbis_reduce      weights, ESS, log evidence                           (Eqs. 5-6)
+ *   mbis_destroy
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes, never exceptions or aborts.  mbis_last_error() gives the message of
+ *     the last failure on a context (or of the last context-free failure when ctx is NULL).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of
+ *     the current device (e.g. a torch tensor's data_ptr()).  The caller owns every buffer
+ *     it passes; the library deep-copies what it keeps and never frees caller memory.
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *     device work of a call is enqueued on that stream.  Calls that return host results
+ *     (mbis_reduce, mbis_fisher, mbis_inject) synchronise that stream before returning.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Parameter slots (full 11-parameter sample):
+ *       0 Mc (detector-frame chirp mass, Msun)  1 q = m1/m2 (>= 1 inside the prior)
+ *       2 chi1z  3 chi2z  4 RA (rad)  5 dec (rad)  6 psi (rad)  7 iota (rad)
+ *       8 d_L (Mpc)  9 t_c (s, geocentre)  10 phi_c (rad, GW phase)
+ *   - Sample arrays are structure-of-arrays: theta[p * n + i] is slot ids[p] of sample i.
+ */
+#ifndef MBIS_H
+#define MBIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbis_ctx mbis_ctx;
+
+typedef enum {
+  MBIS_OK = 0,
+  MBIS_E_INVALID = 1,     /* bad argument: null pointer, size, slot id, inconsistent mode */
+  MBIS_E_OOM = 2,         /* device or host allocation failed */
+  MBIS_E_CUDA = 3,        /* a CUDA call failed; message holds cudaGetErrorString */
+  MBIS_E_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  MBIS_E_STATE = 5,       /* call out of order (e.g. mbis_draw before mbis_set_metric) */
+  MBIS_E_UNSUPPORTED = 6  /* valid request this build does not implement */
+} mbis_status;
+
+enum {
+  MBIS_P_MC = 0, MBIS_P_Q = 1, MBIS_P_CHI1 = 2, MBIS_P_CHI2 = 3, MBIS_P_RA = 4, MBIS_P_DEC = 5,
+  MBIS_P_PSI = 6, MBIS_P_IOTA = 7, MBIS_P_DL = 8, MBIS_P_TC = 9, MBIS_P_PHIC = 10, MBIS_NPAR = 11
+};
+
+/* marginalisation bits (Sec. III: analytic phase and distance, numeric time) */
+enum { MBIS_MARG_PHASE = 1, MBIS_MARG_DISTANCE = 2, MBIS_MARG_TIME = 4 };
+/* strain storage (the PSD is always double: aLIGO-like values ~1e-47 lie below FLT_MIN) */
+enum { MBIS_C128 = 0, MBIS_C64 = 1 };
+/* arithmetic of mbis_loglike */
+enum { MBIS_FP64 = 0, MBIS_MIXED = 1 };
+/* prior flags */
+enum { MBIS_PRIOR_M1M2 = 1 };
+
+/* Uniform grid f_k = f_lo + k df, k = 0 .. n_bins-1 (Eq. 1 as a rectangle sum, weight df). */
+typedef struct {
+  double f_lo, df;
+  int32_t n_bins;
+} mbis_freq_grid;
+
+/* Detector: vertex in Earth-centred Earth-fixed metres, unit arm vectors. */
+typedef struct {
+  double vertex_m[3], xarm[3], yarm[3];
+} mbis_detector;
+
+typedef struct {
+  int32_t n_det;        /* 1..4 */
+  int32_t dtype;        /* strain storage: MBIS_C128 (complex128) or MBIS_C64 (complex64) */
+  const void* strain;   /* host, [n_det][n_bins] interleaved (re, im), frequency-domain data d(f) */
+  double gmst_rad;      /* Greenwich mean sidereal time at the reference time */
+  double fixed[11];     /* values of the slots that are neither sampled nor marginalised */
+} mbis_event;
+
+typedef struct {
+  int32_t precision;    /* MBIS_FP64 or MBIS_MIXED */
+  uint32_t marg;        /* 0, PHASE, PHASE|DISTANCE, or TIME */
+  int32_t n_tshift;     /* TIME: number of shifts J (tau_j = (j - J/2) dt_shift) */
+  double dt_shift;      /* TIME: shift spacing, s */
+  double dmin_mpc, dmax_mpc;  /* DISTANCE: prior p(d) ~ d^2 on [dmin, dmax] */
+  int32_t debug_checks; /* nonzero: kernels check indices and report MBIS_E_INVALID */
+} mbis_options;
+
+/* Running reducer state and its derived summary (Eq. 6).  max_logw = -inf and ess = 0
+ * when every weight is zero (all_zero = 1). */
+typedef struct {
+  double ess, log_z, max_logw;
+  int64_t n;
+  double s1, s2;        /* sum e^(log w - max), sum e^(2 (log w - max)) */
+  int32_t all_zero;
+} mbis_summary;
+
+/* Create a context for one event.  Paper: Eqs. 1-3 (data d, PSD S_n).
+ *   event, psd (host, [n_det][n_bins] double, one-sided, > 0), dets
+ *   (host, n_det), grid, opts: read during the call and copied to the device; the caller
+ *   may free them afterwards.  *out receives the context (NULL on failure).
+ *   Errors: MBIS_E_INVALID (null, n_det/n_bins/grid out of range, unsupported marg or
+ *   precision combination), MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_create(const mbis_event* event, const double* psd, const mbis_detector* dets,
+                        const mbis_freq_grid* grid, const mbis_options* opts, mbis_ctx** out);
+
+/* Set the proposal: a Gaussian N(mean, scale^2 L L^T) over the P sampled slots (the
+ * local metric of Sec. II A, whose tiling the proposal of Sec. II approximates), and the
+ * prior box.  param_ids (host, P distinct slots), mean (host, P), chol_lower (host,
+ * P x P row-major lower-triangular factor, positive diagonal), prior_lo / prior_hi
+ * (host, P; ignored for RA, psi, phi_c, which take their full period).  prior_flags:
+ * MBIS_PRIOR_M1M2 makes the (Mc, q) prior flat in component masses (both slots must be
+ * sampled).  Slots marginalised by the options may not be sampled.
+ * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_set_metric(mbis_ctx* ctx, int32_t P, const int32_t* param_ids, const double* mean,
+                            const double* chol_lower, double scale, const double* prior_lo,
+                            const double* prior_hi, uint32_t prior_flags);
+
+/* Draw n proposal samples (g of Eq. 5) with Philox4x32-10: sample i uses counter
+ * (lo32(ctr0+i), hi32(ctr0+i), 2, block) and key (lo32(seed), hi32(seed)); Box-Muller
+ * normals z, theta = mean + scale L z, RA and phi_c wrapped into [0, 2 pi), psi into
+ * [0, pi).  Outputs (device): theta [P][n] SoA, log_q [n] = unwrapped Gaussian log
+ * density, log_prior [n] (-inf outside the prior).  log_q / log_prior may be NULL.
+ * Errors: MBIS_E_STATE (no metric), MBIS_E_INVALID (n < 0, null theta), MBIS_E_CUDA. */
+mbis_status mbis_draw(mbis_ctx* ctx, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
+                      double* log_prior, void* cuda_stream);
+
+/* Log likelihood ratio ln(L/L_n) of Eq. 3 (the -(d|d)/2 of Eq. 2 dropped) for n samples,
+ * marginalised as the options say: PHASE -> ln I0(|Z|) - H/2; PHASE|DISTANCE ->
+ * ln int p(d) I0(|Z1|/d) e^(-H1/(2 d^2)) dd; TIME -> ln mean_j e^(Re z_j - H/2).  theta
+ * (device, [P][n] SoA as written by mbis_draw), loglike (device, n).  Samples with an
+ * unphysical parameter (Mc <= 0, q <= 0, |chi| >= 1, d_L <= 0) get -inf.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_UNSUPPORTED, MBIS_E_CUDA. */
+mbis_status mbis_loglike(mbis_ctx* ctx, int64_t n, const double* theta, double* loglike, void* cuda_stream);
+
+/* Importance weights and Kish ESS (Eqs. 5-6), evidence Z = mean(w).  Two passes on the
+ * device: m = max(log L + log pi - log g), then FP64 sums S1 = sum e^(log w - m),
+ * S2 = sum e^(2 (log w - m)).  Inputs (device, n each).  weights_out (device, n) gets the
+ * normalised weights e^(log w - m) / S1 when not NULL.  accumulate != 0 merges this batch
+ * into the context's running state and reports the merged summary; 0 reports this batch
+ * alone and leaves the running state untouched.  *out (host) receives the summary;
+ * the stream is synchronised.  Uses device scratch owned by the context.
+ * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_reduce(mbis_ctx* ctx, int64_t n, const double* loglike, const double* log_prior,
+                        const double* log_q, double* weights_out, int32_t accumulate, mbis_summary* out,
+                        void* cuda_stream);
+
+/* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
+mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
+mbis_status mbis_reset_running(mbis_ctx* ctx);
+
+/* Merge two reducer states (associative; used to combine shards of one event). */
+void mbis_merge_summaries(const mbis_summary* a, const mbis_summary* b, mbis_summary* out);
+
+void mbis_destroy(mbis_ctx* ctx);
+const char* mbis_last_error(const mbis_ctx* ctx);
+
+/* ---- set-up helpers (not on the per-sample path) ------------------------------------ */
+
+/* Analytic aLIGO-like PSD fit (Ajith 2011) on the grid; out (host, n_bins doubles).
+ * The paper names only "Advanced LIGO O3-like" sensitivity (Sec. III A). */
+mbis_status mbis_psd_aligo(const mbis_freq_grid* grid, double* out);
+
+/* Synthetic data for one event: d = h(theta_true) (+ noise n_k = sqrt(S_k / (4 df))
+ * (g1 + i g2) when add_noise, g from Philox counter (k, det, 1, 0), key = noise_seed).
+ * theta_true (host, 11 slots).  strain_out (host, [n_det][n_bins] complex128 interleaved),
+ * snr2_out (host, may be NULL): optimal network SNR^2 = sum_det (h|h).  Computed in FP64
+ * on the device.  Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_inject(const mbis_freq_grid* grid, int32_t n_det, const mbis_detector* dets, const double* psd,
+                        double gmst_rad, const double* theta_true, uint64_t noise_seed, int32_t add_noise,
+                        double* strain_out, double* snr2_out);
+
+/* Fisher matrix Gamma_ij = sum_det (d_i h | d_j h) (the metric of the inner product of
+ * Eq. 1, Sec. II A) at theta (host, 11 slots) over slots ids (host, P), by FP64 central
+ * differences with absolute steps (host, P), computed on the device.  gamma_out (host,
+ * P x P row-major).  Uses the context's PSD, detectors and grid (not its data).
+ * Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_fisher(mbis_ctx* ctx, const double* theta, int32_t P, const int32_t* ids, const double* steps,
+                        double* gamma_out);
+
+/* Library build/version string. */
+const char* mbis_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBIS_H */

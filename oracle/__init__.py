@@ -31,12 +31,21 @@ PRIOR_M1M2 = 1
 
 def build(force: bool = False) -> str:
     """Compile ``mbis_oracle.c`` into ``liboracle.so`` (gcc, OpenMP, no fast-math)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC) or not _native(LIB):
         cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-std=gnu11",
                "-o", LIB + ".tmp", SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(LIB + ".tmp", LIB)
     return LIB
+
+
+def _native(path):
+    import platform
+    import struct
+    want = {"x86_64": 62, "amd64": 62, "aarch64": 183, "arm64": 183}.get(platform.machine().lower())
+    with open(path, "rb") as f:
+        head = f.read(20)
+    return head[:4] == b"\x7fELF" and (want is None or struct.unpack("<H", head[18:20])[0] == want)
 
 
 class _Complex(C.Structure):

@@ -1,8 +1,9 @@
-"""Test-side construction of synthetic events and proposals with the FP64 oracle.
+"""Synthetic events and proposals built with the FP64 oracle (test infrastructure).
 
 Every array produced here comes from the oracle (or from the seeded recipes in
 ``workloads``), never from the CUDA path, so it can serve as input to both sides of a
-parity comparison and as the source of expected values.
+parity comparison, as the source of expected values, and as the input of the timed CPU
+baseline.
 """
 import math
 
@@ -67,8 +68,8 @@ def make_proposal(ev, w: workloads.Workload, th):
         G = A - B @ np.linalg.solve(Cm, B.T)
     else:
         G = G[:P, :P]
-    width = {CHI1: 2 * w.chi_max, CHI2: 2 * w.chi_max, RA: 2 * math.pi, DEC: math.pi, PSI: math.pi, IOTA: math.pi,
-             PHIC: 2 * math.pi, DL: w.dmax - w.dmin}
+    width = {Q: 2.0, CHI1: 2 * w.chi_max, CHI2: 2 * w.chi_max, RA: 2 * math.pi, DEC: math.pi, PSI: math.pi,
+             IOTA: math.pi, PHIC: 2 * math.pi, DL: w.dmax - w.dmin}
     for p, i in enumerate(sampled):
         if i in width:
             G[p, p] += 12.0 / width[i] ** 2

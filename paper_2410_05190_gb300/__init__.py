@@ -1,0 +1,245 @@
+"""GB300-native metric-based importance sampling for compact-binary parameter estimation.
+
+Thin Python binding over the C ABI of ``libmbis.so`` (declared in ``include/mbis.h``):
+the functions below carry the same names as the C entry points and only marshal
+arguments (numpy arrays for host buffers, torch tensors or raw integers for device
+buffers and streams).  Every step of the computation runs in the library's CUDA kernels.
+Importing this package fails loudly when the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+MBIS_OK, MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA, MBIS_E_TIMEOUT, MBIS_E_STATE, MBIS_E_UNSUPPORTED = range(7)
+STATUS_NAMES = ["MBIS_OK", "MBIS_E_INVALID", "MBIS_E_OOM", "MBIS_E_CUDA", "MBIS_E_TIMEOUT", "MBIS_E_STATE",
+                "MBIS_E_UNSUPPORTED"]
+P_MC, P_Q, P_CHI1, P_CHI2, P_RA, P_DEC, P_PSI, P_IOTA, P_DL, P_TC, P_PHIC = range(11)
+NPAR = 11
+MARG_PHASE, MARG_DISTANCE, MARG_TIME = 1, 2, 4
+C128, C64 = 0, 1
+FP64, MIXED = 0, 1
+PRIOR_M1M2 = 1
+
+
+class MbisError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
+        self.status = status
+
+
+class FreqGrid(C.Structure):
+    _fields_ = [("f_lo", C.c_double), ("df", C.c_double), ("n_bins", C.c_int32)]
+
+
+class Detector(C.Structure):
+    _fields_ = [("vertex_m", C.c_double * 3), ("xarm", C.c_double * 3), ("yarm", C.c_double * 3)]
+
+
+class Event(C.Structure):
+    _fields_ = [("n_det", C.c_int32), ("dtype", C.c_int32), ("strain", C.c_void_p), ("gmst_rad", C.c_double),
+                ("fixed", C.c_double * 11)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("marg", C.c_uint32), ("n_tshift", C.c_int32), ("dt_shift", C.c_double),
+                ("dmin_mpc", C.c_double), ("dmax_mpc", C.c_double), ("debug_checks", C.c_int32)]
+
+
+class Summary(C.Structure):
+    _fields_ = [("ess", C.c_double), ("log_z", C.c_double), ("max_logw", C.c_double), ("n", C.c_int64),
+                ("s1", C.c_double), ("s2", C.c_double), ("all_zero", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    p, i32, i64, u32, u64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+    sigs = {
+        "mbis_create": [p, p, p, p, p, p],
+        "mbis_set_metric": [p, i32, p, p, p, d, p, p, u32],
+        "mbis_draw": [p, u64, u64, i64, p, p, p, p],
+        "mbis_loglike": [p, i64, p, p, p],
+        "mbis_reduce": [p, i64, p, p, p, p, i32, p, p],
+        "mbis_get_running": [p, p],
+        "mbis_reset_running": [p],
+        "mbis_psd_aligo": [p, p],
+        "mbis_inject": [p, i32, p, p, d, p, u64, i32, p, p],
+        "mbis_fisher": [p, p, i32, p, p, p],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        f.argtypes = args
+    lib.mbis_merge_summaries.restype = None
+    lib.mbis_merge_summaries.argtypes = [p, p, p]
+    lib.mbis_destroy.restype = None
+    lib.mbis_destroy.argtypes = [p]
+    lib.mbis_last_error.restype = C.c_char_p
+    lib.mbis_last_error.argtypes = [p]
+    lib.mbis_version.restype = C.c_char_p
+    lib.mbis_version.argtypes = []
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != MBIS_OK:
+        msg = _lib.mbis_last_error(ctx)
+        raise MbisError(status, msg.decode() if msg else "")
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _dev(x):
+    """Device pointer of a torch tensor (or a raw integer address); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_detectors(vertex, xarm, yarm):
+    n = len(vertex)
+    arr = (Detector * n)()
+    for d in range(n):
+        arr[d].vertex_m[:] = list(map(float, vertex[d]))
+        arr[d].xarm[:] = list(map(float, xarm[d]))
+        arr[d].yarm[:] = list(map(float, yarm[d]))
+    return arr
+
+
+# ------------------------------------------------------------------------------- entry points
+def mbis_create(strain, psd, detectors, f_lo, df, fixed, gmst=0.0, precision=MIXED, marg=MARG_PHASE, n_tshift=128,
+                dt_shift=1e-4, dmin=10.0, dmax=1000.0, debug_checks=0):
+    """strain: complex host array [n_det, n_bins] (complex128 or complex64); psd: float64
+    host array [n_det, n_bins]; detectors: ctypes array from make_detectors; fixed: 11
+    slot values.  Returns the context handle (int)."""
+    strain = np.ascontiguousarray(strain)
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    if strain.dtype == np.complex128:
+        dtype = C128
+    elif strain.dtype == np.complex64:
+        dtype = C64
+    else:
+        raise TypeError("strain must be complex128 or complex64")
+    n_det, n_bins = strain.shape
+    ev = Event(n_det, dtype, strain.ctypes.data, gmst, (C.c_double * 11)(*map(float, fixed)))
+    grid = FreqGrid(f_lo, df, n_bins)
+    opts = Options(precision, marg, n_tshift, dt_shift, dmin, dmax, debug_checks)
+    out = C.c_void_p()
+    _check(_lib.mbis_create(C.byref(ev), psd.ctypes.data, detectors, C.byref(grid), C.byref(opts), C.byref(out)))
+    return out.value
+
+
+def mbis_set_metric(ctx, param_ids, mean, chol_lower, scale, prior_lo, prior_hi, prior_flags=0):
+    ids, pid = _host(param_ids, np.int32)
+    m, pm = _host(mean, np.float64)
+    L, pL = _host(chol_lower, np.float64)
+    lo, plo = _host(prior_lo, np.float64)
+    hi, phi = _host(prior_hi, np.float64)
+    _check(_lib.mbis_set_metric(ctx, len(ids), pid, pm, pL, scale, plo, phi, prior_flags), ctx)
+
+
+def mbis_draw(ctx, seed, ctr0, n, theta, log_q=None, log_prior=None, stream=None):
+    _check(_lib.mbis_draw(ctx, seed, ctr0, n, _dev(theta), _dev(log_q), _dev(log_prior), _stream(stream)), ctx)
+
+
+def mbis_loglike(ctx, n, theta, loglike, stream=None):
+    _check(_lib.mbis_loglike(ctx, n, _dev(theta), _dev(loglike), _stream(stream)), ctx)
+
+
+def mbis_reduce(ctx, n, loglike, log_prior, log_q, weights_out=None, accumulate=False, stream=None):
+    out = Summary()
+    _check(_lib.mbis_reduce(ctx, n, _dev(loglike), _dev(log_prior), _dev(log_q), _dev(weights_out), int(accumulate),
+                            C.byref(out), _stream(stream)), ctx)
+    return out.as_dict()
+
+
+def mbis_get_running(ctx):
+    out = Summary()
+    _check(_lib.mbis_get_running(ctx, C.byref(out)), ctx)
+    return out.as_dict()
+
+
+def mbis_reset_running(ctx):
+    _check(_lib.mbis_reset_running(ctx), ctx)
+
+
+def mbis_merge_summaries(a: dict, b: dict):
+    sa = Summary(**a)
+    sb = Summary(**b)
+    out = Summary()
+    _lib.mbis_merge_summaries(C.byref(sa), C.byref(sb), C.byref(out))
+    return out.as_dict()
+
+
+def mbis_destroy(ctx):
+    _lib.mbis_destroy(ctx)
+
+
+def mbis_last_error(ctx=None):
+    m = _lib.mbis_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def mbis_version():
+    return _lib.mbis_version().decode()
+
+
+def mbis_psd_aligo(f_lo, df, n_bins):
+    out = np.zeros(n_bins)
+    grid = FreqGrid(f_lo, df, n_bins)
+    _check(_lib.mbis_psd_aligo(C.byref(grid), out.ctypes.data))
+    return out
+
+
+def mbis_inject(f_lo, df, n_bins, detectors, psd, gmst, theta_true, noise_seed=0, add_noise=False):
+    """Returns (strain complex128 [n_det, n_bins], optimal SNR^2)."""
+    n_det = len(detectors)
+    psd = np.ascontiguousarray(psd, dtype=np.float64).reshape(n_det, n_bins)
+    th, pth = _host(theta_true, np.float64)
+    out = np.zeros((n_det, n_bins), dtype=np.complex128)
+    snr2 = C.c_double()
+    grid = FreqGrid(f_lo, df, n_bins)
+    _check(_lib.mbis_inject(C.byref(grid), n_det, detectors, psd.ctypes.data, gmst, pth, noise_seed, int(add_noise),
+                            out.ctypes.data, C.byref(snr2)))
+    return out, snr2.value
+
+
+def mbis_fisher(ctx, theta, ids, steps):
+    th, pth = _host(theta, np.float64)
+    ids, pid = _host(ids, np.int32)
+    st, pst = _host(steps, np.float64)
+    P = len(ids)
+    g = np.zeros((P, P))
+    _check(_lib.mbis_fisher(ctx, pth, P, pid, pst, g.ctypes.data), ctx)
+    return g

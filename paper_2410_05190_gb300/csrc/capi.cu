@@ -1,0 +1,592 @@
+// capi.cu -- extern "C" entry points declared in include/mbis.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "marg.cuh"
+
+using namespace mbis;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mbis_status fail(mbis_ctx* ctx, mbis_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+#define CU_TRY(ctx, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+    }                                                                                            \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+bool is_periodic(int id) { return id == kRa || id == kPsi || id == kPhic; }
+
+// integral of (1 + q)^(2/5) q^(-6/5) over [a, b]: composite 8-point Gauss-Legendre
+double q_integral(double a, double b) {
+  double x[kGL8], w[kGL8];
+  gauss_legendre(kGL8, x, w);
+  const int panels = 256;
+  const double h = (b - a) / panels;
+  double s = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    const double mid = a + (p + 0.5) * h;
+    for (int i = 0; i < kGL8; ++i) {
+      const double q = mid + 0.5 * h * x[i];
+      s += 0.5 * h * w[i] * pow(1.0 + q, 0.4) * pow(q, -1.2);
+    }
+  }
+  return s;
+}
+
+void free_tables(mbis_ctx* c) {
+  dfree(c->d_cfold64);
+  dfree(c->d_tfold);
+  dfree(c->d_cdet64);
+  dfree(c->d_tdet);
+  dfree(c->d_cfold32);
+  dfree(c->d_plan);
+  c->n_blocks = 0;
+  c->tables_mode = -1;
+}
+
+DetResponse response_of(const mbis_ctx* c, int d) {
+  double fp, fc;
+  antenna(c->dets[d].xarm, c->dets[d].yarm, c->fixed[kRa], c->fixed[kDec], c->fixed[kPsi], c->gmst, &fp, &fc);
+  const double ci = cos(c->fixed[kIota]);
+  DetResponse r;
+  r.pre = fp * 0.5 * (1.0 + ci * ci);
+  r.pim = -fc * ci;
+  r.dt = geocentre_delay(c->dets[d].vertex_m, c->fixed[kRa], c->fixed[kDec], c->gmst);
+  return r;
+}
+
+bool sampled(const mbis_ctx* c, int slot) {
+  for (int p = 0; p < c->P; ++p)
+    if (c->ids[p] == slot) return true;
+  return false;
+}
+
+// bound on |C_j| over the prior box (grid over Mc, q, chi1, chi2; 50% margin)
+void coefficient_bounds(const mbis_ctx* c, double* cmax) {
+  double lo[4], hi[4];
+  const int slots[4] = {kMc, kQ, kChi1, kChi2};
+  for (int s = 0; s < 4; ++s) {
+    lo[s] = hi[s] = c->fixed[slots[s]];
+    for (int p = 0; p < c->P; ++p)
+      if (c->ids[p] == slots[s]) {
+        lo[s] = c->lo[p];
+        hi[s] = c->hi[p];
+      }
+  }
+  for (int j = 0; j < kNumBasis; ++j) cmax[j] = 0.0;
+  const int g = 5;
+  for (int a = 0; a < g; ++a)
+    for (int b = 0; b < g; ++b)
+      for (int x = 0; x < g; ++x)
+        for (int y = 0; y < g; ++y) {
+          const double mc = lo[0] + (hi[0] - lo[0]) * a / (g - 1), q = lo[1] + (hi[1] - lo[1]) * b / (g - 1);
+          const double c1 = lo[2] + (hi[2] - lo[2]) * x / (g - 1), c2 = lo[3] + (hi[3] - lo[3]) * y / (g - 1);
+          if (!(mc > 0 && q > 0)) continue;
+          const PhaseCoeffs pc = phase_coeffs(mc, q, c1, c2, 0.0, 0.0);
+          for (int j = 0; j < kNumBasis; ++j) cmax[j] = std::max(cmax[j], 1.5 * std::fabs(pc.C[j]));
+        }
+}
+
+mbis_status build_tables(mbis_ctx* c) {
+  const bool fold = !(sampled(c, kRa) || sampled(c, kDec) || sampled(c, kPsi) || sampled(c, kIota));
+  free_tables(c);
+  const int32_t n = c->n_bins, nd = c->n_det;
+  cudaStream_t s = nullptr;
+  double* d_w = nullptr;
+  if (fold) {
+    DetResponse det[kMaxDet];
+    for (int d = 0; d < nd; ++d) det[d] = response_of(c, d);
+    CU_TRY(c, cudaMalloc(&c->d_cfold64, sizeof(double2) * n));
+    CU_TRY(c, cudaMalloc(&c->d_tfold, sizeof(double) * (n + 1)));
+    CU_TRY(c, cudaMalloc(&d_w, sizeof(double) * n));
+    CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 1, det, c->d_cfold64, d_w, s));
+    CU_TRY(c, launch_prefix_rows(d_w, 1, n, c->d_tfold, s));
+    if (c->opts.precision == MBIS_MIXED) {
+      double* d_max = nullptr;
+      CU_TRY(c, cudaMalloc(&d_max, sizeof(double)));
+      CU_TRY(c, launch_max_abs(c->d_cfold64, n, d_max, s));
+      double mx = 0.0;
+      CU_TRY(c, cudaMemcpy(&mx, d_max, sizeof(double), cudaMemcpyDeviceToHost));
+      cudaFree(d_max);
+      c->cscale = (mx > 0.0 && std::isfinite(mx)) ? std::ldexp(1.0, std::ilogb(mx) + 1) : 1.0;
+      const int32_t n_pad = (n + kChunk - 1) / kChunk * kChunk;
+      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float2) * n_pad));
+      CU_TRY(c, launch_to_f32(c->d_cfold64, n, n_pad, 1.0 / c->cscale, c->d_cfold32, s));
+      PlanInput pin;
+      pin.f_lo = c->f_lo;
+      pin.df = c->df;
+      pin.n_bins = n;
+      coefficient_bounds(c, pin.cmax);
+      pin.tol_turns = 2e-8;
+      pin.rmax_turns = 1.0;
+      pin.max_block = 4096;
+      const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
+      c->n_blocks = (int32_t)plan.size();
+      CU_TRY(c, cudaMalloc(&c->d_plan, sizeof(AnchorBlock) * plan.size()));
+      CU_TRY(c, cudaMemcpy(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice));
+    }
+  } else {
+    CU_TRY(c, cudaMalloc(&c->d_cdet64, sizeof(double2) * (size_t)n * nd));
+    CU_TRY(c, cudaMalloc(&c->d_tdet, sizeof(double) * (size_t)(n + 1) * nd));
+    CU_TRY(c, cudaMalloc(&d_w, sizeof(double) * (size_t)n * nd));
+    CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 0, nullptr, c->d_cdet64,
+                                  d_w, s));
+    CU_TRY(c, launch_prefix_rows(d_w, nd, n, c->d_tdet, s));
+  }
+  CU_TRY(c, cudaDeviceSynchronize());
+  cudaFree(d_w);
+  c->tables_mode = fold ? 1 : 0;
+  return MBIS_OK;
+}
+
+void summary_from_state(double m, double s1, double s2, int64_t n, mbis_summary* out) {
+  out->max_logw = m;
+  out->s1 = s1;
+  out->s2 = s2;
+  out->n = n;
+  out->all_zero = !(m > -INFINITY) || !(s1 > 0.0);
+  out->ess = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+  out->log_z = (m > -INFINITY && s1 > 0.0 && n > 0) ? m + log(s1) - log((double)n) : -INFINITY;
+}
+
+__global__ void central_diff_kernel(int32_t P, const double2* h, const double* steps, int64_t len, double2* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t p = blockIdx.y;
+  if (i >= len || p >= P) return;
+  const double2 a = h[(2 * (int64_t)p) * len + i], b = h[(2 * (int64_t)p + 1) * len + i];
+  const double inv = 1.0 / (2.0 * steps[p]);
+  out[(int64_t)p * len + i] = make_double2((a.x - b.x) * inv, (a.y - b.y) * inv);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mbis_version(void) { return "mbis 0.1 (sm_103a)"; }
+
+const char* mbis_last_error(const mbis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_detector* dets, const mbis_freq_grid* grid,
+                        const mbis_options* opts, mbis_ctx** out) {
+  if (out) *out = nullptr;
+  if (!ev || !psd || !dets || !grid || !opts || !out || !ev->strain)
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: null argument");
+  if (ev->n_det < 1 || ev->n_det > kMaxDet) return fail(nullptr, MBIS_E_INVALID, "mbis_create: n_det must be 1..4");
+  if (ev->dtype != MBIS_C128 && ev->dtype != MBIS_C64) return fail(nullptr, MBIS_E_INVALID, "mbis_create: bad dtype");
+  if (grid->n_bins < 1 || !(grid->df > 0.0) || !(grid->f_lo > 0.0))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: grid needs n_bins >= 1, df > 0, f_lo > 0");
+  if (opts->precision != MBIS_FP64 && opts->precision != MBIS_MIXED)
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: precision must be MBIS_FP64 or MBIS_MIXED");
+  const uint32_t mg = opts->marg;
+  if (!(mg == 0 || mg == MBIS_MARG_PHASE || mg == (MBIS_MARG_PHASE | MBIS_MARG_DISTANCE) || mg == MBIS_MARG_TIME))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: marg must be 0, PHASE, PHASE|DISTANCE or TIME");
+  if ((mg & MBIS_MARG_DISTANCE) && !(opts->dmin_mpc > 0.0 && opts->dmax_mpc > opts->dmin_mpc))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: distance range needs 0 < dmin < dmax");
+  if ((mg & MBIS_MARG_TIME) && !(opts->n_tshift >= 1 && opts->dt_shift > 0.0))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: time grid needs n_tshift >= 1 and dt_shift > 0");
+
+  mbis_ctx* c = new (std::nothrow) mbis_ctx();
+  if (!c) return fail(nullptr, MBIS_E_OOM, "mbis_create: host allocation failed");
+  c->n_det = ev->n_det;
+  c->n_bins = grid->n_bins;
+  c->dtype = ev->dtype;
+  c->f_lo = grid->f_lo;
+  c->df = grid->df;
+  c->gmst = ev->gmst_rad;
+  std::memcpy(c->fixed, ev->fixed, sizeof(c->fixed));
+  std::memcpy(c->dets, dets, sizeof(mbis_detector) * ev->n_det);
+  c->opts = *opts;
+  auto bail = [&](mbis_status st) {
+    std::string m = c->err;
+    mbis_destroy(c);
+    g_last_error = m;
+    return st;
+  };
+  cudaGetDevice(&c->device);
+  const size_t nb = (size_t)c->n_bins * c->n_det;
+  const size_t csz = ev->dtype == MBIS_C128 ? 16 : 8;
+  cudaError_t e;
+#define CREATE_TRY(call)                                                                                 \
+  if ((e = (call)) != cudaSuccess) {                                                                     \
+    fail(c, e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA, std::string(#call) + ": " +        \
+                                                                        cudaGetErrorString(e));          \
+    return bail(e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA);                              \
+  }
+  CREATE_TRY(cudaMalloc(&c->d_strain, csz * nb));
+  CREATE_TRY(cudaMemcpy(c->d_strain, ev->strain, csz * nb, cudaMemcpyHostToDevice));
+  for (size_t i = 0; i < nb; ++i)
+    if (!(psd[i] > 0.0) || !std::isfinite(psd[i])) {
+      fail(c, MBIS_E_INVALID, "mbis_create: PSD must be positive and finite");
+      return bail(MBIS_E_INVALID);
+    }
+  CREATE_TRY(cudaMalloc(&c->d_psd64, sizeof(double) * nb));
+  CREATE_TRY(cudaMemcpy(c->d_psd64, psd, sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CREATE_TRY(cudaMalloc(&c->d_basis, sizeof(double) * kNumBasis * (size_t)c->n_bins));
+  CREATE_TRY(launch_basis_table(c->f_lo, c->df, c->n_bins, c->d_basis, nullptr));
+  {
+    double gl[kGLSize];
+    fill_gauss_legendre(gl);
+    CREATE_TRY(cudaMalloc(&c->d_gl, sizeof(gl)));
+    CREATE_TRY(cudaMemcpy(c->d_gl, gl, sizeof(gl), cudaMemcpyHostToDevice));
+  }
+  CREATE_TRY(cudaMalloc(&c->d_err, sizeof(int32_t)));
+  CREATE_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+  CREATE_TRY(cudaMalloc(&c->red.partials, sizeof(double) * 2 * kReduceBlocks));
+  CREATE_TRY(cudaMalloc(&c->red.counter, sizeof(unsigned int)));
+  CREATE_TRY(cudaMemset(c->red.counter, 0, sizeof(unsigned int)));
+  CREATE_TRY(cudaMalloc(&c->red.result, sizeof(double) * 4));
+  CREATE_TRY(cudaMallocHost(&c->h_result, sizeof(double) * 5));
+  CREATE_TRY(cudaDeviceSynchronize());
+#undef CREATE_TRY
+  *out = c;
+  return MBIS_OK;
+}
+
+void mbis_destroy(mbis_ctx* c) {
+  if (!c) return;
+  free_tables(c);
+  dfree(c->d_strain);
+  dfree(c->d_psd64);
+  dfree(c->d_basis);
+  dfree(c->d_gl);
+  dfree(c->d_err);
+  dfree(c->red.partials);
+  dfree(c->red.counter);
+  dfree(c->red.result);
+  if (c->h_result) cudaFreeHost(c->h_result);
+  delete c;
+}
+
+mbis_status mbis_set_metric(mbis_ctx* c, int32_t P, const int32_t* ids, const double* mean, const double* chol,
+                            double scale, const double* lo, const double* hi, uint32_t flags) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_set_metric: null context");
+  if (P < 1 || P > kMaxP || !ids || !mean || !chol || !lo || !hi)
+    return fail(c, MBIS_E_INVALID, "mbis_set_metric: P must be 1..11 and arrays non-null");
+  if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, MBIS_E_INVALID, "mbis_set_metric: scale must be > 0");
+  bool seen[kNumSlots] = {};
+  for (int p = 0; p < P; ++p) {
+    const int id = ids[p];
+    if (id < 0 || id >= kNumSlots || seen[id]) return fail(c, MBIS_E_INVALID, "mbis_set_metric: bad or repeated slot");
+    seen[id] = true;
+    if ((id == kPhic && (c->opts.marg & MBIS_MARG_PHASE)) || (id == kDl && (c->opts.marg & MBIS_MARG_DISTANCE)))
+      return fail(c, MBIS_E_INVALID, "mbis_set_metric: a marginalised slot cannot be sampled");
+    if (!(chol[p * P + p] > 0.0)) return fail(c, MBIS_E_INVALID, "mbis_set_metric: Cholesky diagonal must be > 0");
+    if (!is_periodic(id) && !(lo[p] < hi[p])) return fail(c, MBIS_E_INVALID, "mbis_set_metric: need prior_lo < hi");
+    if (id == kDec && (lo[p] < -kPi / 2 || hi[p] > kPi / 2))
+      return fail(c, MBIS_E_INVALID, "mbis_set_metric: dec prior outside [-pi/2, pi/2]");
+    if (id == kIota && (lo[p] < 0 || hi[p] > kPi))
+      return fail(c, MBIS_E_INVALID, "mbis_set_metric: iota prior outside [0, pi]");
+    if ((id == kMc || id == kQ || id == kDl) && !(lo[p] > 0.0))
+      return fail(c, MBIS_E_INVALID, "mbis_set_metric: Mc, q and d_L priors need lo > 0");
+  }
+  if ((flags & MBIS_PRIOR_M1M2) && !(seen[kMc] && seen[kQ]))
+    return fail(c, MBIS_E_INVALID, "mbis_set_metric: the component-mass prior needs Mc and q sampled");
+  c->P = P;
+  for (int p = 0; p < P; ++p) {
+    c->ids[p] = ids[p];
+    c->mean[p] = mean[p];
+    c->lo[p] = is_periodic(ids[p]) ? 0.0 : lo[p];
+    c->hi[p] = is_periodic(ids[p]) ? (ids[p] == kPsi ? kPi : kTwoPi) : hi[p];
+    for (int r = 0; r < kMaxP; ++r) c->chol[p * kMaxP + r] = (r <= p && r < P) ? chol[p * P + r] : 0.0;
+  }
+  c->scale = scale;
+  c->prior_flags = flags;
+  c->log_mass_norm = 0.0;
+  if (flags & MBIS_PRIOR_M1M2) {
+    double mlo = 0, mhi = 0, qlo = 0, qhi = 0;
+    for (int p = 0; p < P; ++p) {
+      if (ids[p] == kMc) { mlo = lo[p]; mhi = hi[p]; }
+      if (ids[p] == kQ) { qlo = lo[p]; qhi = hi[p]; }
+    }
+    c->log_mass_norm = log(0.5 * (mhi * mhi - mlo * mlo) * q_integral(qlo, qhi));
+  }
+  const mbis_status st = build_tables(c);
+  if (st != MBIS_OK) return st;
+  c->has_metric = true;
+  return MBIS_OK;
+}
+
+mbis_status mbis_draw(mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
+                      double* log_prior, void* stream) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_draw: null context");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_draw: call mbis_set_metric first");
+  if (n < 0 || (n > 0 && !theta)) return fail(c, MBIS_E_INVALID, "mbis_draw: bad n or null theta");
+  DrawArgs a = {};
+  a.P = c->P;
+  double logdet = 0.0;
+  for (int p = 0; p < c->P; ++p) {
+    a.ids[p] = c->ids[p];
+    a.mean[p] = c->mean[p];
+    a.lo[p] = c->lo[p];
+    a.hi[p] = c->hi[p];
+    logdet += log(c->chol[p * kMaxP + p]);
+  }
+  std::memcpy(a.chol, c->chol, sizeof(a.chol));
+  a.scale = c->scale;
+  a.flags = c->prior_flags;
+  a.log_mass_norm = c->log_mass_norm;
+  a.log_q_const = -logdet - 0.5 * c->P * log(kTwoPi) - c->P * log(c->scale);
+  a.seed = seed;
+  a.ctr0 = ctr0;
+  a.n = n;
+  a.theta = theta;
+  a.logq = log_q;
+  a.logp = log_prior;
+  CU_TRY(c, launch_draw(a, static_cast<cudaStream_t>(stream)));
+  return MBIS_OK;
+}
+
+mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* loglike, void* stream) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_loglike: null context");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_loglike: call mbis_set_metric first");
+  if (n < 0 || (n > 0 && (!theta || !loglike))) return fail(c, MBIS_E_INVALID, "mbis_loglike: bad n or null buffer");
+  if (c->opts.marg & MBIS_MARG_TIME)
+    return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: time marginalisation is not available in this build");
+  LikeArgs a = {};
+  a.n = n;
+  a.theta = theta;
+  a.out = loglike;
+  a.P = c->P;
+  for (int p = 0; p < c->P; ++p) a.ids[p] = c->ids[p];
+  std::memcpy(a.fixed, c->fixed, sizeof(a.fixed));
+  a.marg = c->opts.marg;
+  a.dmin = c->opts.dmin_mpc;
+  a.dmax = c->opts.dmax_mpc;
+  a.n_tshift = c->opts.n_tshift;
+  a.dt_shift = c->opts.dt_shift;
+  a.n_bins = c->n_bins;
+  a.n_det = c->n_det;
+  a.f_lo = c->f_lo;
+  a.df = c->df;
+  a.fold = c->tables_mode == 1;
+  a.basis = c->d_basis;
+  a.cfold64 = c->d_cfold64;
+  a.tfold = c->d_tfold;
+  a.cdet64 = c->d_cdet64;
+  a.tdet = c->d_tdet;
+  for (int d = 0; d < c->n_det; ++d)
+    for (int i = 0; i < 3; ++i) {
+      a.det_vertex[d][i] = c->dets[d].vertex_m[i];
+      a.det_x[d][i] = c->dets[d].xarm[i];
+      a.det_y[d][i] = c->dets[d].yarm[i];
+    }
+  a.gmst = c->gmst;
+  a.cfold32 = c->d_cfold32;
+  a.cscale = c->cscale;
+  a.plan = c->d_plan;
+  a.n_blocks = c->n_blocks;
+  a.err = c->d_err;
+  a.gl = c->d_gl;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->opts.precision == MBIS_FP64) {
+    CU_TRY(c, launch_loglike_fp64(a, s));
+  } else {
+    if (!a.fold)
+      return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: mixed precision with sampled sky/orientation not available");
+    CU_TRY(c, launch_loglike_mixed(a, s));
+  }
+  return MBIS_OK;
+}
+
+void mbis_merge_summaries(const mbis_summary* a, const mbis_summary* b, mbis_summary* out) {
+  const double m = std::max(a->max_logw, b->max_logw);
+  double s1 = 0.0, s2 = 0.0;
+  if (m > -INFINITY) {
+    if (a->max_logw > -INFINITY) {
+      const double r = exp(a->max_logw - m);
+      s1 += a->s1 * r;
+      s2 += a->s2 * r * r;
+    }
+    if (b->max_logw > -INFINITY) {
+      const double r = exp(b->max_logw - m);
+      s1 += b->s1 * r;
+      s2 += b->s2 * r * r;
+    }
+  }
+  summary_from_state(m, s1, s2, a->n + b->n, out);
+}
+
+mbis_status mbis_reduce(mbis_ctx* c, int64_t n, const double* loglike, const double* log_prior, const double* log_q,
+                        double* weights_out, int32_t accumulate, mbis_summary* out, void* stream) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_reduce: null context");
+  if (n < 0 || !out || (n > 0 && (!loglike || !log_prior || !log_q)))
+    return fail(c, MBIS_E_INVALID, "mbis_reduce: bad n or null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU_TRY(c, launch_reduce(n, loglike, log_prior, log_q, weights_out, c->red, s));
+  CU_TRY(c, cudaMemcpyAsync(c->h_result, c->red.result, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  CU_TRY(c, cudaMemcpyAsync(c->h_result + 4, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CU_TRY(c, cudaStreamSynchronize(s));
+  int32_t derr;
+  std::memcpy(&derr, c->h_result + 4, sizeof(int32_t));
+  if (derr != 0) {
+    cudaMemset(c->d_err, 0, sizeof(int32_t));
+    return fail(c, MBIS_E_TIMEOUT, "a device-side wait timed out in an earlier kernel of this context");
+  }
+  mbis_summary batch;
+  summary_from_state(n > 0 ? c->h_result[0] : -INFINITY, c->h_result[1], c->h_result[2], n, &batch);
+  if (n == 0) summary_from_state(-INFINITY, 0.0, 0.0, 0, &batch);
+  if (accumulate) {
+    if (c->has_running) {
+      mbis_summary merged;
+      mbis_merge_summaries(&c->running, &batch, &merged);
+      c->running = merged;
+    } else {
+      c->running = batch;
+      c->has_running = true;
+    }
+    *out = c->running;
+  } else {
+    *out = batch;
+  }
+  return MBIS_OK;
+}
+
+mbis_status mbis_get_running(const mbis_ctx* c, mbis_summary* out) {
+  if (!c || !out) return fail(nullptr, MBIS_E_INVALID, "mbis_get_running: null argument");
+  if (c->has_running)
+    *out = c->running;
+  else
+    summary_from_state(-INFINITY, 0.0, 0.0, 0, out);
+  return MBIS_OK;
+}
+
+mbis_status mbis_reset_running(mbis_ctx* c) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_reset_running: null context");
+  c->has_running = false;
+  c->running = mbis_summary{};
+  return MBIS_OK;
+}
+
+mbis_status mbis_psd_aligo(const mbis_freq_grid* grid, double* out) {
+  if (!grid || !out || grid->n_bins < 1 || !(grid->f_lo > 0.0) || !(grid->df > 0.0))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_psd_aligo: bad grid or null output");
+  for (int32_t k = 0; k < grid->n_bins; ++k) {
+    const double f = grid->f_lo + k * grid->df, x = f / 215.0, x2 = x * x;
+    out[k] = 1e-49 * (pow(x, -4.14) - 5.0 / x2 + 111.0 * (1.0 - x2 + 0.5 * x2 * x2) / (1.0 + 0.5 * x2));
+  }
+  return MBIS_OK;
+}
+
+mbis_status mbis_inject(const mbis_freq_grid* grid, int32_t n_det, const mbis_detector* dets, const double* psd,
+                        double gmst, const double* theta, uint64_t seed, int32_t add_noise, double* strain_out,
+                        double* snr2_out) {
+  if (!grid || !dets || !psd || !theta || !strain_out || n_det < 1 || n_det > kMaxDet || grid->n_bins < 1)
+    return fail(nullptr, MBIS_E_INVALID, "mbis_inject: bad argument");
+  const int32_t n = grid->n_bins;
+  const size_t len = (size_t)n * n_det;
+  double *d_psd = nullptr, *d_geom = nullptr, *d_par = nullptr, *d_snr = nullptr;
+  double2* d_h = nullptr;
+  std::vector<double> geom(9 * n_det);
+  for (int d = 0; d < n_det; ++d)
+    for (int i = 0; i < 3; ++i) {
+      geom[9 * d + i] = dets[d].vertex_m[i];
+      geom[9 * d + 3 + i] = dets[d].xarm[i];
+      geom[9 * d + 6 + i] = dets[d].yarm[i];
+    }
+  mbis_status st = MBIS_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&d_psd, sizeof(double) * len))) break;
+    if ((e = cudaMalloc(&d_geom, sizeof(double) * geom.size()))) break;
+    if ((e = cudaMalloc(&d_par, sizeof(double) * kNumSlots))) break;
+    if ((e = cudaMalloc(&d_snr, sizeof(double)))) break;
+    if ((e = cudaMalloc(&d_h, sizeof(double2) * len))) break;
+    if ((e = cudaMemcpy(d_psd, psd, sizeof(double) * len, cudaMemcpyHostToDevice))) break;
+    if ((e = cudaMemcpy(d_geom, geom.data(), sizeof(double) * geom.size(), cudaMemcpyHostToDevice))) break;
+    if ((e = cudaMemcpy(d_par, theta, sizeof(double) * kNumSlots, cudaMemcpyHostToDevice))) break;
+    if ((e = launch_waveforms(1, d_par, n_det, n, grid->f_lo, grid->df, nullptr, d_geom, gmst, d_h, nullptr))) break;
+    if ((e = launch_inner_products(1, d_h, 1, d_h, n_det, n, grid->df, d_psd, d_snr, nullptr))) break;
+    if (add_noise && (e = launch_noise(n_det, n, grid->df, d_psd, seed, d_h, nullptr))) break;
+    if ((e = cudaMemcpy(strain_out, d_h, sizeof(double2) * len, cudaMemcpyDeviceToHost))) break;
+    double snr2 = 0.0;
+    if ((e = cudaMemcpy(&snr2, d_snr, sizeof(double), cudaMemcpyDeviceToHost))) break;
+    if (snr2_out) *snr2_out = snr2;
+  } while (0);
+  if (e != cudaSuccess)
+    st = fail(nullptr, e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,
+              std::string("mbis_inject: ") + cudaGetErrorString(e));
+  cudaFree(d_psd);
+  cudaFree(d_geom);
+  cudaFree(d_par);
+  cudaFree(d_snr);
+  cudaFree(d_h);
+  return st;
+}
+
+mbis_status mbis_fisher(mbis_ctx* c, const double* theta, int32_t P, const int32_t* ids, const double* steps,
+                        double* gamma_out) {
+  if (!c || !theta || !ids || !steps || !gamma_out || P < 1 || P > kNumSlots)
+    return fail(c, MBIS_E_INVALID, "mbis_fisher: bad argument");
+  for (int p = 0; p < P; ++p)
+    if (ids[p] < 0 || ids[p] >= kNumSlots || !(steps[p] > 0.0))
+      return fail(c, MBIS_E_INVALID, "mbis_fisher: bad slot or non-positive step");
+  const int32_t n = c->n_bins, nd = c->n_det;
+  const int64_t len = (int64_t)n * nd;
+  std::vector<double> par(2 * P * kNumSlots), geom(9 * nd);
+  for (int p = 0; p < P; ++p)
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      double* v = &par[(2 * p + sgn) * kNumSlots];
+      std::memcpy(v, theta, sizeof(double) * kNumSlots);
+      v[ids[p]] += sgn == 0 ? steps[p] : -steps[p];
+    }
+  for (int d = 0; d < nd; ++d)
+    for (int i = 0; i < 3; ++i) {
+      geom[9 * d + i] = c->dets[d].vertex_m[i];
+      geom[9 * d + 3 + i] = c->dets[d].xarm[i];
+      geom[9 * d + 6 + i] = c->dets[d].yarm[i];
+    }
+  double *d_par = nullptr, *d_geom = nullptr, *d_steps = nullptr, *d_g = nullptr;
+  double2 *d_h = nullptr, *d_D = nullptr;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&d_par, sizeof(double) * par.size()))) break;
+    if ((e = cudaMalloc(&d_geom, sizeof(double) * geom.size()))) break;
+    if ((e = cudaMalloc(&d_steps, sizeof(double) * P))) break;
+    if ((e = cudaMalloc(&d_g, sizeof(double) * P * P))) break;
+    if ((e = cudaMalloc(&d_h, sizeof(double2) * 2 * P * len))) break;
+    if ((e = cudaMalloc(&d_D, sizeof(double2) * P * len))) break;
+    if ((e = cudaMemcpy(d_par, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice))) break;
+    if ((e = cudaMemcpy(d_geom, geom.data(), sizeof(double) * geom.size(), cudaMemcpyHostToDevice))) break;
+    if ((e = cudaMemcpy(d_steps, steps, sizeof(double) * P, cudaMemcpyHostToDevice))) break;
+    if ((e = launch_waveforms(2 * P, d_par, nd, n, c->f_lo, c->df, nullptr, d_geom, c->gmst, d_h, nullptr))) break;
+    dim3 grid((unsigned)((len + 255) / 256), P);
+    central_diff_kernel<<<grid, 256>>>(P, d_h, d_steps, len, d_D);
+    if ((e = cudaGetLastError())) break;
+    if ((e = launch_inner_products(P, d_D, P, d_D, nd, n, c->df, c->d_psd64, d_g, nullptr))) break;
+    if ((e = cudaMemcpy(gamma_out, d_g, sizeof(double) * P * P, cudaMemcpyDeviceToHost))) break;
+  } while (0);
+  cudaFree(d_par);
+  cudaFree(d_geom);
+  cudaFree(d_steps);
+  cudaFree(d_g);
+  cudaFree(d_h);
+  cudaFree(d_D);
+  if (e != cudaSuccess)
+    return fail(c, e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,
+                std::string("mbis_fisher: ") + cudaGetErrorString(e));
+  return MBIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// internal.h -- context layout and kernel launchers of the CUDA path (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mbis.h"
+#include "physics.cuh"
+
+namespace mbis {
+
+constexpr int kMaxDet = 4;
+constexpr int kMaxP = 11;
+constexpr int kRemDeg = 5;          // degree of the FP32 remainder polynomial per anchor block
+constexpr int kChunk = 512;         // bins per shared-memory chunk of the mixed kernel
+constexpr int kMixedThreads = 128;  // samples per CTA of the mixed kernel
+constexpr int kReduceBlocks = 608;  // 4 x 152 SMs
+constexpr int kReduceThreads = 256;
+
+// Anchor block of the mixed-precision phase: bins [k0, k1) expanded about bin kc.
+//   Psi(f_k)/2pi = [cst + sum_j C_j B_j(f_c)] + (k - kc) [sum_j C_j dB_j] + sum_j C_j R_j(k - kc)
+// with R_j(w) ~ sum_m E[j][m] w^m the remainder of basis j beyond its tangent at f_c.
+struct AnchorBlock {
+  int32_t k0, k1, kc, pad;
+  double B[kNumBasis];     // basis_j(f_kc)
+  double dB[kNumBasis];    // basis_j'(f_kc) * df
+  float E[kNumBasis - 1][kRemDeg + 1];  // basis 8 (f) is linear: no remainder
+};
+
+struct DetResponse {
+  double pre, pim;  // P_det = F+ (1 + cos^2 i)/2 - i Fx cos i
+  double dt;        // geocentre delay, s
+};
+
+// Arguments shared by the likelihood kernels.
+struct LikeArgs {
+  int64_t n;
+  const double* theta;  // [P][n]
+  double* out;          // [n]
+  int32_t P;
+  int32_t ids[kMaxP];
+  double fixed[kNumSlots];
+  uint32_t marg;
+  double dmin, dmax;
+  int32_t n_tshift;
+  double dt_shift;
+  int32_t n_bins, n_det;
+  double f_lo, df;
+  int32_t fold;               // extrinsics fixed: detectors folded into one table
+  // FP64 tables
+  const double* basis;        // [9][n_bins]
+  const double2* cfold64;     // [n_bins] (fold)
+  const double* tfold;        // [n_bins + 1] (fold) prefix sums for <h|h>
+  const double2* cdet64;      // [n_det][n_bins] (non-fold)
+  const double* tdet;         // [n_det][n_bins + 1]
+  double det_vertex[kMaxDet][3], det_x[kMaxDet][3], det_y[kMaxDet][3];
+  double gmst;
+  // mixed tables
+  const float2* cfold32;      // [padded n_bins], scaled by 1 / cscale
+  double cscale;
+  const AnchorBlock* plan;
+  int32_t n_blocks;
+  int32_t* err;               // device error word (timeouts)
+  const double* gl;           // Gauss-Legendre nodes / weights (marg.cuh layout)
+};
+
+struct DrawArgs {
+  int32_t P;
+  int32_t ids[kMaxP];
+  double mean[kMaxP];
+  double chol[kMaxP * kMaxP];
+  double scale;
+  double lo[kMaxP], hi[kMaxP];
+  uint32_t flags;
+  double log_mass_norm;  // ln of the (Mc, q) volume of the flat-in-(m1, m2) prior
+  double log_q_const;    // -sum ln L_pp - (P/2) ln 2pi - P ln s
+  uint64_t seed, ctr0;
+  int64_t n;
+  double* theta;
+  double* logq;
+  double* logp;
+};
+
+// kernel launchers (each returns cudaGetLastError() of its launch)
+cudaError_t launch_basis_table(double f_lo, double df, int32_t n, double* out, cudaStream_t s);
+cudaError_t launch_event_tables(int32_t n_det, int32_t n_bins, double f_lo, double df, int32_t dtype,
+                                const void* strain, const double* psd, int32_t fold, const DetResponse* det,
+                                double2* c_out, double* w_out, cudaStream_t s);
+cudaError_t launch_prefix_rows(const double* w, int32_t rows, int32_t n, double* T, cudaStream_t s);
+cudaError_t launch_max_abs(const double2* c, int32_t n, double* out, cudaStream_t s);
+cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float2* out, cudaStream_t s);
+cudaError_t launch_draw(const DrawArgs& a, cudaStream_t s);
+cudaError_t launch_loglike_fp64(const LikeArgs& a, cudaStream_t s);
+cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s);
+
+// two-pass weight reduction; partials / counter / result are device scratch
+struct ReduceScratch {
+  double* partials;       // [2 * kReduceBlocks]
+  unsigned int* counter;  // [1], zero between calls
+  double* result;         // [4]: m, s1, s2, n
+};
+cudaError_t launch_reduce(int64_t n, const double* loglike, const double* logp, const double* logq,
+                          double* weights, const ReduceScratch& scr, cudaStream_t s);
+
+// waveform helpers (FP64): strain of n_par parameter vectors, and inner products
+cudaError_t launch_waveforms(int32_t n_par, const double* par /*[n_par][11] device*/, int32_t n_det, int32_t n_bins,
+                             double f_lo, double df, const DetResponse* unused, const double* det_geom /*device*/,
+                             double gmst, double2* h_out /*[n_par][n_det][n_bins]*/, cudaStream_t s);
+cudaError_t launch_noise(int32_t n_det, int32_t n_bins, double df, const double* psd, uint64_t seed, double2* h_io,
+                         cudaStream_t s);
+cudaError_t launch_inner_products(int32_t n_a, const double2* a, int32_t n_b, const double2* b, int32_t n_det,
+                                  int32_t n_bins, double df, const double* psd, double* out /*[n_a][n_b]*/,
+                                  cudaStream_t s);
+
+// host-side anchor planning of the mixed kernel
+struct PlanInput {
+  double f_lo, df;
+  int32_t n_bins;
+  double cmax[kNumBasis];  // bound on |C_j| over the prior
+  double tol_turns;        // bound on the fit error of the phase
+  double rmax_turns;       // bound on |remainder| kept in FP32
+  int32_t max_block;
+};
+std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in);
+
+}  // namespace mbis
+
+// the context behind the opaque handle
+struct mbis_ctx {
+  int32_t n_det = 0, n_bins = 0, dtype = 0;
+  double f_lo = 0, df = 0, gmst = 0;
+  double fixed[mbis::kNumSlots] = {};
+  mbis_detector dets[mbis::kMaxDet] = {};
+  mbis_options opts = {};
+  int device = 0;
+  void* d_strain = nullptr;
+  double* d_psd64 = nullptr;  // [n_det][n_bins]
+  // proposal
+  bool has_metric = false;
+  int32_t P = 0;
+  int32_t ids[mbis::kMaxP] = {};
+  double mean[mbis::kMaxP] = {}, chol[mbis::kMaxP * mbis::kMaxP] = {}, lo[mbis::kMaxP] = {}, hi[mbis::kMaxP] = {};
+  double scale = 1.0;
+  uint32_t prior_flags = 0;
+  double log_mass_norm = 0.0;
+  // tables
+  int32_t tables_mode = -1;  // -1 none, 1 fold, 0 per-detector
+  double* d_basis = nullptr;
+  double2* d_cfold64 = nullptr;
+  double* d_tfold = nullptr;
+  double2* d_cdet64 = nullptr;
+  double* d_tdet = nullptr;
+  float2* d_cfold32 = nullptr;
+  double cscale = 1.0;
+  mbis::AnchorBlock* d_plan = nullptr;
+  int32_t n_blocks = 0;
+  int32_t* d_err = nullptr;
+  double* d_gl = nullptr;
+  // reduction scratch
+  mbis::ReduceScratch red = {};
+  double* h_result = nullptr;  // pinned, 4 doubles
+  mbis_summary running = {};
+  bool has_running = false;
+  std::string err;
+};

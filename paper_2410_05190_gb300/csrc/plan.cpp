@@ -1,0 +1,149 @@
+// plan.cpp -- host-side anchor-block plan of the mixed-precision phase.
+//
+// The TaylorF2 phase reaches ~10^4 turns at 20 Hz for a neutron-star binary, far beyond
+// what FP32 resolves, while the GB300 executes FP64 at a small fraction of its FP32 rate.
+// The bins are therefore cut into blocks.  In block [k0, k1) with centre bin kc the phase is
+//   Psi_k/2pi = X + (k - kc) Y + sum_j C_j R_j(k - kc),
+// where X and Y (value and per-bin slope at kc) are taken in FP64 once per block and sample
+// and reduced modulo one turn, and R_j, the remainder of basis function j beyond its tangent
+// at f_kc, is a small smooth function that a degree-5 polynomial in w = k - kc represents
+// to well below 1e-7 turns.  Blocks grow as long as (i) sum_j max|C_j| * fit_error_j stays
+// under tol and (ii) sum_j max|C_j| * max|R_j| stays under rmax, so that the FP32 remainder
+// keeps ~1e-7-turn resolution.  max|C_j| is bounded over the prior box by the caller.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace mbis {
+namespace {
+
+// solve the (n x n) system A x = b in place (partial pivoting)
+void solve_dense(int n, double* A, double* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = b[c];
+    for (int k = c + 1; k < n; ++k) s -= A[c * n + k] * b[k];
+    b[c] = s / A[c * n + c];
+  }
+}
+
+struct Fit {
+  AnchorBlock blk;
+  double err_bound, r_bound;
+};
+
+Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
+  constexpr int D = kRemDeg + 1;
+  Fit out;
+  AnchorBlock& b = out.blk;
+  b.k0 = k0;
+  b.k1 = k0 + S;
+  b.kc = k0 + (S - 1) / 2;
+  b.pad = 0;
+  const double fc = in.f_lo + (double)b.kc * in.df;
+  for (int j = 0; j < kNumBasis; ++j) {
+    b.B[j] = basis(j, fc);
+    b.dB[j] = basis_deriv(j, fc) * in.df;
+  }
+  const double wa = (double)(k0 - b.kc), wb = (double)(k0 + S - 1 - b.kc);
+  const double h = std::max(1.0, std::max(std::fabs(wa), std::fabs(wb)));
+  const double mid = 0.5 * (wa + wb), half = std::max(0.5 * (wb - wa), 0.5);
+  out.err_bound = 0.0;
+  out.r_bound = 0.0;
+  for (int j = 0; j < kNumBasis - 1; ++j) {
+    auto rem = [&](double w) { return basis(j, fc + w * in.df) - b.B[j] - w * b.dB[j]; };
+    // interpolate at Chebyshev points of the block, monomials in u = w / h
+    double V[D * D], y[D];
+    for (int i = 0; i < D; ++i) {
+      const double w = mid + half * std::cos(kPi * (i + 0.5) / D);
+      const double u = w / h;
+      double p = 1.0;
+      for (int m = 0; m < D; ++m) {
+        V[i * D + m] = p;
+        p *= u;
+      }
+      y[i] = rem(w);
+    }
+    solve_dense(D, V, y);
+    double hm = 1.0;
+    for (int m = 0; m < D; ++m) {
+      b.E[j][m] = (float)(y[m] / hm);
+      hm *= h;
+    }
+    // error of the FP32-stored polynomial on the block's bins (all, or 257 evenly spaced)
+    double emax = 0.0, rmax = 0.0;
+    const int32_t npts = std::min<int32_t>(S, 257);
+    for (int32_t i = 0; i < npts; ++i) {
+      const int32_t kk = (npts == S) ? k0 + i : k0 + (int32_t)std::llround((double)i * (S - 1) / (npts - 1));
+      const double w = (double)(kk - b.kc);
+      double p = 0.0;
+      for (int m = D - 1; m >= 0; --m) p = p * w + (double)b.E[j][m];
+      const double r = rem(w);
+      emax = std::max(emax, std::fabs(p - r));
+      rmax = std::max(rmax, std::fabs(r));
+    }
+    out.err_bound += in.cmax[j] * emax;
+    out.r_bound += in.cmax[j] * rmax;
+  }
+  return out;
+}
+
+}  // namespace
+
+std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
+  std::vector<AnchorBlock> blocks;
+  int32_t k0 = 0;
+  int32_t guess = 64;
+  while (k0 < in.n_bins) {
+    const int32_t remaining = in.n_bins - k0;
+    const int32_t cap = std::min(remaining, in.max_block);
+    auto ok = [&](int32_t S) {
+      const Fit f = fit_block(in, k0, S);
+      return f.err_bound <= in.tol_turns && f.r_bound <= in.rmax_turns;
+    };
+    int32_t good = std::min<int32_t>(cap, 8);  // short blocks are interpolated exactly
+    int32_t S = std::min(cap, std::max(good, guess));
+    int32_t bad = -1;
+    if (ok(S)) {
+      good = S;
+      while (good < cap) {
+        S = std::min(cap, good * 2);
+        if (ok(S)) {
+          good = S;
+        } else {
+          bad = S;
+          break;
+        }
+      }
+    } else {
+      bad = S;
+    }
+    if (bad > 0) {
+      while (bad - good > 1) {
+        const int32_t m = good + (bad - good) / 2;
+        if (ok(m)) good = m; else bad = m;
+      }
+    }
+    blocks.push_back(fit_block(in, k0, good).blk);
+    k0 += good;
+    guess = good;
+  }
+  return blocks;
+}
+
+}  // namespace mbis

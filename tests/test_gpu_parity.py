@@ -1,0 +1,261 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: |delta log L| <= 1e-3 per sample (the stated bound of the method); draws to
+1e-12 relative (both sides evaluate the same Philox words in FP64); ESS and log Z to 1e-3
+relative when computed from each side's own log L, and to 1e-12 when the reduction
+alone is compared on identical inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads import MC, Q, CHI1, CHI2, RA, DEC, PSI, IOTA, DL, TC, PHIC
+from oracle.events import make_event, make_proposal
+
+pytestmark = pytest.mark.gpu
+
+LOGL_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2410_05190_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def to_fp32_data(ev):
+    """Round an oracle event's data to the complex64 the GPU stores (the PSD stays FP64)."""
+    s = (ev.strain[..., 0] + 1j * ev.strain[..., 1]).astype(np.complex64)
+    ev.set_strain(np.stack([s.real.astype(np.float64), s.imag.astype(np.float64)], axis=-1))
+    return s, ev.psd.copy()
+
+
+def gpu_context(m, ev, w, spec, th, precision):
+    if w.complex_dtype == "c64":
+        strain, psd = to_fp32_data(ev)
+    else:
+        strain, psd = ev.strain[..., 0] + 1j * ev.strain[..., 1], ev.psd.copy()
+    dets = m.make_detectors(ev.vertex, ev.xarm, ev.yarm)
+    return m.mbis_create(strain, psd, dets, w.f_lo, w.df, th, gmst=spec.gmst, precision=precision, marg=w.marg,
+                         n_tshift=w.n_tshift, dt_shift=w.dt_shift, dmin=w.dmin, dmax=w.dmax)
+
+
+def set_metric(m, ctx, prop):
+    m.mbis_set_metric(ctx, prop["ids"], prop["mean"], prop["chol"], prop["scale"], prop["lo"], prop["hi"],
+                      prop["flags"])
+
+
+def gpu_loglike(m, torch, ctx, theta_soa):
+    th = torch.tensor(np.ascontiguousarray(theta_soa), dtype=torch.float64, device="cuda")
+    n = th.shape[1]
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    m.mbis_loglike(ctx, n, th, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def compare_loglike(got, ref, logp):
+    inside = np.isfinite(logp)
+    assert np.all(np.isfinite(ref[inside]))
+    d = np.abs(got[inside] - ref[inside])
+    assert d.max() <= LOGL_TOL, (d.max(), int(np.argmax(d)))
+    return d.max()
+
+
+# --------------------------------------------------------------------------------- tiny event
+@pytest.fixture(scope="module")
+def tiny():
+    w = workloads.tiny(n_samples=4096)
+    spec = w.events[0]
+    ev, th, _ = make_event(w, spec)
+    prop = make_proposal(ev, w, th)
+    return w, spec, ev, th, prop
+
+
+def test_draws_match_oracle(m, torch, tiny):
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64)
+    try:
+        set_metric(m, ctx, prop)
+        for n, ctr0 in [(4096, 0), (1000, 123457)]:   # full and ragged batches
+            P = len(prop["ids"])
+            theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+            lq = torch.empty(n, dtype=torch.float64, device="cuda")
+            lp = torch.empty(n, dtype=torch.float64, device="cuda")
+            m.mbis_draw(ctx, spec.draw_seed, ctr0, n, theta, lq, lp)
+            torch.cuda.synchronize()
+            ref_th, ref_lq = oracle.draw(spec.draw_seed, ctr0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+            ref_lp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], ref_th)
+            np.testing.assert_allclose(theta.cpu().numpy(), ref_th, rtol=1e-12, atol=1e-13)
+            np.testing.assert_allclose(lq.cpu().numpy(), ref_lq, rtol=1e-12, atol=1e-12)
+            g = lp.cpu().numpy()
+            assert np.array_equal(np.isfinite(g), np.isfinite(ref_lp))
+            np.testing.assert_allclose(g[np.isfinite(g)], ref_lp[np.isfinite(ref_lp)], rtol=1e-12, atol=1e-12)
+    finally:
+        m.mbis_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tiny_loglike_matches_oracle(m, torch, tiny, precision):
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64 if precision == "fp64" else m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        theta, _ = oracle.draw(spec.draw_seed, 0, w.n_samples, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+        logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], theta, th))
+        got = gpu_loglike(m, torch, ctx, theta)
+        dmax = compare_loglike(got, ref, logp)
+        if precision == "fp64":
+            assert dmax < 1e-8
+        # at the injection (zero noise): ln I0(rho^2) - rho^2 / 2
+        t0 = np.array([[th[i]] for i in prop["ids"]])
+        g0 = gpu_loglike(m, torch, ctx, t0)[0]
+        assert abs(g0 - (oracle.log_i0([225.0])[0] - 112.5)) < (1e-8 if precision == "fp64" else LOGL_TOL)
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def test_reduce_matches_oracle(m, torch, tiny):
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64)
+    try:
+        set_metric(m, ctx, prop)
+        n = w.n_samples
+        P = len(prop["ids"])
+        theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+        lq = torch.empty(n, dtype=torch.float64, device="cuda")
+        lp = torch.empty(n, dtype=torch.float64, device="cuda")
+        ll = torch.empty(n, dtype=torch.float64, device="cuda")
+        wts = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.mbis_draw(ctx, spec.draw_seed, 0, n, theta, lq, lp)
+        m.mbis_loglike(ctx, n, theta, ll)
+        s = m.mbis_reduce(ctx, n, ll, lp, lq, wts)
+        # oracle end to end on its own draws
+        ref_th, ref_lq = oracle.draw(spec.draw_seed, 0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+        ref_lp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], ref_th)
+        ref_ll = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], ref_th, th))
+        r = oracle.reduce(ref_ll, ref_lp, ref_lq, want_weights=True)
+        assert abs(s["ess"] / r["ess"] - 1) < 1e-3
+        assert abs(s["log_z"] - r["log_z"]) < 1e-3 * max(1.0, abs(r["log_z"]))
+        assert s["n"] == n
+        # the reduction alone on identical inputs
+        d_ll = torch.tensor(ref_ll, device="cuda")
+        d_lp = torch.tensor(ref_lp, device="cuda")
+        d_lq = torch.tensor(ref_lq, device="cuda")
+        s2 = m.mbis_reduce(ctx, n, d_ll, d_lp, d_lq, wts)
+        assert abs(s2["ess"] / r["ess"] - 1) < 1e-12
+        assert abs(s2["log_z"] - r["log_z"]) < 1e-12 * max(1.0, abs(r["log_z"]))
+        np.testing.assert_allclose(wts.cpu().numpy(), r["weights"], rtol=1e-12, atol=1e-300)
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def test_reduce_edge_cases_and_accumulation(m, torch, tiny):
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64)
+    try:
+        z = torch.zeros(0, dtype=torch.float64, device="cuda")
+        s = m.mbis_reduce(ctx, 0, z, z, z)
+        assert s["n"] == 0 and s["ess"] == 0 and s["all_zero"]
+        n = 1000
+        ninf = torch.full((n,), -math.inf, dtype=torch.float64, device="cuda")
+        zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s = m.mbis_reduce(ctx, n, ninf, zero, zero)
+        assert s["ess"] == 0 and s["log_z"] == -math.inf and s["all_zero"]
+        # merging batches equals one batch
+        rng = np.random.default_rng(2)
+        ll = rng.normal(10, 3, 5000)
+        lp = np.where(rng.uniform(size=5000) < 0.1, -np.inf, rng.normal(0, 1, 5000))
+        lq = rng.normal(0, 1, 5000)
+        T = lambda a: torch.tensor(a, device="cuda")
+        whole = m.mbis_reduce(ctx, 5000, T(ll), T(lp), T(lq))
+        m.mbis_reset_running(ctx)
+        for a, b in [(0, 1234), (1234, 4000), (4000, 5000)]:
+            part = m.mbis_reduce(ctx, b - a, T(ll[a:b]), T(lp[a:b]), T(lq[a:b]), accumulate=True)
+        assert part["n"] == 5000
+        assert abs(part["ess"] / whole["ess"] - 1) < 1e-12
+        assert abs(part["log_z"] - whole["log_z"]) < 1e-12
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def test_unphysical_samples_get_minus_infinity(m, torch, tiny):
+    w, spec, ev, th, prop = tiny
+    for prec in (m.FP64, m.MIXED):
+        ctx = gpu_context(m, ev, w, spec, th, prec)
+        try:
+            set_metric(m, ctx, prop)
+            t = np.array([[th[MC], -1.0, th[MC], th[MC]], [th[Q], 1.2, 0.0, 1.2], [0.1, 0.1, 0.1, 1.5],
+                          [0.0, 0.0, 0.0, 0.0]])
+            got = gpu_loglike(m, torch, ctx, t)
+            assert np.isfinite(got[0]) and np.all(got[1:] == -np.inf)
+        finally:
+            m.mbis_destroy(ctx)
+
+
+# ------------------------------------------------------------------ BNS population, full grid
+@pytest.fixture(scope="module")
+def bns():
+    w = workloads.bns_population(n_events=2, n_samples=1 << 20)
+    spec = w.events[1]
+    ev, th, _ = make_event(w, spec)
+    to_fp32_data(ev)   # both sides see the complex64 / float32 data
+    prop = make_proposal(ev, w, th)
+    return w, spec, ev, th, prop
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_bns_full_grid_matches_oracle(m, torch, bns, precision):
+    w, spec, ev, th, prop = bns
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED if precision == "mixed" else m.FP64)
+    try:
+        set_metric(m, ctx, prop)
+        n = 48
+        theta, _ = oracle.draw(spec.draw_seed, 0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+        theta[:, 0] = [th[i] for i in prop["ids"]]       # include the injection
+        logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], theta, th))
+        got = gpu_loglike(m, torch, ctx, theta)
+        compare_loglike(got, ref, logp)
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def test_bns_full_size_launch_sampled_outputs(m, torch, bns):
+    """The benchmark's launch: 2^20 samples of one BNS event in one call; outputs at 24
+    sampled indices against the oracle, and all outputs finite or -inf where invalid."""
+    w, spec, ev, th, prop = bns
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        n = w.n_samples
+        P = len(prop["ids"])
+        theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+        lq = torch.empty(n, dtype=torch.float64, device="cuda")
+        lp = torch.empty(n, dtype=torch.float64, device="cuda")
+        ll = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.mbis_draw(ctx, spec.draw_seed, 0, n, theta, lq, lp)
+        m.mbis_loglike(ctx, n, theta, ll)
+        s = m.mbis_reduce(ctx, n, ll, lp, lq)
+        torch.cuda.synchronize()
+        llh = ll.cpu().numpy()
+        assert not np.any(np.isnan(llh))
+        idx = np.random.default_rng(7).choice(n, 24, replace=False)
+        idx[0] = n - 1
+        th_s = theta.cpu().numpy()[:, idx]
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], th_s, th))
+        compare_loglike(llh[idx], ref, oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], th_s))
+        assert s["ess"] > 100 and np.isfinite(s["log_z"])
+    finally:
+        m.mbis_destroy(ctx)

@@ -14,7 +14,7 @@ from scipy import special, integrate
 import oracle
 import workloads
 from workloads import MC, Q, CHI1, CHI2, RA, DEC, PSI, IOTA, DL, TC, PHIC
-from oracle_events import make_event
+from oracle.events import make_event
 
 
 def small_workload(marg, detectors=("H1", "L1"), f_hi=128.0, df=0.25, snr=15.0, noise_seed=None):
