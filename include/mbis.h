@@ -149,6 +149,24 @@ mbis_status mbis_reduce(mbis_ctx* ctx, int64_t n, const double* loglike, const d
                         const double* log_q, double* weights_out, int32_t accumulate, mbis_summary* out,
                         void* cuda_stream);
 
+/* mbis_reduce without a context and without any allocation.  The paper has no
+ * counterpart: this is for callers that must not call cudaMalloc once they run -- e.g. a
+ * low-latency loop in which an allocation would synchronise the device, or a host
+ * framework that owns all device memory and forbids allocations after start-up.  The
+ * caller passes the inputs (device, n each) and the outputs (weights_out: device n
+ * doubles or NULL; *out: host summary of this batch); the stream is synchronised.
+ * Scratch is a file-scope device array of the library (about 128 KiB on every GPU that
+ * loads it, kept until exit) with room for MBIS_NOALLOC_MAX_SAMPLES samples per call;
+ * larger n returns MBIS_E_INVALID with a message in mbis_last_error(NULL).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents; each call zeroes the part that must start
+ * at zero.  Calls that overlap on the GPU (other streams or threads) race on it.
+ * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+#define MBIS_NOALLOC_MAX_SAMPLES 16777216
+mbis_status mbis_reduce_noalloc(int64_t n, const double* loglike, const double* log_prior, const double* log_q,
+                                double* weights_out, mbis_summary* out, void* cuda_stream);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

@@ -76,6 +76,7 @@ def _load():
         "mbis_psd_aligo": [p, p],
         "mbis_inject": [p, i32, p, p, d, p, u64, i32, p, p],
         "mbis_fisher": [p, p, i32, p, p, p],
+        "mbis_reduce_noalloc": [i64, p, p, p, p, p, p],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -181,6 +182,17 @@ def mbis_reduce(ctx, n, loglike, log_prior, log_q, weights_out=None, accumulate=
     out = Summary()
     _check(_lib.mbis_reduce(ctx, n, _dev(loglike), _dev(log_prior), _dev(log_q), _dev(weights_out), int(accumulate),
                             C.byref(out), _stream(stream)), ctx)
+    return out.as_dict()
+
+
+NOALLOC_MAX_SAMPLES = 16777216
+
+
+def mbis_reduce_noalloc(n, loglike, log_prior, log_q, weights_out=None, stream=None):
+    """The reduction without a context or any allocation (see include/mbis.h)."""
+    out = Summary()
+    _check(_lib.mbis_reduce_noalloc(n, _dev(loglike), _dev(log_prior), _dev(log_q), _dev(weights_out), C.byref(out),
+                                    _stream(stream)))
     return out.as_dict()
 
 

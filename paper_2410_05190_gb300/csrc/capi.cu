@@ -182,6 +182,11 @@ __global__ void central_diff_kernel(int32_t P, const double2* h, const double* s
 
 }  // namespace
 
+namespace mbis {
+// message for mbis_last_error(NULL) from entry points defined in other files
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace mbis
+
 extern "C" {
 
 const char* mbis_version(void) { return "mbis 0.1 (sm_103a)"; }

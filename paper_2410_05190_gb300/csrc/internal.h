@@ -125,6 +125,8 @@ struct PlanInput {
 };
 std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in);
 
+void set_last_error(const std::string& msg);
+
 }  // namespace mbis
 
 // the context behind the opaque handle
