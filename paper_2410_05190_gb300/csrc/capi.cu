@@ -132,7 +132,7 @@ mbis_status build_tables(mbis_ctx* c) {
       cudaFree(d_max);
       c->cscale = (mx > 0.0 && std::isfinite(mx)) ? std::ldexp(1.0, std::ilogb(mx) + 1) : 1.0;
       const int32_t n_pad = (n + kChunk - 1) / kChunk * kChunk;
-      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float2) * n_pad));
+      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float4) * (n_pad / 2)));
       CU_TRY(c, launch_to_f32(c->d_cfold64, n, n_pad, 1.0 / c->cscale, c->d_cfold32, s));
       PlanInput pin;
       pin.f_lo = c->f_lo;
@@ -374,7 +374,11 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
   a.theta = theta;
   a.out = loglike;
   a.P = c->P;
-  for (int p = 0; p < c->P; ++p) a.ids[p] = c->ids[p];
+  for (int s = 0; s < kNumSlots; ++s) a.pos[s] = -1;
+  for (int p = 0; p < c->P; ++p) {
+    a.ids[p] = c->ids[p];
+    a.pos[c->ids[p]] = (int8_t)p;
+  }
   std::memcpy(a.fixed, c->fixed, sizeof(a.fixed));
   a.marg = c->opts.marg;
   a.dmin = c->opts.dmin_mpc;

@@ -41,6 +41,7 @@ struct LikeArgs {
   double* out;          // [n]
   int32_t P;
   int32_t ids[kMaxP];
+  int8_t pos[kNumSlots];      // row of slot s in theta, or -1 when the slot is fixed
   double fixed[kNumSlots];
   uint32_t marg;
   double dmin, dmax;
@@ -58,7 +59,7 @@ struct LikeArgs {
   double det_vertex[kMaxDet][3], det_x[kMaxDet][3], det_y[kMaxDet][3];
   double gmst;
   // mixed tables
-  const float2* cfold32;      // [padded n_bins], scaled by 1 / cscale
+  const float4* cfold32;      // [n_pad / 2] bin pairs (re_k, re_k+1, im_k, im_k+1), scaled by 1 / cscale
   double cscale;
   const AnchorBlock* plan;
   int32_t n_blocks;
@@ -90,7 +91,7 @@ cudaError_t launch_event_tables(int32_t n_det, int32_t n_bins, double f_lo, doub
                                 double2* c_out, double* w_out, cudaStream_t s);
 cudaError_t launch_prefix_rows(const double* w, int32_t rows, int32_t n, double* T, cudaStream_t s);
 cudaError_t launch_max_abs(const double2* c, int32_t n, double* out, cudaStream_t s);
-cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float2* out, cudaStream_t s);
+cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float4* out, cudaStream_t s);
 cudaError_t launch_draw(const DrawArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_fp64(const LikeArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s);
@@ -154,7 +155,7 @@ struct mbis_ctx {
   double* d_tfold = nullptr;
   double2* d_cdet64 = nullptr;
   double* d_tdet = nullptr;
-  float2* d_cfold32 = nullptr;
+  float4* d_cfold32 = nullptr;
   double cscale = 1.0;
   mbis::AnchorBlock* d_plan = nullptr;
   int32_t n_blocks = 0;

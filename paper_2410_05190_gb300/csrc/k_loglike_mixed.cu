@@ -3,18 +3,21 @@
 // waveform h(f) is never written to memory.
 //
 // One thread per proposal sample, 128 samples per CTA.  The folded data table C_k (FP32,
-// detectors and their fixed responses folded in) streams through shared memory in chunks
-// of 512 bins by TMA bulk copies (cp.async.bulk + mbarrier, two buffers); every thread of
-// the CTA reads the same bin at the same time (shared-memory broadcast).
+// detectors and their fixed responses folded in, stored as bin pairs
+// (re_k, re_k+1, im_k, im_k+1)) streams through shared memory in chunks of 512 bins by TMA
+// bulk copies (cp.async.bulk + mbarrier, two buffers); every thread of the CTA reads the
+// same pair at the same time (one LDS.128 broadcast per two bins).
 //
 // Phase per bin (anchor blocks, see plan.cpp): at the start of a block each thread forms,
 // in FP64, the linear phase X + (k - kc) Y, reduces it modulo one turn and keeps it as a
 // 32-bit fixed-point turn count (exact wrap-around on integer add), and forms in FP32 the
 // coefficients of the degree-5 remainder polynomial.  The FP64 rounding residuals of the
-// fixed-point value and slope are folded into that polynomial.  Per bin: one integer add,
-// a 5-FMA Horner step, the fixed-point -> float conversion through the mantissa, one FMA
-// to radians, MUFU sin/cos, and a complex FMA with C_k.  Per-chunk FP32 partial sums are
-// accumulated in FP64.
+// fixed-point value and slope are folded into that polynomial.  Bins are taken in pairs
+// with packed FP32x2 arithmetic: a 5-step Horner on both bins, the fixed-point -> float
+// conversion through the mantissa, one FMA to radians, MUFU sine and cosine per bin, and
+// a complex multiply-accumulate with C_k.  Per-chunk FP32 partial sums are accumulated in
+// FP64.  The per-sample FP64 phase coefficients wait in shared memory between blocks so
+// the loop keeps few registers (two CTAs more per SM).
 #include "internal.h"
 #include "marg.cuh"
 
@@ -71,21 +74,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 struct BlockState {
   uint32_t acc, step;
-  float c0, c1, c2, c3, c4, c5;
+  float c[kRemDeg + 1];
   float w;
-  int32_t end;
 };
 
-__device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan, int blk, const PhaseCoeffs& pc,
+// Enter anchor block blk: FP64 linear phase -> fixed point, FP32 remainder coefficients.
+// pc / cf are this thread's coefficient columns in shared memory (stride kMixedThreads).
+__device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan, int blk, const double* pc,
                                             const float* cf, BlockState& st) {
   const AnchorBlock& B = plan[blk];
-  double x = pc.cst, y = 0.0;
+  double x = pc[kNumBasis * kMixedThreads], y = 0.0;  // cst
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
-    x = fma(pc.C[j], B.B[j], x);
-    y = fma(pc.C[j], B.dB[j], y);
+    const double Cj = pc[j * kMixedThreads];
+    x = fma(Cj, B.B[j], x);
+    y = fma(Cj, B.dB[j], y);
   }
   const double w0 = (double)(B.k0 - B.kc);
   const double ph0 = fma(w0, y, x);  // linear phase at the first bin of the block, turns
@@ -97,59 +104,63 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   // +256: round rather than truncate when the top 23 bits become the float mantissa
   st.acc = (uint32_t)p0 + 256u;
   st.step = (uint32_t)p1;
-  float c[kRemDeg + 1];
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j], B.E[j][m], s);
-    c[m] = s;
+    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j * kMixedThreads], B.E[j][m], s);
+    st.c[m] = s;
   }
-  c[0] += (float)(r0 - w0 * r1);
-  c[1] += (float)r1;
+  st.c[0] += (float)(r0 - w0 * r1);
+  st.c[1] += (float)r1;
   // angle = 2 pi (acc / 2^32) + 2 pi R = 2 pi f1 + (2 pi R - 2 pi), f1 = 1 + acc / 2^32
-  st.c0 = kTwoPiF * c[0] - kTwoPiF;
-  st.c1 = kTwoPiF * c[1];
-  st.c2 = kTwoPiF * c[2];
-  st.c3 = kTwoPiF * c[3];
-  st.c4 = kTwoPiF * c[4];
-  st.c5 = kTwoPiF * c[5];
-  st.w = (float)(B.k0 - B.kc);
-  st.end = B.k1;
+#pragma unroll
+  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  st.c[0] -= kTwoPiF;
+  st.w = (float)w0;
 }
 
-__global__ void __launch_bounds__(kMixedThreads, 4) loglike_mixed_fold_kernel(LikeArgs a) {
-  __shared__ __align__(128) float2 sC[kNbuf][kChunk];
+__device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
+
+__global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
+  __shared__ __align__(128) float4 sC[kNbuf][kChunk / 2];
   __shared__ __align__(8) uint64_t bar[kNbuf];
+  __shared__ double sPC[(kNumBasis + 1) * kMixedThreads];  // C_j and cst per thread
+  __shared__ float sCF[(kNumBasis - 1) * kMixedThreads];   // FP32 copies of C_0..C_7
   __shared__ int s_kmax;
   const int tid = threadIdx.x;
   const int64_t s = (int64_t)blockIdx.x * kMixedThreads + tid;
   const bool active = s < a.n;
 
+  // ---- per-sample set-up (FP64)
   double par[kNumSlots];
 #pragma unroll
-  for (int i = 0; i < kNumSlots; ++i) par[i] = a.fixed[i];
-  if (active)
-    for (int p = 0; p < a.P; ++p) par[a.ids[p]] = a.theta[(int64_t)p * a.n + s];
+  for (int i = 0; i < kNumSlots; ++i) par[i] = (active && a.pos[i] >= 0) ? a.theta[(int64_t)a.pos[i] * a.n + s] : a.fixed[i];
   if (a.marg & MBIS_MARG_PHASE) par[kPhic] = 0.0;
   if (a.marg & MBIS_MARG_DISTANCE) par[kDl] = 1.0;
   const bool valid = active && par[kMc] > 0.0 && par[kQ] > 0.0 && fabs(par[kChi1]) < 1.0 &&
                      fabs(par[kChi2]) < 1.0 && par[kDl] > 0.0 && isfinite(par[kTc]) && isfinite(par[kPhic]);
-  PhaseCoeffs pc;
   int32_t kcut = 0;
   double A = 0.0;
-  if (valid) {
-    pc = phase_coeffs(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic]);
-    kcut = live_bins(par[kMc], par[kQ], a.f_lo, a.df, a.n_bins);
-    A = amplitude(par[kMc], par[kDl]);
-  } else {
+  {
+    PhaseCoeffs pc;
+    if (valid) {
+      pc = phase_coeffs(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic]);
+      kcut = live_bins(par[kMc], par[kQ], a.f_lo, a.df, a.n_bins);
+      A = amplitude(par[kMc], par[kDl]);
+    } else {
 #pragma unroll
-    for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
-    pc.cst = 0.0;
+      for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
+      pc.cst = 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kNumBasis; ++j) sPC[j * kMixedThreads + tid] = pc.C[j];
+    sPC[kNumBasis * kMixedThreads + tid] = pc.cst;
+#pragma unroll
+    for (int j = 0; j < kNumBasis - 1; ++j) sCF[j * kMixedThreads + tid] = (float)pc.C[j];
   }
-  float cf[kNumBasis - 1];
-#pragma unroll
-  for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = (float)pc.C[j];
+  const double* my_pc = sPC + tid;
+  const float* my_cf = sCF + tid;
 
   if (tid == 0) {
     s_kmax = 0;
@@ -166,14 +177,15 @@ __global__ void __launch_bounds__(kMixedThreads, 4) loglike_mixed_fold_kernel(Li
   if (tid == 0) {
     for (int b = 0; b < kNbuf && b < nch; ++b) {
       mbar_expect_tx(&bar[b], kBytes);
-      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)b * kChunk, kBytes, &bar[b]);
+      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)b * (kChunk / 2), kBytes, &bar[b]);
       ++issued[b];
     }
   }
 
+  // ---- sweep over frequency
   double Zr = 0.0, Zi = 0.0;
   BlockState st;
-  st.end = 0;
+  int32_t blk_end = 0;
   int blk = -1;
   bool timed_out = false;
   for (int32_t ch = 0; ch < nch; ++ch) {
@@ -183,47 +195,74 @@ __global__ void __launch_bounds__(kMixedThreads, 4) loglike_mixed_fold_kernel(Li
       timed_out = true;
       break;
     }
-    const float2* __restrict__ cb = sC[b];
+    const float4* __restrict__ cb = sC[b];
     const int32_t kb = ch * kChunk, ke = min(kb + kChunk, kmax);
-    float zr = 0.f, zi = 0.f;
+    float2 zr = f2(0.f), zi = f2(0.f), zn = f2(0.f);  // zn accumulates re(C) sin, subtracted at the end
     int32_t k = kb;
     while (k < ke) {
-      if (k == st.end) {
+      if (k == blk_end) {
         ++blk;
-        if (k < kcut) enter_block(a.plan, blk, pc, cf, st);
-        st.end = a.plan[blk].k1;
+        if (k < kcut) enter_block(a.plan, blk, my_pc, my_cf, st);
+        blk_end = a.plan[blk].k1;
       }
-      const int32_t seg_end = min(ke, st.end);
+      const int32_t seg_end = min(ke, blk_end);
       const int32_t my_end = min(seg_end, kcut);
-      uint32_t acc = st.acc;
-      float w = st.w;
-      const uint32_t step = st.step;
-      const float c0 = st.c0, c1 = st.c1, c2 = st.c2, c3 = st.c3, c4 = st.c4, c5 = st.c5;
-#pragma unroll 4
-      for (int32_t kk = k; kk < my_end; ++kk) {
-        const float R = fmaf(fmaf(fmaf(fmaf(fmaf(c5, w, c4), w, c3), w, c2), w, c1), w, c0);
-        const float f1 = __uint_as_float((acc >> 9) | 0x3f800000u);
-        const float ang = fmaf(f1, kTwoPiF, R);
-        float sn, cs;
-        __sincosf(ang, &sn, &cs);
-        const float2 c = cb[kk - kb];
-        zr = fmaf(c.x, cs, fmaf(c.y, sn, zr));
-        zi = fmaf(c.y, cs, fmaf(-c.x, sn, zi));
-        acc += step;
-        w += 1.0f;
+      if (k < my_end) {
+        const float2 c0 = f2(st.c[0]), c1 = f2(st.c[1]), c2 = f2(st.c[2]), c3 = f2(st.c[3]), c4 = f2(st.c[4]),
+                     c5 = f2(st.c[5]);
+        const float2 two = f2(2.0f), twopi = f2(kTwoPiF);
+        const uint32_t step = st.step, step2 = 2u * st.step;
+        uint32_t acc = st.acc;
+        float2 w = make_float2(st.w, st.w + 1.0f);
+        const int32_t npair = (my_end - k) >> 1;
+        const float4* cp = cb + ((k - kb) >> 1);
+#pragma unroll 2
+        for (int32_t p = 0; p < npair; ++p) {
+          float2 R = __ffma2_rn(c5, w, c4);
+          R = __ffma2_rn(R, w, c3);
+          R = __ffma2_rn(R, w, c2);
+          R = __ffma2_rn(R, w, c1);
+          R = __ffma2_rn(R, w, c0);
+          const float2 f1 = make_float2(mantissa_turn(acc), mantissa_turn(acc + step));
+          const float2 ang = __ffma2_rn(f1, twopi, R);
+          float2 sn, cs;
+          __sincosf(ang.x, &sn.x, &cs.x);
+          __sincosf(ang.y, &sn.y, &cs.y);
+          const float4 c = cp[p];
+          const float2 cre = make_float2(c.x, c.y), cim = make_float2(c.z, c.w);
+          zr = __ffma2_rn(cre, cs, __ffma2_rn(cim, sn, zr));
+          zi = __ffma2_rn(cim, cs, zi);
+          zn = __ffma2_rn(cre, sn, zn);
+          acc += step2;
+          w = __fadd2_rn(w, two);
+        }
+        int32_t kk = k + 2 * npair;
+        if (kk < my_end) {  // one bin left (odd cut): the even half of the pair
+          const float R = fmaf(fmaf(fmaf(fmaf(fmaf(st.c[5], w.x, st.c[4]), w.x, st.c[3]), w.x, st.c[2]), w.x, st.c[1]),
+                               w.x, st.c[0]);
+          const float ang = fmaf(mantissa_turn(acc), kTwoPiF, R);
+          float sn, cs;
+          __sincosf(ang, &sn, &cs);
+          const float4 c = cp[npair];
+          zr.x = fmaf(c.x, cs, fmaf(c.z, sn, zr.x));
+          zi.x = fmaf(c.z, cs, zi.x);
+          zn.x = fmaf(c.x, sn, zn.x);
+          acc += step;
+          w.x += 1.0f;
+          ++kk;
+        }
+        st.acc = acc;
+        st.w = w.x;
       }
-      // the state now stands at my_end; threads past their cut never use it again
-      st.acc = acc;
-      st.w = w;
       k = seg_end;
     }
-    Zr += (double)zr;
-    Zi += (double)zi;
+    Zr += (double)zr.x + (double)zr.y;
+    Zi += ((double)zi.x + (double)zi.y) - ((double)zn.x + (double)zn.y);
     __syncthreads();  // every thread is done with buffer b
     if (tid == 0 && ch + kNbuf < nch) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar[b], kBytes);
-      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)(ch + kNbuf) * kChunk, kBytes, &bar[b]);
+      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)(ch + kNbuf) * (kChunk / 2), kBytes, &bar[b]);
       ++issued[b];
     }
   }
@@ -243,6 +282,7 @@ __global__ void __launch_bounds__(kMixedThreads, 4) loglike_mixed_fold_kernel(Li
     a.out[s] = -INFINITY;
     return;
   }
+  // ---- marginalisation (Sec. III)
   const double zr = A * a.cscale * Zr, zi = A * a.cscale * Zi;
   const double H = A * A * a.tfold[kcut];
   double ll;
@@ -251,7 +291,7 @@ __global__ void __launch_bounds__(kMixedThreads, 4) loglike_mixed_fold_kernel(Li
   } else if (a.marg == MBIS_MARG_PHASE) {
     ll = log_i0(hypot(zr, zi)) - 0.5 * H;
   } else {
-    ll = log_distance_marginal(hypot(zr, zi), H, a.dmin, a.dmax, a.gl);
+    ll = log_distance_marginal_mixed(hypot(zr, zi), H, a.dmin, a.dmax, a.gl);
   }
   a.out[s] = ll;
 }

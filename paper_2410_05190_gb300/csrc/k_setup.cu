@@ -107,13 +107,15 @@ __global__ void max_abs_kernel(const double2* c, int32_t n, double* out) {
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
-__global__ void to_f32_kernel(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float2* out) {
-  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_pad) return;
-  if (k < n)
-    out[k] = make_float2((float)(c[k].x * inv_scale), (float)(c[k].y * inv_scale));
-  else
-    out[k] = make_float2(0.f, 0.f);
+// FP32 table in bin pairs: (re_k, re_k+1, im_k, im_k+1) for even k, zero past n
+__global__ void to_f32_kernel(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float4* out) {
+  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n_pad) return;
+  const int32_t k = 2 * p;
+  const double2 a = k < n ? c[k] : make_double2(0.0, 0.0);
+  const double2 b = k + 1 < n ? c[k + 1] : make_double2(0.0, 0.0);
+  out[p] = make_float4((float)(a.x * inv_scale), (float)(b.x * inv_scale), (float)(a.y * inv_scale),
+                       (float)(b.y * inv_scale));
 }
 
 }  // namespace
@@ -143,8 +145,8 @@ cudaError_t launch_max_abs(const double2* c, int32_t n, double* out, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float2* out, cudaStream_t s) {
-  to_f32_kernel<<<(n_pad + 255) / 256, 256, 0, s>>>(c, n, n_pad, inv_scale, out);
+cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv_scale, float4* out, cudaStream_t s) {
+  to_f32_kernel<<<(n_pad / 2 + 255) / 256, 256, 0, s>>>(c, n, n_pad, inv_scale, out);
   return cudaGetLastError();
 }
 

@@ -85,6 +85,83 @@ __device__ __forceinline__ double log_distance_marginal(double Z, double H, doub
   }
   return L.value();
 }
+
+// ln I0(x) - x in FP32 (x >= 0): slowly varying, so FP32 keeps its absolute accuracy
+__device__ __forceinline__ float log_i0_minus_x_f(float x) {
+  if (x < 15.0f) return logf(cyl_bessel_i0f(x)) - x;
+  const float t = 1.0f / (8.0f * x);
+  const float s = t * (1.0f + t * (4.5f + t * (37.5f + t * 459.375f)));
+  return -0.5f * logf(6.28318530717958647692f * x) + log1pf(s);
+}
+
+struct LogSumExpF {
+  float m = -INFINITY, acc = 0.0f;
+  __device__ __forceinline__ void add(float g, float w) {
+    if (g > m) {
+      acc = acc * __expf(m - g) + w;
+      m = g;
+    } else {
+      acc += w * __expf(g - m);
+    }
+  }
+};
+
+// The same quadrature as log_distance_marginal, with the nodes evaluated in FP32 as
+// differences G(s) - G(s_ref) from one FP64 evaluation at s_ref (the peak, or the
+// large-distance end when there is none).  The differences are formed from small
+// quantities (u - u_ref = u_ref expm1(s - s_ref)), so FP32 keeps ~1e-6 relative accuracy
+// on each weight and the result carries the FP64 accuracy of G(s_ref).
+__device__ __forceinline__ void dist_rule_f(LogSumExpF& L, double a, double b, int panels, int n, const double* x,
+                                            const double* w, float Z, float H, double s_ref, float u_ref,
+                                            float phi_ref) {
+  const double h = (b - a) / panels;
+  for (int p = 0; p < panels; ++p) {
+    const double mid = a + (p + 0.5) * h;
+    const float half = (float)(0.5 * h);
+    const float dmid = (float)(mid - s_ref);
+    for (int i = 0; i < n; ++i) {
+      const float d = fmaf(half, (float)x[i], dmid);  // s - s_ref
+      const float du = u_ref * expm1f(d);
+      const float u = u_ref + du;
+      const float g = Z * du - 0.5f * H * du * (2.0f * u_ref + du) - 3.0f * d + (log_i0_minus_x_f(Z * u) - phi_ref);
+      L.add(g, half * (float)w[i]);
+    }
+  }
+}
+
+__device__ __forceinline__ double log_distance_marginal_mixed(double Z, double H, double dmin, double dmax,
+                                                              const double* gl) {
+  const double* x48 = gl;
+  const double* w48 = gl + kGL48;
+  const double* x8 = gl + 2 * kGL48;
+  const double* w8 = gl + 2 * kGL48 + kGL8;
+  const double c0 = log(3.0 / (dmax * dmax * dmax - dmin * dmin * dmin));
+  const double s_lo = -log(dmax), s_hi = -log(dmin);
+  bool window = false;
+  double wlo = s_lo, whi = s_hi, s_ref = s_lo;
+  if (H > 0.0 && Z * Z > 14.0 * H) {
+    const double u = (Z + sqrt(Z * Z - 14.0 * H)) / (2.0 * H);
+    const double sig = 1.0 / sqrt(fmax(Z * u - 7.0, 1e-300));
+    const double sc = log(u);
+    wlo = fmax(s_lo, sc - 12.0 * sig);
+    whi = fmin(s_hi, sc + 12.0 * sig);
+    window = wlo < whi;
+    s_ref = fmin(fmax(sc, s_lo), s_hi);
+  }
+  const double u_ref = exp(s_ref);
+  const double g_ref = c0 - 3.0 * s_ref + log_i0(Z * u_ref) - 0.5 * H * u_ref * u_ref;
+  const float Zf = (float)Z, Hf = (float)H, uf = (float)u_ref;
+  const float phi_ref = log_i0_minus_x_f(Zf * uf);
+  LogSumExpF L;
+  if (window) {
+    dist_rule_f(L, wlo, whi, 1, kGL48, x48, w48, Zf, Hf, s_ref, uf, phi_ref);
+    if (wlo > s_lo) dist_rule_f(L, s_lo, wlo, 4, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
+    if (whi < s_hi) dist_rule_f(L, whi, s_hi, 4, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
+  } else {
+    dist_rule_f(L, s_lo, s_hi, 24, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
+  }
+  return g_ref + (double)L.m + log((double)L.acc);
+}
 #endif
 
 // host: Gauss-Legendre nodes by Newton iteration on the Legendre recurrence

@@ -117,6 +117,7 @@ std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
       return f.err_bound <= in.tol_turns && f.r_bound <= in.rmax_turns;
     };
     int32_t good = std::min<int32_t>(cap, 8);  // short blocks are interpolated exactly
+    if (good < remaining && (good & 1)) good -= 1;
     int32_t S = std::min(cap, std::max(good, guess));
     int32_t bad = -1;
     if (ok(S)) {
@@ -139,6 +140,8 @@ std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
         if (ok(m)) good = m; else bad = m;
       }
     }
+    // even sizes keep every block start even, so the kernel can take bins in pairs
+    if (good < remaining && good > 2) good &= ~1;
     blocks.push_back(fit_block(in, k0, good).blk);
     k0 += good;
     guess = good;
