@@ -61,6 +61,9 @@ void free_tables(mbis_ctx* c) {
   dfree(c->d_cdet64);
   dfree(c->d_tdet);
   dfree(c->d_cfold32);
+  dfree(c->d_twiddle);
+  dfree(c->d_cdet32);
+  dfree(c->d_ttiles);
   dfree(c->d_plan);
   c->n_blocks = 0;
   c->tables_mode = -1;
@@ -123,30 +126,6 @@ mbis_status build_tables(mbis_ctx* c) {
     CU_TRY(c, cudaMalloc(&d_w, sizeof(double) * n));
     CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 1, det, c->d_cfold64, d_w, s));
     CU_TRY(c, launch_prefix_rows(d_w, 1, n, c->d_tfold, s));
-    if (c->opts.precision == MBIS_MIXED) {
-      double* d_max = nullptr;
-      CU_TRY(c, cudaMalloc(&d_max, sizeof(double)));
-      CU_TRY(c, launch_max_abs(c->d_cfold64, n, d_max, s));
-      double mx = 0.0;
-      CU_TRY(c, cudaMemcpy(&mx, d_max, sizeof(double), cudaMemcpyDeviceToHost));
-      cudaFree(d_max);
-      c->cscale = (mx > 0.0 && std::isfinite(mx)) ? std::ldexp(1.0, std::ilogb(mx) + 1) : 1.0;
-      const int32_t n_pad = (n + kChunk - 1) / kChunk * kChunk;
-      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float4) * (n_pad / 2)));
-      CU_TRY(c, launch_to_f32(c->d_cfold64, n, n_pad, 1.0 / c->cscale, c->d_cfold32, s));
-      PlanInput pin;
-      pin.f_lo = c->f_lo;
-      pin.df = c->df;
-      pin.n_bins = n;
-      coefficient_bounds(c, pin.cmax);
-      pin.tol_turns = 2e-8;
-      pin.rmax_turns = 1.0;
-      pin.max_block = 4096;
-      const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
-      c->n_blocks = (int32_t)plan.size();
-      CU_TRY(c, cudaMalloc(&c->d_plan, sizeof(AnchorBlock) * plan.size()));
-      CU_TRY(c, cudaMemcpy(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice));
-    }
   } else {
     CU_TRY(c, cudaMalloc(&c->d_cdet64, sizeof(double2) * (size_t)n * nd));
     CU_TRY(c, cudaMalloc(&c->d_tdet, sizeof(double) * (size_t)(n + 1) * nd));
@@ -154,6 +133,48 @@ mbis_status build_tables(mbis_ctx* c) {
     CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 0, nullptr, c->d_cdet64,
                                   d_w, s));
     CU_TRY(c, launch_prefix_rows(d_w, nd, n, c->d_tdet, s));
+  }
+  if (c->opts.precision == MBIS_MIXED) {
+    // FP32 copies are scaled by a power of two near the largest magnitude
+    const double2* src = fold ? c->d_cfold64 : c->d_cdet64;
+    const int32_t rows = fold ? 1 : nd;
+    double* d_max = nullptr;
+    CU_TRY(c, cudaMalloc(&d_max, sizeof(double)));
+    CU_TRY(c, launch_max_abs(src, n * rows, d_max, s));
+    double mx = 0.0;
+    CU_TRY(c, cudaMemcpy(&mx, d_max, sizeof(double), cudaMemcpyDeviceToHost));
+    cudaFree(d_max);
+    c->cscale = (mx > 0.0 && std::isfinite(mx)) ? std::ldexp(1.0, std::ilogb(mx) + 1) : 1.0;
+    if (c->opts.marg & MBIS_MARG_TIME) {
+      c->n_pad16 = (n + kKBlockBins - 1) / kKBlockBins * kKBlockBins;
+      c->n_kb = c->n_pad16 / kKBlockBins;
+      CU_TRY(c, cudaMalloc(&c->d_cdet32, sizeof(float2) * (size_t)c->n_pad16 * rows));
+      CU_TRY(c, launch_rows_to_f32(src, rows, n, c->n_pad16, 1.0 / c->cscale, c->d_cdet32, s));
+      if (c->opts.n_tshift == kTimeShifts) {
+        CU_TRY(c, cudaMalloc(&c->d_ttiles, sizeof(float) * (size_t)c->n_kb * 2 * 4096));
+        CU_TRY(c, launch_twiddle_tiles(n, c->f_lo, c->df, c->opts.dt_shift, c->n_kb, c->d_ttiles, s));
+      }
+    } else if (fold) {
+      const int32_t n_pad = (n + kChunk - 1) / kChunk * kChunk;
+      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float4) * (n_pad / 2)));
+      CU_TRY(c, launch_to_f32(c->d_cfold64, n, n_pad, 1.0 / c->cscale, c->d_cfold32, s));
+    }
+    PlanInput pin;
+    pin.f_lo = c->f_lo;
+    pin.df = c->df;
+    pin.n_bins = n;
+    coefficient_bounds(c, pin.cmax);
+    pin.tol_turns = 2e-8;
+    pin.rmax_turns = 1.0;
+    pin.max_block = 4096;
+    const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
+    c->n_blocks = (int32_t)plan.size();
+    CU_TRY(c, cudaMalloc(&c->d_plan, sizeof(AnchorBlock) * plan.size()));
+    CU_TRY(c, cudaMemcpy(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice));
+  }
+  if ((c->opts.marg & MBIS_MARG_TIME) && c->opts.precision == MBIS_FP64) {
+    CU_TRY(c, cudaMalloc(&c->d_twiddle, sizeof(double2) * (size_t)n * c->opts.n_tshift));
+    CU_TRY(c, launch_twiddles(n, c->f_lo, c->df, c->opts.n_tshift, c->opts.dt_shift, c->d_twiddle, s));
   }
   CU_TRY(c, cudaDeviceSynchronize());
   cudaFree(d_w);
@@ -209,8 +230,8 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
     return fail(nullptr, MBIS_E_INVALID, "mbis_create: marg must be 0, PHASE, PHASE|DISTANCE or TIME");
   if ((mg & MBIS_MARG_DISTANCE) && !(opts->dmin_mpc > 0.0 && opts->dmax_mpc > opts->dmin_mpc))
     return fail(nullptr, MBIS_E_INVALID, "mbis_create: distance range needs 0 < dmin < dmax");
-  if ((mg & MBIS_MARG_TIME) && !(opts->n_tshift >= 1 && opts->dt_shift > 0.0))
-    return fail(nullptr, MBIS_E_INVALID, "mbis_create: time grid needs n_tshift >= 1 and dt_shift > 0");
+  if ((mg & MBIS_MARG_TIME) && !(opts->n_tshift >= 1 && opts->n_tshift <= 256 && opts->dt_shift > 0.0))
+    return fail(nullptr, MBIS_E_INVALID, "mbis_create: time grid needs 1 <= n_tshift <= 256 and dt_shift > 0");
 
   mbis_ctx* c = new (std::nothrow) mbis_ctx();
   if (!c) return fail(nullptr, MBIS_E_OOM, "mbis_create: host allocation failed");
@@ -367,8 +388,8 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
   if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_loglike: null context");
   if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_loglike: call mbis_set_metric first");
   if (n < 0 || (n > 0 && (!theta || !loglike))) return fail(c, MBIS_E_INVALID, "mbis_loglike: bad n or null buffer");
-  if (c->opts.marg & MBIS_MARG_TIME)
-    return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: time marginalisation is not available in this build");
+  if ((c->opts.marg & MBIS_MARG_TIME) && c->opts.precision == MBIS_MIXED && c->d_ttiles == nullptr)
+    return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: mixed-precision time marginalisation needs n_tshift = 128");
   LikeArgs a = {};
   a.n = n;
   a.theta = theta;
@@ -402,18 +423,26 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
       a.det_y[d][i] = c->dets[d].yarm[i];
     }
   a.gmst = c->gmst;
+  a.twiddle = c->d_twiddle;
   a.cfold32 = c->d_cfold32;
   a.cscale = c->cscale;
   a.plan = c->d_plan;
   a.n_blocks = c->n_blocks;
+  a.cdet32 = c->d_cdet32;
+  a.n_pad16 = c->n_pad16;
+  a.ttiles = c->d_ttiles;
+  a.n_kb = c->n_kb;
   a.err = c->d_err;
   a.gl = c->d_gl;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (c->opts.precision == MBIS_FP64) {
     CU_TRY(c, launch_loglike_fp64(a, s));
+  } else if (c->opts.marg & MBIS_MARG_TIME) {
+    CU_TRY(c, launch_loglike_mixed_time(a, s));
   } else {
     if (!a.fold)
-      return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: mixed precision with sampled sky/orientation not available");
+      return fail(c, MBIS_E_UNSUPPORTED,
+                  "mbis_loglike: mixed precision with sampled sky/orientation needs MBIS_MARG_TIME");
     CU_TRY(c, launch_loglike_mixed(a, s));
   }
   return MBIS_OK;

@@ -58,11 +58,16 @@ struct LikeArgs {
   const double* tdet;         // [n_det][n_bins + 1]
   double det_vertex[kMaxDet][3], det_x[kMaxDet][3], det_y[kMaxDet][3];
   double gmst;
+  const double2* twiddle;     // TIME: [n_bins][n_tshift] (cos, sin) of 2 pi f_k tau_j
   // mixed tables
   const float4* cfold32;      // [n_pad / 2] bin pairs (re_k, re_k+1, im_k, im_k+1), scaled by 1 / cscale
   double cscale;
   const AnchorBlock* plan;
   int32_t n_blocks;
+  const float2* cdet32;       // TIME, mixed: [n_rows][n_pad16] per-detector (or folded) tables / cscale
+  int32_t n_pad16;            // row length of cdet32 (multiple of 16)
+  const float* ttiles;        // TIME, mixed: [n_kb][2][4096] swizzled twiddle head / tail tiles
+  int32_t n_kb;               // K-blocks of 16 bins covering n_bins
   int32_t* err;               // device error word (timeouts)
   const double* gl;           // Gauss-Legendre nodes / weights (marg.cuh layout)
 };
@@ -86,6 +91,15 @@ struct DrawArgs {
 
 // kernel launchers (each returns cudaGetLastError() of its launch)
 cudaError_t launch_basis_table(double f_lo, double df, int32_t n, double* out, cudaStream_t s);
+cudaError_t launch_twiddles(int32_t n, double f_lo, double df, int32_t J, double dt, double2* out, cudaStream_t s);
+cudaError_t launch_rows_to_f32(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
+                               float2* out, cudaStream_t s);
+cudaError_t launch_twiddle_tiles(int32_t n, double f_lo, double df, double dt, int32_t n_kb, float* out,
+                                 cudaStream_t s);
+cudaError_t launch_loglike_mixed_time(const LikeArgs& a, cudaStream_t s);
+
+constexpr int kTimeShifts = 128;  // shifts of the tensor-core time marginalisation (MMA N)
+constexpr int kKBlockBins = 16;   // bins per K-block of the time-shift contraction
 cudaError_t launch_event_tables(int32_t n_det, int32_t n_bins, double f_lo, double df, int32_t dtype,
                                 const void* strain, const double* psd, int32_t fold, const DetResponse* det,
                                 double2* c_out, double* w_out, cudaStream_t s);
@@ -156,6 +170,10 @@ struct mbis_ctx {
   double2* d_cdet64 = nullptr;
   double* d_tdet = nullptr;
   float4* d_cfold32 = nullptr;
+  double2* d_twiddle = nullptr;  // TIME marginalisation, FP64
+  float2* d_cdet32 = nullptr;    // TIME marginalisation, mixed: FP32 tables
+  float* d_ttiles = nullptr;     // TIME marginalisation, mixed: twiddle tiles
+  int32_t n_pad16 = 0, n_kb = 0;
   double cscale = 1.0;
   mbis::AnchorBlock* d_plan = nullptr;
   int32_t n_blocks = 0;

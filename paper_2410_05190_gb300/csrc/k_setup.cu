@@ -118,7 +118,79 @@ __global__ void to_f32_kernel(const double2* c, int32_t n, int32_t n_pad, double
                        (float)(b.y * inv_scale));
 }
 
+// e^(-2 pi i f_k tau_j) as (cos, sin) of 2 pi f_k tau_j, tau_j = (j - J/2) dt: [n][J]
+__global__ void twiddle_kernel(int32_t n, double f_lo, double df, int32_t J, double dt, double2* out) {
+  const int32_t k = blockIdx.x;
+  for (int32_t j = threadIdx.x; j < J; j += blockDim.x) {
+    const double f = f_lo + (double)k * df, tau = (double)(j - J / 2) * dt;
+    double s, c;
+    sincospi(2.0 * f * tau, &s, &c);
+    out[(int64_t)k * J + j] = make_double2(c, s);
+  }
+}
+
+// per-detector FP32 tables, scaled, zero-padded to n_pad: [rows][n_pad]
+__global__ void rows_to_f32_kernel(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
+                                   float2* out) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t r = blockIdx.y;
+  if (k >= n_pad || r >= rows) return;
+  const double2 v = k < n ? c[(int64_t)r * n + k] : make_double2(0.0, 0.0);
+  out[(int64_t)r * n_pad + k] = make_float2((float)(v.x * inv_scale), (float)(v.y * inv_scale));
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+// Twiddle operand of the time-shift contraction, one 16-bin K-block per CTA, one shift per
+// thread: row j holds (cos, sin)(2 pi f_k tau_j) for the block's 16 bins, split into a TF32
+// head and an FP32 tail, each in the 128-byte-swizzled K-major layout that the tensor core
+// reads (16-byte chunk c of row j at byte j*128 + ((c ^ (j & 7)) << 4)).
+// out: [n_kb][2 (head, tail)][128 rows x 128 bytes].
+__global__ void twiddle_tiles_kernel(int32_t n, double f_lo, double df, double dt, int32_t n_kb, float* out) {
+  const int32_t kb = blockIdx.x, j = threadIdx.x;
+  if (kb >= n_kb || j >= 128) return;
+  const double tau = (double)(j - 64) * dt;
+  float* head = out + (int64_t)kb * 2 * 4096;
+  float* tail = head + 4096;
+  for (int kk = 0; kk < 16; ++kk) {
+    const int32_t k = 16 * kb + kk;
+    double s = 0.0, c = 0.0;
+    if (k < n) sincospi(2.0 * (f_lo + (double)k * df) * tau, &s, &c);
+    const float v[2] = {(float)c, (float)s};
+    for (int e = 0; e < 2; ++e) {
+      const int kidx = 2 * kk + e;  // K index inside the block
+      const int chunk = kidx >> 2, pos = kidx & 3;
+      const int word = j * 32 + (((chunk ^ (j & 7)) << 2) | pos);
+      const float h = tf32_round(v[e]);
+      head[word] = h;
+      tail[word] = v[e] - h;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rows_to_f32(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
+                               float2* out, cudaStream_t s) {
+  dim3 grid((n_pad + 255) / 256, rows);
+  rows_to_f32_kernel<<<grid, 256, 0, s>>>(c, rows, n, n_pad, inv_scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle_tiles(int32_t n, double f_lo, double df, double dt, int32_t n_kb, float* out,
+                                 cudaStream_t s) {
+  twiddle_tiles_kernel<<<n_kb, 128, 0, s>>>(n, f_lo, df, dt, n_kb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles(int32_t n, double f_lo, double df, int32_t J, double dt, double2* out, cudaStream_t s) {
+  twiddle_kernel<<<n, 128, 0, s>>>(n, f_lo, df, J, dt, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_basis_table(double f_lo, double df, int32_t n, double* out, cudaStream_t s) {
   basis_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(f_lo, df, n, out);
@@ -129,7 +201,8 @@ cudaError_t launch_event_tables(int32_t n_det, int32_t n_bins, double f_lo, doub
                                 const void* strain, const double* psd, int32_t fold, const DetResponse* det,
                                 double2* c_out, double* w_out, cudaStream_t s) {
   DetPack p = {};
-  for (int d = 0; d < n_det && d < kMaxDet; ++d) p.d[d] = det[d];
+  if (det != nullptr)  // the per-detector tables (fold = 0) take no responses
+    for (int d = 0; d < n_det && d < kMaxDet; ++d) p.d[d] = det[d];
   event_tables_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(n_det, n_bins, f_lo, df, dtype, strain, psd, fold, p,
                                                             c_out, w_out);
   return cudaGetLastError();

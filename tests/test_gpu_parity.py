@@ -259,3 +259,48 @@ def test_bns_full_size_launch_sampled_outputs(m, torch, bns):
         assert s["ess"] > 100 and np.isfinite(s["log_z"])
     finally:
         m.mbis_destroy(ctx)
+
+
+# ------------------------------------------------- BBH with full extrinsics, time marginalised
+@pytest.fixture(scope="module")
+def bbh():
+    w = workloads.bbh_population(n_events=2, n_samples=1 << 12)
+    spec = w.events[0]
+    ev, th, _ = make_event(w, spec)
+    to_fp32_data(ev)
+    prop = make_proposal(ev, w, th)
+    return w, spec, ev, th, prop
+
+
+def test_bbh_time_marginalised_fp64_matches_oracle(m, torch, bbh):
+    w, spec, ev, th, prop = bbh
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64)
+    try:
+        set_metric(m, ctx, prop)
+        n = 33   # ragged: one warp per sample
+        theta, _ = oracle.draw(spec.draw_seed, 0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+        theta[:, 0] = [th[i] for i in prop["ids"]]
+        logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], theta, th))
+        got = gpu_loglike(m, torch, ctx, theta)
+        assert compare_loglike(got, ref, logp) < 1e-6
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def test_bbh_time_marginalised_tensor_core_matches_oracle(m, torch, bbh):
+    """The tcgen05 time-shift contraction (split TF32, FP32 accumulation in TMEM) against
+    the oracle; 300 samples = one full CTA of 256 and a ragged second one."""
+    w, spec, ev, th, prop = bbh
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        n = 300
+        theta, _ = oracle.draw(spec.draw_seed, 0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+        theta[:, 0] = [th[i] for i in prop["ids"]]
+        logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], theta, th))
+        got = gpu_loglike(m, torch, ctx, theta)
+        compare_loglike(got, ref, logp)
+    finally:
+        m.mbis_destroy(ctx)
