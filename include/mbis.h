@@ -167,6 +167,85 @@ mbis_status mbis_reduce(mbis_ctx* ctx, int64_t n, const double* loglike, const d
 mbis_status mbis_reduce_noalloc(int64_t n, const double* loglike, const double* log_prior, const double* log_q,
                                 double* weights_out, mbis_summary* out, void* cuda_stream);
 
+/* Weighted mean and covariance of n proposal samples: the ingredients of refitting the
+ * Gaussian proposal from importance-weighted samples (the iterative update of the proposal
+ * suggested in Sec. III A).  theta (device, [P][n] as drawn), weights (device, n; e.g. the
+ * normalised weights of mbis_reduce; zero or negative weights are skipped).  mean_out
+ * (host, P) and cov_out (host, P x P row-major) are normalised by the sum of the weights.
+ * Periodic slots (RA, phi_c: 2 pi; psi: pi) are averaged as offsets wrapped around the
+ * current proposal mean.  The stream is synchronised.
+ * Errors: MBIS_E_STATE (no metric), MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_weighted_moments(mbis_ctx* ctx, int64_t n, const double* theta, const double* weights,
+                                  double* mean_out, double* cov_out, void* cuda_stream);
+
+/* Replace the Gaussian proposal (mean, P x P lower Cholesky factor, scale) and keep the
+ * sampled slots and prior of the last mbis_set_metric; no table is rebuilt.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID. */
+mbis_status mbis_set_proposal(mbis_ctx* ctx, const double* mean, const double* chol_lower, double scale);
+
+typedef struct {
+  double ess_target;    /* stop once the running ESS reaches this */
+  int64_t batch;        /* samples per batch; the caller's buffers hold one batch */
+  int64_t max_samples;  /* stop after this many draws even if the target is not reached */
+  int32_t refine;       /* refit the proposal after each of the first `refine` batches */
+  double refine_scale;  /* width scale of a refitted proposal (<= 0 keeps the current scale) */
+  uint64_t seed;        /* Philox key; batch b uses counters [b * batch, (b + 1) * batch) */
+} mbis_ess_options;
+
+/* ESS-target loop: batches of draw -> likelihood -> weights merged into the running state
+ * until ESS >= ess_target (the paper quotes costs for a target of 10^4 effective samples,
+ * App. C).  With refine > 0, each of the first `refine` batches refits the proposal
+ * (weighted mean and covariance, mbis_weighted_moments) when its own ESS is at least 2P + 1;
+ * batches drawn before the last refit only adapt the proposal and do not enter the
+ * estimate.  Buffers (device, one batch): theta [P][batch], log_q, log_prior, loglike,
+ * weights [batch].  *out: summary of the estimate; n_drawn (host, nullable): every draw,
+ * adaptation included; n_used (host, nullable): draws in the estimate.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_UNSUPPORTED, MBIS_E_CUDA, MBIS_E_TIMEOUT. */
+mbis_status mbis_run_to_ess(mbis_ctx* ctx, const mbis_ess_options* opts, double* theta, double* log_q,
+                            double* log_prior, double* loglike, double* weights, mbis_summary* out,
+                            int64_t* n_drawn, int64_t* n_used, void* cuda_stream);
+
+/* ---- many events in one launch ----------------------------------------------------- */
+
+typedef struct mbis_batch mbis_batch;
+
+/* A batch of events whose likelihoods run in one persistent launch: the 128-sample tiles of
+ * every event form one work list, longest first, consumed by a persistent grid; a step
+ * (draws, likelihoods, reductions, summaries of every event) is one CUDA graph replay.
+ * ctxs: n_ctx contexts with a metric set, MBIS_MIXED, fixed sky/orientation, PHASE or
+ * PHASE|DISTANCE marginalisation (they stay owned by the caller and must outlive the
+ * batch; a context re-targeted by mbis_set_metric / mbis_set_proposal between steps is
+ * picked up by the next step, which rebuilds the launch arguments and re-captures the
+ * graph).  A context belongs to at most one batch at a time
+ * (the batch uses the context's reduction scratch).  n_samples[i] samples per step for
+ * event i (1..2^30), seeds[i] its Philox key.  The batch allocates the sample buffers of
+ * every event on the device and its own non-blocking stream.
+ * Errors: MBIS_E_INVALID, MBIS_E_STATE, MBIS_E_UNSUPPORTED, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_t* n_samples, const uint64_t* seeds,
+                              mbis_batch** out);
+
+/* One step: event i draws counters [step * n_i, (step + 1) * n_i).  out: host array of n_ctx
+ * summaries (this step alone).  Synchronises the batch's own stream. */
+mbis_status mbis_batch_step(mbis_batch* b, uint64_t step, mbis_summary* out);
+
+/* Times the persistent launch for 2, 4, 6 and 8 CTAs per SM on the current samples and keeps
+ * the fastest (re-capturing the step graph).  grid_out / ms_out (host, nullable). */
+mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out);
+
+/* The persistent likelihood launch alone, on the batch's current samples, on a caller
+ * stream (for timing and tests). */
+mbis_status mbis_batch_loglike(mbis_batch* b, void* cuda_stream);
+
+/* Device pointers of event i's sample and log-likelihood buffers ([P][n_i] and [n_i]),
+ * owned by the batch. */
+mbis_status mbis_batch_buffers(mbis_batch* b, int32_t i, double** theta, double** loglike);
+
+/* Copy event i's current samples (host, [P][n_i]) and log-likelihoods (host, [n_i]) out;
+ * either pointer may be NULL.  Synchronises the batch's stream. */
+mbis_status mbis_batch_copy_out(mbis_batch* b, int32_t i, double* theta_host, double* loglike_host);
+
+void mbis_batch_destroy(mbis_batch* b);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

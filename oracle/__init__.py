@@ -99,6 +99,7 @@ def lib():
             "or_log_prior": (d, [i32, p, p, p, u32, p]),
             "or_draw": (None, [u64, u64, i64, i32, p, p, p, d, p, p]),
             "or_reduce": (None, [i64, p, p, p, p, p]),
+            "or_weighted_moments": (None, [i64, i32, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -324,6 +325,17 @@ def reduce(loglike, logp, logq, want_weights=False):
     if want_weights:
         res["weights"] = w
     return res
+
+
+def weighted_moments(ids, theta, weights, ref):
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    th, w, r = _f64(theta), _f64(weights), _f64(ref)
+    P = len(ids)
+    n = th.reshape(P, -1).shape[1]
+    mean = np.zeros(P)
+    cov = np.zeros((P, P))
+    lib().or_weighted_moments(n, P, _ptr(ids), _ptr(th), _ptr(w), _ptr(r), _ptr(mean), _ptr(cov))
+    return mean, cov
 
 
 def full_params(ids, theta_cols, fixed):

@@ -617,6 +617,47 @@ void or_draw(uint64_t seed, uint64_t ctr0, int64_t n, int32_t P, const int32_t* 
   }
 }
 
+/* Weighted mean and covariance of samples (the refit of the Gaussian proposal from the
+ * weighted samples suggested in Sec. III A), two passes.  Periodic slots (RA, phi_c: 2 pi,
+ * psi: pi) are taken as offsets from ref wrapped into [-period/2, period/2); the mean is
+ * wrapped back into the period.  theta SoA [P][n]; weights <= 0 are skipped. */
+void or_weighted_moments(int64_t n, int32_t P, const int32_t* ids, const double* theta, const double* w,
+                         const double* ref, double* mean_out, double* cov_out) {
+  double period[16], wsum = 0.0, mu[16];
+  for (int32_t p = 0; p < P; ++p) {
+    period[p] = (ids[p] == OR_PSI) ? OR_PI : (ids[p] == OR_RA || ids[p] == OR_PHIC) ? OR_TWO_PI : 0.0;
+    mu[p] = 0.0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(w[i] > 0.0)) continue;
+    wsum += w[i];
+    for (int32_t p = 0; p < P; ++p) {
+      double d = theta[(int64_t)p * n + i] - ref[p];
+      if (period[p] > 0.0) d -= period[p] * floor(d / period[p] + 0.5);
+      mu[p] += w[i] * d;
+    }
+  }
+  for (int32_t p = 0; p < P; ++p) mu[p] /= wsum;
+  for (int32_t p = 0; p < P; ++p)
+    for (int32_t q = 0; q < P; ++q) cov_out[p * P + q] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(w[i] > 0.0)) continue;
+    double d[16];
+    for (int32_t p = 0; p < P; ++p) {
+      double x = theta[(int64_t)p * n + i] - ref[p];
+      if (period[p] > 0.0) x -= period[p] * floor(x / period[p] + 0.5);
+      d[p] = x - mu[p];
+    }
+    for (int32_t p = 0; p < P; ++p)
+      for (int32_t q = 0; q < P; ++q) cov_out[p * P + q] += w[i] * d[p] * d[q] / wsum;
+  }
+  for (int32_t p = 0; p < P; ++p) {
+    double x = ref[p] + mu[p];
+    if (period[p] > 0.0) x -= period[p] * floor(x / period[p]);
+    mean_out[p] = x;
+  }
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Importance weights (Eq. 5), Kish effective sample size (Eq. 6) and the evidence.
  *   log w_i = log L_i + log pi_i - log g_i

@@ -77,7 +77,18 @@ def _load():
         "mbis_inject": [p, i32, p, p, d, p, u64, i32, p, p],
         "mbis_fisher": [p, p, i32, p, p, p],
         "mbis_reduce_noalloc": [i64, p, p, p, p, p, p],
+        "mbis_weighted_moments": [p, i64, p, p, p, p, p],
+        "mbis_set_proposal": [p, p, p, d],
+        "mbis_run_to_ess": [p, p, p, p, p, p, p, p, p, p, p],
+        "mbis_batch_create": [i32, p, p, p, p],
+        "mbis_batch_step": [p, u64, p],
+        "mbis_batch_autotune": [p, p, p],
+        "mbis_batch_loglike": [p, p],
+        "mbis_batch_buffers": [p, i32, p, p],
+        "mbis_batch_copy_out": [p, i32, p, p],
     }
+    lib.mbis_batch_destroy.restype = None
+    lib.mbis_batch_destroy.argtypes = [p]
     for name, args in sigs.items():
         f = getattr(lib, name)
         f.restype = C.c_int
@@ -183,6 +194,83 @@ def mbis_reduce(ctx, n, loglike, log_prior, log_q, weights_out=None, accumulate=
     _check(_lib.mbis_reduce(ctx, n, _dev(loglike), _dev(log_prior), _dev(log_q), _dev(weights_out), int(accumulate),
                             C.byref(out), _stream(stream)), ctx)
     return out.as_dict()
+
+
+class EssOptions(C.Structure):
+    _fields_ = [("ess_target", C.c_double), ("batch", C.c_int64), ("max_samples", C.c_int64), ("refine", C.c_int32),
+                ("refine_scale", C.c_double), ("seed", C.c_uint64)]
+
+
+def mbis_weighted_moments(ctx, n, theta, weights, stream=None):
+    """Returns (mean [P], covariance [P, P]) of the weighted samples."""
+    P = len(theta) if not isinstance(theta, int) else None
+    mean = np.zeros(11)
+    cov = np.zeros(121)
+    _check(_lib.mbis_weighted_moments(ctx, n, _dev(theta), _dev(weights), mean.ctypes.data, cov.ctypes.data,
+                                      _stream(stream)), ctx)
+    if P is None:
+        raise ValueError("pass theta as a [P, n] tensor")
+    return mean[:P].copy(), cov[:P * P].reshape(P, P).copy()
+
+
+def mbis_set_proposal(ctx, mean, chol_lower, scale):
+    m, pm = _host(mean, np.float64)
+    L, pL = _host(chol_lower, np.float64)
+    _check(_lib.mbis_set_proposal(ctx, pm, pL, scale), ctx)
+
+
+def mbis_run_to_ess(ctx, theta, log_q, log_prior, loglike, weights, ess_target, batch, max_samples, seed, refine=0,
+                    refine_scale=0.0, stream=None):
+    """Returns (summary dict, n_drawn, n_used)."""
+    opts = EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed)
+    out = Summary()
+    nd, nu = C.c_int64(), C.c_int64()
+    _check(_lib.mbis_run_to_ess(ctx, C.byref(opts), _dev(theta), _dev(log_q), _dev(log_prior), _dev(loglike),
+                                _dev(weights), C.byref(out), C.byref(nd), C.byref(nu), _stream(stream)), ctx)
+    return out.as_dict(), nd.value, nu.value
+
+
+def mbis_batch_create(ctxs, n_samples, seeds):
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*ctxs)
+    ns = np.ascontiguousarray(n_samples, dtype=np.int64)
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    out = C.c_void_p()
+    _check(_lib.mbis_batch_create(n, arr, ns.ctypes.data, sd.ctypes.data, C.byref(out)))
+    return out.value
+
+
+def mbis_batch_step(b, step, n_ctx):
+    out = (Summary * n_ctx)()
+    _check(_lib.mbis_batch_step(b, step, out))
+    return [s.as_dict() for s in out]
+
+
+def mbis_batch_autotune(b):
+    g, ms = C.c_int32(), C.c_float()
+    _check(_lib.mbis_batch_autotune(b, C.byref(g), C.byref(ms)))
+    return g.value, ms.value
+
+
+def mbis_batch_loglike(b, stream=None):
+    _check(_lib.mbis_batch_loglike(b, _stream(stream)))
+
+
+def mbis_batch_buffers(b, i):
+    th, ll = C.c_void_p(), C.c_void_p()
+    _check(_lib.mbis_batch_buffers(b, i, C.byref(th), C.byref(ll)))
+    return th.value, ll.value
+
+
+def mbis_batch_copy_out(b, i, P, n):
+    th = np.zeros((P, n))
+    ll = np.zeros(n)
+    _check(_lib.mbis_batch_copy_out(b, i, th.ctypes.data, ll.ctypes.data))
+    return th, ll
+
+
+def mbis_batch_destroy(b):
+    _lib.mbis_batch_destroy(b)
 
 
 NOALLOC_MAX_SAMPLES = 16777216

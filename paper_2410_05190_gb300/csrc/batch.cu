@@ -1,0 +1,305 @@
+// batch.cu -- many events in one persistent likelihood launch, one CUDA graph per step.
+//
+// Events of uneven size (frequency grids of 2k-128k bins, 2 or 3 detectors, 2^14-2^20
+// samples) share the GPU in a single launch: their 128-sample tiles form one work list,
+// ordered longest first (estimated live bins), that a persistent grid of CTAs consumes
+// through a device counter.  One step -- upload of the Philox counters, the draws of every
+// event, the persistent likelihood launch, the two-pass reduction of every event and the
+// copy of the summaries to pinned host memory -- is captured once in a CUDA graph and
+// replayed.  The size of the persistent grid is picked by timing candidates (autotuner).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mbis;
+
+struct mbis_batch {
+  int32_t n = 0;
+  std::vector<mbis_ctx*> ctx;
+  std::vector<uint64_t> gen;  // each context's generation when the launch arguments were made
+  std::vector<int64_t> ns;
+  std::vector<uint64_t> seeds;
+  std::vector<double*> theta, logq, logp, ll;
+  LikeArgs* d_args = nullptr;
+  BatchItem* d_items = nullptr;
+  int32_t n_items = 0;
+  int32_t* d_next = nullptr;
+  uint64_t* d_ctr = nullptr;
+  uint64_t* h_ctr = nullptr;  // pinned
+  double* h_res = nullptr;    // pinned, 4 per event
+  int32_t grid = 152 * 8;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+mbis_status berr(mbis_status st, const std::string& m) {
+  set_last_error(m);
+  return st;
+}
+
+#define B_TRY(call)                                                                            \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return berr(e_ == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,                   \
+                  std::string("mbis_batch: ") + #call + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+// enqueue one step on b->stream (also used inside stream capture)
+mbis_status enqueue_step(mbis_batch* b) {
+  B_TRY(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(uint64_t) * b->n, cudaMemcpyHostToDevice, b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    DrawArgs da = make_draw_args(b->ctx[i], b->seeds[i], 0, b->ns[i], b->theta[i], b->logq[i], b->logp[i]);
+    da.d_ctr0 = b->d_ctr + i;
+    B_TRY(launch_draw(da, b->stream));
+  }
+  B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid, b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    B_TRY(launch_reduce(b->ns[i], b->ll[i], b->logp[i], b->logq[i], nullptr, b->ctx[i]->red, b->stream));
+    B_TRY(cudaMemcpyAsync(b->h_res + 4 * i, b->ctx[i]->red.result, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                          b->stream));
+  }
+  return MBIS_OK;
+}
+
+mbis_status capture(mbis_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  B_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const mbis_status st = enqueue_step(b);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (st != MBIS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  B_TRY(e);
+  b->graph = g;
+  B_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return MBIS_OK;
+}
+
+mbis_status check_ctx(const mbis_ctx* c) {
+  if (!c || !c->has_metric) return berr(MBIS_E_STATE, "mbis_batch: every context needs a metric");
+  if (c->opts.precision != MBIS_MIXED || c->tables_mode != 1 || (c->opts.marg & MBIS_MARG_TIME))
+    return berr(MBIS_E_UNSUPPORTED,
+                "mbis_batch: contexts must be mixed precision with fixed extrinsics and phase "
+                "(or phase + distance) marginalisation");
+  return MBIS_OK;
+}
+
+// A context re-targeted since the launch arguments were made (mbis_set_metric rebuilds its
+// tables, mbis_set_proposal moves the Gaussian): rebuild the arguments and re-capture.
+mbis_status refresh(mbis_batch* b) {
+  bool stale = false;
+  for (int i = 0; i < b->n; ++i) stale |= b->ctx[i]->gen != b->gen[i];
+  if (!stale) return MBIS_OK;
+  std::vector<LikeArgs> args(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    if (const mbis_status st = check_ctx(b->ctx[i]); st != MBIS_OK) return st;
+    args[i] = make_like_args(b->ctx[i], b->ns[i], b->theta[i], b->ll[i]);
+  }
+  B_TRY(cudaStreamSynchronize(b->stream));
+  B_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * b->n, cudaMemcpyHostToDevice));
+  for (int i = 0; i < b->n; ++i) b->gen[i] = b->ctx[i]->gen;
+  return capture(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_t* n_samples, const uint64_t* seeds,
+                              mbis_batch** out) {
+  if (out) *out = nullptr;
+  if (n_ctx < 1 || !ctxs || !n_samples || !seeds || !out) return berr(MBIS_E_INVALID, "mbis_batch_create: bad argument");
+  for (int i = 0; i < n_ctx; ++i) {
+    if (const mbis_status st = check_ctx(ctxs[i]); st != MBIS_OK) return st;
+    if (n_samples[i] < 1 || n_samples[i] > ((int64_t)1 << 30))
+      return berr(MBIS_E_INVALID, "mbis_batch_create: n_samples must be in [1, 2^30]");
+  }
+  mbis_batch* b = new (std::nothrow) mbis_batch();
+  if (!b) return berr(MBIS_E_OOM, "mbis_batch_create: host allocation failed");
+  b->n = n_ctx;
+  b->ctx.assign(ctxs, ctxs + n_ctx);
+  for (int i = 0; i < n_ctx; ++i) b->gen.push_back(ctxs[i]->gen);
+  b->ns.assign(n_samples, n_samples + n_ctx);
+  b->seeds.assign(seeds, seeds + n_ctx);
+  b->theta.assign(n_ctx, nullptr);
+  b->logq.assign(n_ctx, nullptr);
+  b->logp.assign(n_ctx, nullptr);
+  b->ll.assign(n_ctx, nullptr);
+  auto fail = [&](mbis_status st) {
+    mbis_batch_destroy(b);
+    return st;
+  };
+#define C_TRY(call)                                                                               \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      berr(e_ == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,                            \
+           std::string("mbis_batch_create: ") + #call + ": " + cudaGetErrorString(e_));           \
+      return fail(e_ == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA);                     \
+    }                                                                                             \
+  } while (0)
+  C_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  std::vector<LikeArgs> args(n_ctx);
+  struct Cost {
+    double cost;
+    BatchItem item;
+  };
+  std::vector<Cost> items;
+  for (int i = 0; i < n_ctx; ++i) {
+    const mbis_ctx* c = ctxs[i];
+    const int64_t n = n_samples[i];
+    C_TRY(cudaMalloc(&b->theta[i], sizeof(double) * n * c->P));
+    C_TRY(cudaMalloc(&b->logq[i], sizeof(double) * n));
+    C_TRY(cudaMalloc(&b->logp[i], sizeof(double) * n));
+    C_TRY(cudaMalloc(&b->ll[i], sizeof(double) * n));
+    args[i] = make_like_args(c, n, b->theta[i], b->ll[i]);
+    // estimated work of a tile: live bins at the proposal mean
+    double mc = c->fixed[kMc], q = c->fixed[kQ];
+    for (int p = 0; p < c->P; ++p) {
+      if (c->ids[p] == kMc) mc = c->mean[p];
+      if (c->ids[p] == kQ) q = c->mean[p];
+    }
+    const double live = (double)live_bins(mc, q > 0 ? q : 1.0, c->f_lo, c->df, c->n_bins);
+    const int32_t tiles = (int32_t)((n + kMixedThreads - 1) / kMixedThreads);
+    for (int32_t t = 0; t < tiles; ++t) items.push_back({live, {i, t}});
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Cost& x, const Cost& y) { return x.cost > y.cost; });
+  std::vector<BatchItem> list(items.size());
+  for (size_t k = 0; k < items.size(); ++k) list[k] = items[k].item;
+  b->n_items = (int32_t)list.size();
+  C_TRY(cudaMalloc(&b->d_args, sizeof(LikeArgs) * n_ctx));
+  C_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * n_ctx, cudaMemcpyHostToDevice));
+  C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * list.size()));
+  C_TRY(cudaMemcpy(b->d_items, list.data(), sizeof(BatchItem) * list.size(), cudaMemcpyHostToDevice));
+  C_TRY(cudaMalloc(&b->d_next, sizeof(int32_t)));
+  C_TRY(cudaMalloc(&b->d_ctr, sizeof(uint64_t) * n_ctx));
+  C_TRY(cudaMallocHost(&b->h_ctr, sizeof(uint64_t) * n_ctx));
+  C_TRY(cudaMallocHost(&b->h_res, sizeof(double) * 4 * n_ctx));
+  std::memset(b->h_ctr, 0, sizeof(uint64_t) * n_ctx);
+#undef C_TRY
+  const mbis_status st = capture(b);
+  if (st != MBIS_OK) return fail(st);
+  *out = b;
+  return MBIS_OK;
+}
+
+void mbis_batch_destroy(mbis_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int i = 0; i < b->n; ++i) {
+    if (b->theta[i]) cudaFree(b->theta[i]);
+    if (b->logq[i]) cudaFree(b->logq[i]);
+    if (b->logp[i]) cudaFree(b->logp[i]);
+    if (b->ll[i]) cudaFree(b->ll[i]);
+  }
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_next) cudaFree(b->d_next);
+  if (b->d_ctr) cudaFree(b->d_ctr);
+  if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->h_res) cudaFreeHost(b->h_res);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+mbis_status mbis_batch_step(mbis_batch* b, uint64_t step, mbis_summary* out) {
+  if (!b || !out) return berr(MBIS_E_INVALID, "mbis_batch_step: null argument");
+  if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
+  for (int i = 0; i < b->n; ++i) b->h_ctr[i] = step * (uint64_t)b->ns[i];
+  B_TRY(cudaGraphLaunch(b->exec, b->stream));
+  B_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    const double* r = b->h_res + 4 * i;
+    const double m = r[0], s1 = r[1], s2 = r[2];
+    out[i].max_logw = m;
+    out[i].s1 = s1;
+    out[i].s2 = s2;
+    out[i].n = b->ns[i];
+    out[i].all_zero = !(m > -INFINITY) || !(s1 > 0.0);
+    out[i].ess = s2 > 0.0 ? s1 * s1 / s2 : 0.0;
+    out[i].log_z = (m > -INFINITY && s1 > 0.0) ? m + log(s1) - log((double)b->ns[i]) : -INFINITY;
+  }
+  return MBIS_OK;
+}
+
+mbis_status mbis_batch_loglike(mbis_batch* b, void* stream) {
+  if (!b) return berr(MBIS_E_INVALID, "mbis_batch_loglike: null batch");
+  if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
+  B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid,
+                                   static_cast<cudaStream_t>(stream)));
+  return MBIS_OK;
+}
+
+mbis_status mbis_batch_buffers(mbis_batch* b, int32_t i, double** theta, double** loglike) {
+  if (!b || i < 0 || i >= b->n) return berr(MBIS_E_INVALID, "mbis_batch_buffers: bad index");
+  if (theta) *theta = b->theta[i];
+  if (loglike) *loglike = b->ll[i];
+  return MBIS_OK;
+}
+
+mbis_status mbis_batch_copy_out(mbis_batch* b, int32_t i, double* theta_host, double* loglike_host) {
+  if (!b || i < 0 || i >= b->n) return berr(MBIS_E_INVALID, "mbis_batch_copy_out: bad index");
+  B_TRY(cudaStreamSynchronize(b->stream));
+  if (theta_host)
+    B_TRY(cudaMemcpy(theta_host, b->theta[i], sizeof(double) * b->ns[i] * b->ctx[i]->P, cudaMemcpyDeviceToHost));
+  if (loglike_host) B_TRY(cudaMemcpy(loglike_host, b->ll[i], sizeof(double) * b->ns[i], cudaMemcpyDeviceToHost));
+  return MBIS_OK;
+}
+
+mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out) {
+  if (!b) return berr(MBIS_E_INVALID, "mbis_batch_autotune: null batch");
+  if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
+  // fill the sample buffers once
+  for (int i = 0; i < b->n; ++i) b->h_ctr[i] = 0;
+  B_TRY(cudaGraphLaunch(b->exec, b->stream));
+  B_TRY(cudaStreamSynchronize(b->stream));
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int cand[] = {2, 4, 6, 8};
+  cudaEvent_t e0, e1;
+  B_TRY(cudaEventCreate(&e0));
+  B_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_grid = sms * 8;
+  for (int c : cand) {
+    b->grid = sms * c;
+    float t = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      B_TRY(cudaEventRecord(e0, b->stream));
+      B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid, b->stream));
+      B_TRY(cudaEventRecord(e1, b->stream));
+      B_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t += ms;  // first repetition warms up
+    }
+    if (t < best) {
+      best = t;
+      best_grid = b->grid;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->grid = best_grid;
+  if (grid_out) *grid_out = best_grid;
+  if (ms_out) *ms_out = best / 2.0f;
+  return capture(b);
+}
+
+}  // extern "C"

@@ -115,6 +115,7 @@ void coefficient_bounds(const mbis_ctx* c, double* cmax) {
 mbis_status build_tables(mbis_ctx* c) {
   const bool fold = !(sampled(c, kRa) || sampled(c, kDec) || sampled(c, kPsi) || sampled(c, kIota));
   free_tables(c);
+  ++c->gen;
   const int32_t n = c->n_bins, nd = c->n_det;
   cudaStream_t s = nullptr;
   double* d_w = nullptr;
@@ -206,6 +207,81 @@ __global__ void central_diff_kernel(int32_t P, const double2* h, const double* s
 namespace mbis {
 // message for mbis_last_error(NULL) from entry points defined in other files
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
+                        double* log_prior) {
+  DrawArgs a = {};
+  a.P = c->P;
+  double logdet = 0.0;
+  for (int p = 0; p < c->P; ++p) {
+    a.ids[p] = c->ids[p];
+    a.mean[p] = c->mean[p];
+    a.lo[p] = c->lo[p];
+    a.hi[p] = c->hi[p];
+    logdet += log(c->chol[p * kMaxP + p]);
+  }
+  std::memcpy(a.chol, c->chol, sizeof(a.chol));
+  a.scale = c->scale;
+  a.flags = c->prior_flags;
+  a.log_mass_norm = c->log_mass_norm;
+  a.log_q_const = -logdet - 0.5 * c->P * log(kTwoPi) - c->P * log(c->scale);
+  a.seed = seed;
+  a.ctr0 = ctr0;
+  a.d_ctr0 = nullptr;
+  a.n = n;
+  a.theta = theta;
+  a.logq = log_q;
+  a.logp = log_prior;
+  return a;
+}
+
+LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, double* loglike) {
+  LikeArgs a = {};
+  a.n = n;
+  a.theta = theta;
+  a.out = loglike;
+  a.P = c->P;
+  for (int s = 0; s < kNumSlots; ++s) a.pos[s] = -1;
+  for (int p = 0; p < c->P; ++p) {
+    a.ids[p] = c->ids[p];
+    a.pos[c->ids[p]] = (int8_t)p;
+  }
+  std::memcpy(a.fixed, c->fixed, sizeof(a.fixed));
+  a.marg = c->opts.marg;
+  a.dmin = c->opts.dmin_mpc;
+  a.dmax = c->opts.dmax_mpc;
+  a.n_tshift = c->opts.n_tshift;
+  a.dt_shift = c->opts.dt_shift;
+  a.n_bins = c->n_bins;
+  a.n_det = c->n_det;
+  a.f_lo = c->f_lo;
+  a.df = c->df;
+  a.fold = c->tables_mode == 1;
+  a.basis = c->d_basis;
+  a.cfold64 = c->d_cfold64;
+  a.tfold = c->d_tfold;
+  a.cdet64 = c->d_cdet64;
+  a.tdet = c->d_tdet;
+  for (int d = 0; d < c->n_det; ++d)
+    for (int i = 0; i < 3; ++i) {
+      a.det_vertex[d][i] = c->dets[d].vertex_m[i];
+      a.det_x[d][i] = c->dets[d].xarm[i];
+      a.det_y[d][i] = c->dets[d].yarm[i];
+    }
+  a.gmst = c->gmst;
+  a.twiddle = c->d_twiddle;
+  a.cfold32 = c->d_cfold32;
+  a.cscale = c->cscale;
+  a.plan = c->d_plan;
+  a.n_blocks = c->n_blocks;
+  a.cdet32 = c->d_cdet32;
+  a.n_pad16 = c->n_pad16;
+  a.ttiles = c->d_ttiles;
+  a.n_kb = c->n_kb;
+  a.err = c->d_err;
+  a.gl = c->d_gl;
+  return a;
+}
 }  // namespace mbis
 
 extern "C" {
@@ -284,6 +360,10 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
   CREATE_TRY(cudaMemset(c->red.counter, 0, sizeof(unsigned int)));
   CREATE_TRY(cudaMalloc(&c->red.result, sizeof(double) * 4));
   CREATE_TRY(cudaMallocHost(&c->h_result, sizeof(double) * 5));
+  CREATE_TRY(cudaMalloc(&c->d_mom_partials, sizeof(double) * moments_partials_size(kMaxP)));
+  CREATE_TRY(cudaMalloc(&c->d_mom_counter, sizeof(unsigned int)));
+  CREATE_TRY(cudaMemset(c->d_mom_counter, 0, sizeof(unsigned int)));
+  CREATE_TRY(cudaMalloc(&c->d_mom_out, sizeof(double) * (1 + kMaxP + kMaxP * (kMaxP + 1) / 2)));
   CREATE_TRY(cudaDeviceSynchronize());
 #undef CREATE_TRY
   *out = c;
@@ -302,6 +382,9 @@ void mbis_destroy(mbis_ctx* c) {
   dfree(c->red.counter);
   dfree(c->red.result);
   if (c->h_result) cudaFreeHost(c->h_result);
+  dfree(c->d_mom_partials);
+  dfree(c->d_mom_counter);
+  dfree(c->d_mom_out);
   delete c;
 }
 
@@ -359,27 +442,7 @@ mbis_status mbis_draw(mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, doub
   if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_draw: null context");
   if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_draw: call mbis_set_metric first");
   if (n < 0 || (n > 0 && !theta)) return fail(c, MBIS_E_INVALID, "mbis_draw: bad n or null theta");
-  DrawArgs a = {};
-  a.P = c->P;
-  double logdet = 0.0;
-  for (int p = 0; p < c->P; ++p) {
-    a.ids[p] = c->ids[p];
-    a.mean[p] = c->mean[p];
-    a.lo[p] = c->lo[p];
-    a.hi[p] = c->hi[p];
-    logdet += log(c->chol[p * kMaxP + p]);
-  }
-  std::memcpy(a.chol, c->chol, sizeof(a.chol));
-  a.scale = c->scale;
-  a.flags = c->prior_flags;
-  a.log_mass_norm = c->log_mass_norm;
-  a.log_q_const = -logdet - 0.5 * c->P * log(kTwoPi) - c->P * log(c->scale);
-  a.seed = seed;
-  a.ctr0 = ctr0;
-  a.n = n;
-  a.theta = theta;
-  a.logq = log_q;
-  a.logp = log_prior;
+  const DrawArgs a = make_draw_args(c, seed, ctr0, n, theta, log_q, log_prior);
   CU_TRY(c, launch_draw(a, static_cast<cudaStream_t>(stream)));
   return MBIS_OK;
 }
@@ -390,50 +453,7 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
   if (n < 0 || (n > 0 && (!theta || !loglike))) return fail(c, MBIS_E_INVALID, "mbis_loglike: bad n or null buffer");
   if ((c->opts.marg & MBIS_MARG_TIME) && c->opts.precision == MBIS_MIXED && c->d_ttiles == nullptr)
     return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: mixed-precision time marginalisation needs n_tshift = 128");
-  LikeArgs a = {};
-  a.n = n;
-  a.theta = theta;
-  a.out = loglike;
-  a.P = c->P;
-  for (int s = 0; s < kNumSlots; ++s) a.pos[s] = -1;
-  for (int p = 0; p < c->P; ++p) {
-    a.ids[p] = c->ids[p];
-    a.pos[c->ids[p]] = (int8_t)p;
-  }
-  std::memcpy(a.fixed, c->fixed, sizeof(a.fixed));
-  a.marg = c->opts.marg;
-  a.dmin = c->opts.dmin_mpc;
-  a.dmax = c->opts.dmax_mpc;
-  a.n_tshift = c->opts.n_tshift;
-  a.dt_shift = c->opts.dt_shift;
-  a.n_bins = c->n_bins;
-  a.n_det = c->n_det;
-  a.f_lo = c->f_lo;
-  a.df = c->df;
-  a.fold = c->tables_mode == 1;
-  a.basis = c->d_basis;
-  a.cfold64 = c->d_cfold64;
-  a.tfold = c->d_tfold;
-  a.cdet64 = c->d_cdet64;
-  a.tdet = c->d_tdet;
-  for (int d = 0; d < c->n_det; ++d)
-    for (int i = 0; i < 3; ++i) {
-      a.det_vertex[d][i] = c->dets[d].vertex_m[i];
-      a.det_x[d][i] = c->dets[d].xarm[i];
-      a.det_y[d][i] = c->dets[d].yarm[i];
-    }
-  a.gmst = c->gmst;
-  a.twiddle = c->d_twiddle;
-  a.cfold32 = c->d_cfold32;
-  a.cscale = c->cscale;
-  a.plan = c->d_plan;
-  a.n_blocks = c->n_blocks;
-  a.cdet32 = c->d_cdet32;
-  a.n_pad16 = c->n_pad16;
-  a.ttiles = c->d_ttiles;
-  a.n_kb = c->n_kb;
-  a.err = c->d_err;
-  a.gl = c->d_gl;
+  const LikeArgs a = make_like_args(c, n, theta, loglike);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (c->opts.precision == MBIS_FP64) {
     CU_TRY(c, launch_loglike_fp64(a, s));
@@ -624,6 +644,130 @@ mbis_status mbis_fisher(mbis_ctx* c, const double* theta, int32_t P, const int32
   if (e != cudaSuccess)
     return fail(c, e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,
                 std::string("mbis_fisher: ") + cudaGetErrorString(e));
+  return MBIS_OK;
+}
+
+mbis_status mbis_weighted_moments(mbis_ctx* c, int64_t n, const double* theta, const double* weights,
+                                  double* mean_out, double* cov_out, void* stream) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_weighted_moments: null context");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_weighted_moments: call mbis_set_metric first");
+  if (n < 0 || !mean_out || !cov_out || (n > 0 && (!theta || !weights)))
+    return fail(c, MBIS_E_INVALID, "mbis_weighted_moments: bad n or null buffer");
+  const int32_t P = c->P, nm = 1 + P + P * (P + 1) / 2;
+  MomentArgs ma = {};
+  for (int p = 0; p < P; ++p) {
+    ma.ref[p] = c->mean[p];
+    ma.period[p] = c->ids[p] == kPsi ? kPi : (c->ids[p] == kRa || c->ids[p] == kPhic) ? kTwoPi : 0.0;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<double> h(nm, 0.0);
+  if (n > 0) {
+    CU_TRY(c, launch_moments(n, P, theta, weights, ma, c->d_mom_partials, c->d_mom_counter, c->d_mom_out, s));
+    CU_TRY(c, cudaMemcpyAsync(h.data(), c->d_mom_out, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+    CU_TRY(c, cudaStreamSynchronize(s));
+  }
+  // normalise by the sum of the weights
+  const double wsum = h[0];
+  if (!(wsum > 0.0)) return fail(c, MBIS_E_INVALID, "mbis_weighted_moments: no positive weight");
+  int m = 1;
+  double d[kMaxP];
+  for (int p = 0; p < P; ++p) d[p] = h[m++] / wsum;
+  for (int p = 0; p < P; ++p)
+    for (int q = p; q < P; ++q) {
+      const double v = h[m++] / wsum - d[p] * d[q];
+      cov_out[p * P + q] = v;
+      cov_out[q * P + p] = v;
+    }
+  for (int p = 0; p < P; ++p) {
+    double x = c->mean[p] + d[p];
+    if (ma.period[p] > 0.0) x -= ma.period[p] * floor(x / ma.period[p]);
+    mean_out[p] = x;
+  }
+  return MBIS_OK;
+}
+
+mbis_status mbis_set_proposal(mbis_ctx* c, const double* mean, const double* chol, double scale) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_set_proposal: null context");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_set_proposal: call mbis_set_metric first");
+  if (!mean || !chol || !(scale > 0.0) || !std::isfinite(scale))
+    return fail(c, MBIS_E_INVALID, "mbis_set_proposal: null array or scale <= 0");
+  const int32_t P = c->P;
+  for (int p = 0; p < P; ++p)
+    if (!(chol[p * P + p] > 0.0) || !std::isfinite(mean[p]))
+      return fail(c, MBIS_E_INVALID, "mbis_set_proposal: Cholesky diagonal must be > 0 and the mean finite");
+  for (int p = 0; p < P; ++p) {
+    c->mean[p] = mean[p];
+    for (int r = 0; r < kMaxP; ++r) c->chol[p * kMaxP + r] = (r <= p && r < P) ? chol[p * P + r] : 0.0;
+  }
+  c->scale = scale;
+  ++c->gen;
+  return MBIS_OK;
+}
+
+mbis_status mbis_run_to_ess(mbis_ctx* c, const mbis_ess_options* o, double* theta, double* log_q, double* log_prior,
+                            double* loglike, double* weights, mbis_summary* out, int64_t* n_drawn, int64_t* n_used,
+                            void* stream) {
+  if (!c || !o || !out) return fail(c, MBIS_E_INVALID, "mbis_run_to_ess: null argument");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_run_to_ess: call mbis_set_metric first");
+  if (o->batch < 1 || o->max_samples < 1 || !theta || !log_q || !log_prior || !loglike || !weights)
+    return fail(c, MBIS_E_INVALID, "mbis_run_to_ess: batch and max_samples must be >= 1, buffers non-null");
+  const int32_t P = c->P;
+  mbis_reset_running(c);
+  int64_t drawn = 0, used = 0;
+  int refits_left = o->refine > 0 ? o->refine : 0;
+  mbis_summary cur = {};
+  for (int64_t b = 0; drawn < o->max_samples; ++b) {
+    const int64_t nb = std::min<int64_t>(o->batch, o->max_samples - drawn);
+    mbis_status st = mbis_draw(c, o->seed, (uint64_t)(b * o->batch), nb, theta, log_q, log_prior, stream);
+    if (st == MBIS_OK) st = mbis_loglike(c, nb, theta, loglike, stream);
+    if (st != MBIS_OK) return st;
+    drawn += nb;
+    if (refits_left > 0) {
+      mbis_summary bs;
+      st = mbis_reduce(c, nb, loglike, log_prior, log_q, weights, 0, &bs, stream);
+      if (st != MBIS_OK) return st;
+      --refits_left;
+      if (bs.ess >= 2.0 * P + 1.0) {
+        double mean[kMaxP], cov[kMaxP * kMaxP], L[kMaxP * kMaxP];
+        st = mbis_weighted_moments(c, nb, theta, weights, mean, cov, stream);
+        if (st != MBIS_OK) return st;
+        // Cholesky of the weighted covariance (a small diagonal jitter if it is not positive)
+        bool okc = true;
+        for (int i = 0; i < P && okc; ++i)
+          for (int j = 0; j <= i; ++j) {
+            double sum = cov[i * P + j];
+            for (int k = 0; k < j; ++k) sum -= L[i * P + k] * L[j * P + k];
+            if (i == j) {
+              if (!(sum > 0.0)) {
+                okc = false;
+                break;
+              }
+              L[i * P + i] = sqrt(sum);
+            } else {
+              L[i * P + j] = sum / L[j * P + j];
+            }
+          }
+        if (okc) {
+          for (int i = 0; i < P; ++i)
+            for (int j = i + 1; j < P; ++j) L[i * P + j] = 0.0;
+          st = mbis_set_proposal(c, mean, L, o->refine_scale > 0.0 ? o->refine_scale : c->scale);
+          if (st != MBIS_OK) return st;
+        }
+      }
+      mbis_reset_running(c);
+      used = 0;
+      cur = mbis_summary{};
+      continue;
+    }
+    st = mbis_reduce(c, nb, loglike, log_prior, log_q, nullptr, 1, &cur, stream);
+    if (st != MBIS_OK) return st;
+    used += nb;
+    if (cur.ess >= o->ess_target) break;
+  }
+  if (used == 0) summary_from_state(-INFINITY, 0.0, 0.0, 0, &cur);
+  *out = cur;
+  if (n_drawn) *n_drawn = drawn;
+  if (n_used) *n_used = used;
   return MBIS_OK;
 }
 

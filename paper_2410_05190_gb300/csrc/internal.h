@@ -83,10 +83,16 @@ struct DrawArgs {
   double log_mass_norm;  // ln of the (Mc, q) volume of the flat-in-(m1, m2) prior
   double log_q_const;    // -sum ln L_pp - (P/2) ln 2pi - P ln s
   uint64_t seed, ctr0;
+  const uint64_t* d_ctr0;  // when set, the counter base is read from device memory (graph replays)
   int64_t n;
   double* theta;
   double* logq;
   double* logp;
+};
+
+// one work item of the persistent multi-event likelihood launch
+struct BatchItem {
+  int32_t ev, tile;
 };
 
 // kernel launchers (each returns cudaGetLastError() of its launch)
@@ -97,6 +103,14 @@ cudaError_t launch_rows_to_f32(const double2* c, int32_t rows, int32_t n, int32_
 cudaError_t launch_twiddle_tiles(int32_t n, double f_lo, double df, double dt, int32_t n_kb, float* out,
                                  cudaStream_t s);
 cudaError_t launch_loglike_mixed_time(const LikeArgs& a, cudaStream_t s);
+
+struct MomentArgs {
+  double ref[kMaxP];     // offsets are taken from this point
+  double period[kMaxP];  // > 0 for periodic slots (offsets wrapped into [-period/2, period/2))
+};
+int moments_partials_size(int32_t P);
+cudaError_t launch_moments(int64_t n, int32_t P, const double* theta, const double* w, const MomentArgs& ma,
+                           double* partials, unsigned int* counter, double* out, cudaStream_t s);
 
 constexpr int kTimeShifts = 128;  // shifts of the tensor-core time marginalisation (MMA N)
 constexpr int kKBlockBins = 16;   // bins per K-block of the time-shift contraction
@@ -109,6 +123,8 @@ cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv
 cudaError_t launch_draw(const DrawArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_fp64(const LikeArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s);
+cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
+                                      int32_t grid, cudaStream_t s);
 
 // two-pass weight reduction; partials / counter / result are device scratch
 struct ReduceScratch {
@@ -144,6 +160,13 @@ void set_last_error(const std::string& msg);
 
 }  // namespace mbis
 
+struct mbis_ctx;
+namespace mbis {
+DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
+                        double* log_prior);
+LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, double* loglike);
+}  // namespace mbis
+
 // the context behind the opaque handle
 struct mbis_ctx {
   int32_t n_det = 0, n_bins = 0, dtype = 0;
@@ -164,6 +187,7 @@ struct mbis_ctx {
   double log_mass_norm = 0.0;
   // tables
   int32_t tables_mode = -1;  // -1 none, 1 fold, 0 per-detector
+  uint64_t gen = 0;          // bumped whenever the tables or the proposal change (batches re-capture)
   double* d_basis = nullptr;
   double2* d_cfold64 = nullptr;
   double* d_tfold = nullptr;
@@ -182,6 +206,10 @@ struct mbis_ctx {
   // reduction scratch
   mbis::ReduceScratch red = {};
   double* h_result = nullptr;  // pinned, 4 doubles
+  // weighted-moment scratch (proposal refits)
+  double* d_mom_partials = nullptr;
+  unsigned int* d_mom_counter = nullptr;
+  double* d_mom_out = nullptr;
   mbis_summary running = {};
   bool has_running = false;
   std::string err;

@@ -54,7 +54,7 @@ struct DrawConsts {
 __global__ void draw_kernel(DrawArgs a, DrawConsts k) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  const uint64_t g = a.ctr0 + (uint64_t)i;
+  const uint64_t g = (a.d_ctr0 ? *a.d_ctr0 : a.ctr0) + (uint64_t)i;
   double z[12];
 #pragma unroll
   for (int blk = 0; blk < 3; ++blk) {

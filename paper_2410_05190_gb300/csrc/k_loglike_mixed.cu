@@ -122,14 +122,16 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
 
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
 
-__global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
+// One tile of 128 samples of one event.  `first` is false when the CTA has already run a
+// tile (persistent launch): the mbarriers are then invalidated and initialised afresh.
+__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first) {
   __shared__ __align__(128) float4 sC[kNbuf][kChunk / 2];
   __shared__ __align__(8) uint64_t bar[kNbuf];
   __shared__ double sPC[(kNumBasis + 1) * kMixedThreads];  // C_j and cst per thread
   __shared__ float sCF[(kNumBasis - 1) * kMixedThreads];   // FP32 copies of C_0..C_7
   __shared__ int s_kmax;
   const int tid = threadIdx.x;
-  const int64_t s = (int64_t)blockIdx.x * kMixedThreads + tid;
+  const int64_t s = tile * kMixedThreads + tid;
   const bool active = s < a.n;
 
   // ---- per-sample set-up (FP64)
@@ -164,6 +166,8 @@ __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(Li
 
   if (tid == 0) {
     s_kmax = 0;
+    if (!first)
+      for (int b = 0; b < kNbuf; ++b) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar[b])) : "memory");
     for (int b = 0; b < kNbuf; ++b) mbar_init(&bar[b], 1);
     mbar_fence_init();
   }
@@ -296,7 +300,41 @@ __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(Li
   a.out[s] = ll;
 }
 
+__global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
+  fold_tile(a, blockIdx.x, true);
+}
+
+// Persistent launch over the tiles of many events: each CTA takes (event, tile) items from a
+// device counter until the list is exhausted.  The host orders the list longest first, so
+// uneven events (2k-128k bins, 2^14-2^20 samples) balance across the SMs.
+__global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_batch_kernel(const LikeArgs* __restrict__ args,
+                                                                               const BatchItem* __restrict__ items,
+                                                                               int32_t n_items, int32_t* next) {
+  __shared__ int s_item;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    fold_tile(args[item.ev], item.tile, first);
+    first = false;
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
+                                      int32_t grid, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  loglike_mixed_batch_kernel<<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;

@@ -162,6 +162,24 @@ def test_reduce_against_scipy_logsumexp():
     assert abs(r["weights"].sum() - 1) < 1e-12
 
 
+def test_weighted_moments_against_numpy_and_wrap():
+    rng = np.random.default_rng(4)
+    n, ids = 5000, [MC, Q, CHI1, RA]
+    theta = np.stack([rng.normal(1.2, 1e-4, n), rng.normal(1.5, 0.1, n), rng.normal(0, 0.02, n),
+                      np.mod(rng.normal(0.05, 0.1, n), 2 * math.pi)])     # RA straddles 0 = 2 pi
+    w = rng.uniform(0, 1, n)
+    w[::7] = 0.0
+    ref = np.array([1.2, 1.5, 0.0, 6.2])
+    mean, cov = oracle.weighted_moments(ids, theta, w, ref)
+    lin = theta.copy()
+    lin[3] = np.where(lin[3] > math.pi, lin[3] - 2 * math.pi, lin[3])    # unwrapped reference copy
+    mu = np.average(lin, axis=1, weights=w)
+    ref_cov = np.cov(lin, aweights=w, bias=True)
+    np.testing.assert_allclose(mean[:3], mu[:3], rtol=1e-12, atol=1e-14)
+    assert abs(((mean[3] - mu[3] + math.pi) % (2 * math.pi)) - math.pi) < 1e-12
+    np.testing.assert_allclose(cov, ref_cov, rtol=1e-9, atol=1e-18)
+
+
 def test_proposal_equal_to_target_gives_ess_n_and_closed_form_evidence():
     """App. A (after Eq. 6): a proposal equal to the posterior makes every weight equal."""
     rng = np.random.default_rng(11)

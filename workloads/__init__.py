@@ -163,6 +163,51 @@ def bbh_population(n_events=128, n_samples=1 << 18, seed=POPULATION_SEED + 3):
                     1.5, PRIOR_M1M2, 0.8, events)
 
 
+UNEVEN_DF = [1.0 / 4, 1.0 / 8, 1.0 / 16, 1.0 / 32, 1.0 / 64, 1.0 / 128]
+
+
+def uneven_batch(n_events=64, seed=POPULATION_SEED + 4):
+    """Events of uneven size for one persistent launch, alternating two families:
+
+    * heavy (the plain-method family): m1, m2 ~ U[20, 40] (sorted), chi ~ U[-0.5, 0.5],
+      20-512 Hz, sampled (Mc, q, chi1, chi2), phase marginalised, SNR ~ U[10, 30];
+    * BNS (the population family): m1, m2 ~ U[1.1, 2.0], chi ~ U[-0.05, 0.05], 20-1024 Hz,
+      sampled (Mc, q, chi1, chi2, t_c), phase and distance marginalised, SNR ~ U[10, 30];
+
+    each with df drawn from {1/4, ..., 1/128} Hz (1,969 to 128,513 bins), H1+L1 or
+    H1+L1+V1 (fixed extrinsics), 2^14 .. 2^20 samples, coloured Gaussian noise, complex64
+    data, mixed precision.  Returns one single-event Workload per event."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for e in range(n_events):
+        bns = e % 2 == 1
+        df = UNEVEN_DF[int(rng.integers(0, len(UNEVEN_DF)))]
+        dets = ["H1", "L1", "V1"] if rng.uniform() < 0.5 else ["H1", "L1"]
+        n_samples = 1 << int(rng.integers(14, 21))
+        if bns:
+            m = np.sort(rng.uniform(1.1, 2.0, size=2))[::-1]
+            chi = rng.uniform(-0.05, 0.05, size=2)
+        else:
+            m = np.sort(rng.uniform(20.0, 40.0, size=2))[::-1]
+            chi = rng.uniform(-0.5, 0.5, size=2)
+        ra, dec, psi, iota = _isotropic(rng)
+        gmst = rng.uniform(0.0, 2 * math.pi)
+        phic = rng.uniform(0.0, 2 * math.pi)
+        snr = rng.uniform(10.0, 30.0)
+        spec = EventSpec(float(m[0]), float(m[1]),
+                         dict(chi1=float(chi[0]), chi2=float(chi[1]), ra=ra, dec=dec, psi=psi, iota=iota, tc=0.0,
+                              phic=phic),
+                         gmst, snr, noise_seed=(seed << 8) + 2 * e + 1, draw_seed=(seed << 8) + 2 * e + 2)
+        if bns:
+            w = Workload(f"uneven_{e}_bns", dets, 20.0, 1024.0, df, [MC, Q, CHI1, CHI2, TC],
+                         MARG_PHASE | MARG_DISTANCE, n_samples, "mixed", "c64", 1.5, PRIOR_M1M2, 0.05, [spec])
+        else:
+            w = Workload(f"uneven_{e}_heavy", dets, 20.0, 512.0, df, [MC, Q, CHI1, CHI2], MARG_PHASE, n_samples,
+                         "mixed", "c64", 1.5, 0, 0.5, [spec])
+        out.append(w)
+    return out
+
+
 def scaled(w: Workload, n_events=None, n_samples=None, f_hi=None):
     """A copy of a workload with fewer events, fewer samples or a shorter band (for the
     oracle-sized parity cases)."""
