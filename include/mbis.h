@@ -246,6 +246,85 @@ mbis_status mbis_batch_copy_out(mbis_batch* b, int32_t i, double* theta_host, do
 
 void mbis_batch_destroy(mbis_batch* b);
 
+/* ---- served stream: requests run to a target ESS with continuous admission ---------- */
+
+typedef struct mbis_server mbis_server;
+
+typedef struct {
+  int64_t hbm_cap_bytes;  /* admission cap on the summed device footprint of admitted requests */
+  int32_t max_active;     /* requests on the device at once (1..256); each has its own stream */
+  int32_t device;         /* CUDA device the server's worker thread uses */
+} mbis_server_options;
+
+/* One parameter-estimation request: an event (as for mbis_create), its proposal (as for
+ * mbis_set_metric) and the ESS-target loop options (as for mbis_run_to_ess).  Every host
+ * array is deep-copied by mbis_server_submit. */
+typedef struct {
+  mbis_event event;
+  const double* psd;          /* host, [n_det][n_bins] */
+  const mbis_detector* dets;  /* host, n_det */
+  mbis_freq_grid grid;
+  mbis_options opts;
+  int32_t P;
+  const int32_t* ids;         /* host, P */
+  const double* mean;         /* host, P */
+  const double* chol;         /* host, P x P lower, row-major */
+  double scale;
+  const double* lo;           /* host, P */
+  const double* hi;           /* host, P */
+  uint32_t prior_flags;
+  mbis_ess_options ess;
+  uint64_t tag;               /* returned unchanged in the result */
+} mbis_request;
+
+typedef struct {
+  uint64_t id, tag;
+  int32_t status;             /* mbis_status of the request */
+  int32_t pad;
+  mbis_summary summary;       /* as mbis_run_to_ess */
+  int64_t n_drawn, n_used;
+  double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock */
+  int64_t footprint_bytes;    /* device bytes reserved for the request while it ran */
+  char message[160];          /* error message when status != MBIS_OK */
+} mbis_result;
+
+typedef struct {
+  int64_t submitted, queued, active, completed, failed;
+  int64_t bytes_in_use, bytes_peak, bytes_cap;
+  int32_t max_active_seen;    /* most requests on the device at one time */
+  int32_t pad;
+} mbis_server_stats;
+
+/* Not in the paper: the paper runs one event at a time.  A served stream admits requests
+ * first-in first-out as soon as a slot is free and the request's device footprint fits
+ * under hbm_cap_bytes beside the requests already admitted; admitted requests keep their
+ * data, PSD, tables and proposal resident and run the ESS-target loop of mbis_run_to_ess
+ * one batch at a time on their own streams, so the batches of different requests overlap
+ * on the device.  Each request's arithmetic is that of mbis_run_to_ess on the same inputs:
+ * its result does not depend on what else runs.  A background thread does the work.
+ * Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_server_create(const mbis_server_options* opts, mbis_server** out);
+
+/* Queue a request (returns at once).  *id (host) identifies its result.  A request whose
+ * footprint alone exceeds hbm_cap_bytes, or that mbis_create / mbis_set_metric would
+ * reject, fails here with MBIS_E_INVALID.  *footprint_out (host, nullable): the bytes the
+ * request reserves. */
+mbis_status mbis_server_submit(mbis_server* s, const mbis_request* req, uint64_t* id, int64_t* footprint_out);
+
+/* Wait up to timeout_s seconds (< 0: forever) for request id; on success *out holds its
+ * result and the server forgets it.  MBIS_E_TIMEOUT when it is not done in time,
+ * MBIS_E_INVALID for an unknown id. */
+mbis_status mbis_server_wait(mbis_server* s, uint64_t id, double timeout_s, mbis_result* out);
+
+/* Up to max finished results not yet taken, oldest first; *n_out how many were written. */
+mbis_status mbis_server_poll(mbis_server* s, mbis_result* out, int32_t max, int32_t* n_out);
+
+mbis_status mbis_server_stats_get(mbis_server* s, mbis_server_stats* out);
+
+/* Requests still queued are dropped; those on the device finish their batch in flight and
+ * are released; then the worker stops and every resource is freed. */
+void mbis_server_destroy(mbis_server* s);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

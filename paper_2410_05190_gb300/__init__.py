@@ -60,6 +60,44 @@ class Summary(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class EssOptions(C.Structure):
+    _fields_ = [("ess_target", C.c_double), ("batch", C.c_int64), ("max_samples", C.c_int64), ("refine", C.c_int32),
+                ("refine_scale", C.c_double), ("seed", C.c_uint64)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_cap_bytes", C.c_int64), ("max_active", C.c_int32), ("device", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("event", Event), ("psd", C.c_void_p), ("dets", C.c_void_p), ("grid", FreqGrid), ("opts", Options),
+                ("P", C.c_int32), ("ids", C.c_void_p), ("mean", C.c_void_p), ("chol", C.c_void_p),
+                ("scale", C.c_double), ("lo", C.c_void_p), ("hi", C.c_void_p), ("prior_flags", C.c_uint32),
+                ("ess", EssOptions), ("tag", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32), ("pad", C.c_int32),
+                ("summary", Summary), ("n_drawn", C.c_int64), ("n_used", C.c_int64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("footprint_bytes", C.c_int64),
+                ("message", C.c_char * 160)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "summary", "message")}
+        d["summary"] = self.summary.as_dict()
+        d["message"] = self.message.decode(errors="replace")
+        return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("bytes_in_use", C.c_int64), ("bytes_peak", C.c_int64),
+                ("bytes_cap", C.c_int64), ("max_active_seen", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
@@ -86,7 +124,14 @@ def _load():
         "mbis_batch_loglike": [p, p],
         "mbis_batch_buffers": [p, i32, p, p],
         "mbis_batch_copy_out": [p, i32, p, p],
+        "mbis_server_create": [p, p],
+        "mbis_server_submit": [p, p, p, p],
+        "mbis_server_wait": [p, u64, d, p],
+        "mbis_server_poll": [p, p, i32, p],
+        "mbis_server_stats_get": [p, p],
     }
+    lib.mbis_server_destroy.restype = None
+    lib.mbis_server_destroy.argtypes = [p]
     lib.mbis_batch_destroy.restype = None
     lib.mbis_batch_destroy.argtypes = [p]
     for name, args in sigs.items():
@@ -196,11 +241,6 @@ def mbis_reduce(ctx, n, loglike, log_prior, log_q, weights_out=None, accumulate=
     return out.as_dict()
 
 
-class EssOptions(C.Structure):
-    _fields_ = [("ess_target", C.c_double), ("batch", C.c_int64), ("max_samples", C.c_int64), ("refine", C.c_int32),
-                ("refine_scale", C.c_double), ("seed", C.c_uint64)]
-
-
 def mbis_weighted_moments(ctx, n, theta, weights, stream=None):
     """Returns (mean [P], covariance [P, P]) of the weighted samples."""
     P = len(theta) if not isinstance(theta, int) else None
@@ -271,6 +311,65 @@ def mbis_batch_copy_out(b, i, P, n):
 
 def mbis_batch_destroy(b):
     _lib.mbis_batch_destroy(b)
+
+
+def mbis_server_create(hbm_cap_bytes=150 * 10**9, max_active=8, device=0):
+    out = C.c_void_p()
+    opts = ServerOptions(int(hbm_cap_bytes), max_active, device)
+    _check(_lib.mbis_server_create(C.byref(opts), C.byref(out)))
+    return out.value
+
+
+def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_ids, mean, chol_lower, scale,
+                       prior_lo, prior_hi, prior_flags=0, gmst=0.0, precision=MIXED, marg=MARG_PHASE, n_tshift=128,
+                       dt_shift=1e-4, dmin=10.0, dmax=1000.0, ess_target=1e4, batch=1 << 16, max_samples=1 << 24,
+                       seed=0, refine=0, refine_scale=0.0, tag=0):
+    """Queue one request (the arguments of mbis_create, mbis_set_metric and
+    mbis_run_to_ess).  Returns (request id, footprint bytes)."""
+    strain = np.ascontiguousarray(strain)
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    if strain.dtype == np.complex128:
+        dtype = C128
+    elif strain.dtype == np.complex64:
+        dtype = C64
+    else:
+        raise TypeError("strain must be complex128 or complex64")
+    n_det, n_bins = strain.shape
+    ids, pid = _host(param_ids, np.int32)
+    m, pm = _host(mean, np.float64)
+    L, pL = _host(chol_lower, np.float64)
+    lo, plo = _host(prior_lo, np.float64)
+    hi, phi = _host(prior_hi, np.float64)
+    req = Request(Event(n_det, dtype, strain.ctypes.data, gmst, (C.c_double * 11)(*map(float, fixed))),
+                  psd.ctypes.data, C.cast(detectors, C.c_void_p), FreqGrid(f_lo, df, n_bins),
+                  Options(precision, marg, n_tshift, dt_shift, dmin, dmax, 0), len(ids), pid, pm, pL, scale, plo, phi,
+                  prior_flags, EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed), tag)
+    rid, fp = C.c_uint64(), C.c_int64()
+    _check(_lib.mbis_server_submit(server, C.byref(req), C.byref(rid), C.byref(fp)))
+    return rid.value, fp.value
+
+
+def mbis_server_wait(server, rid, timeout=-1.0):
+    out = Result()
+    _check(_lib.mbis_server_wait(server, rid, timeout, C.byref(out)))
+    return out.as_dict()
+
+
+def mbis_server_poll(server, max_results=64):
+    out = (Result * max_results)()
+    n = C.c_int32()
+    _check(_lib.mbis_server_poll(server, out, max_results, C.byref(n)))
+    return [out[i].as_dict() for i in range(n.value)]
+
+
+def mbis_server_stats_get(server):
+    out = ServerStats()
+    _check(_lib.mbis_server_stats_get(server, C.byref(out)))
+    return out.as_dict()
+
+
+def mbis_server_destroy(server):
+    _lib.mbis_server_destroy(server)
 
 
 NOALLOC_MAX_SAMPLES = 16777216

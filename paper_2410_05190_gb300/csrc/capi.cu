@@ -30,9 +30,34 @@ mbis_status fail(mbis_ctx* ctx, mbis_status st, const std::string& msg) {
     }                                                                                            \
   } while (0)
 
+// Device memory of a context: stream-ordered from the context's pool when it has one
+// (no device-wide synchronisation), plain cudaMalloc / cudaFree otherwise.
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+cudaError_t dalloc(mbis_ctx* c, T** p, size_t bytes) {
+  void* q = nullptr;
+  const cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&q, bytes, c->pool, c->stream) : cudaMalloc(&q, bytes);
+  if (e == cudaSuccess) {
+    *p = static_cast<T*>(q);
+    c->dev_bytes += bytes;
+    c->dev_peak = std::max(c->dev_peak, c->dev_bytes);
+    c->allocs.push_back({q, bytes});
+  }
+  return e;
+}
+
+template <typename T>
+void dfree(mbis_ctx* c, T*& p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i].first == (void*)p) {
+      c->dev_bytes -= c->allocs[i].second;
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  if (c->pool)
+    cudaFreeAsync((void*)p, c->stream);
+  else
+    cudaFree((void*)p);
   p = nullptr;
 }
 
@@ -56,15 +81,15 @@ double q_integral(double a, double b) {
 }
 
 void free_tables(mbis_ctx* c) {
-  dfree(c->d_cfold64);
-  dfree(c->d_tfold);
-  dfree(c->d_cdet64);
-  dfree(c->d_tdet);
-  dfree(c->d_cfold32);
-  dfree(c->d_twiddle);
-  dfree(c->d_cdet32);
-  dfree(c->d_ttiles);
-  dfree(c->d_plan);
+  dfree(c, c->d_cfold64);
+  dfree(c, c->d_tfold);
+  dfree(c, c->d_cdet64);
+  dfree(c, c->d_tdet);
+  dfree(c, c->d_cfold32);
+  dfree(c, c->d_twiddle);
+  dfree(c, c->d_cdet32);
+  dfree(c, c->d_ttiles);
+  dfree(c, c->d_plan);
   c->n_blocks = 0;
   c->tables_mode = -1;
 }
@@ -117,20 +142,20 @@ mbis_status build_tables(mbis_ctx* c) {
   free_tables(c);
   ++c->gen;
   const int32_t n = c->n_bins, nd = c->n_det;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = c->stream;
   double* d_w = nullptr;
   if (fold) {
     DetResponse det[kMaxDet];
     for (int d = 0; d < nd; ++d) det[d] = response_of(c, d);
-    CU_TRY(c, cudaMalloc(&c->d_cfold64, sizeof(double2) * n));
-    CU_TRY(c, cudaMalloc(&c->d_tfold, sizeof(double) * (n + 1)));
-    CU_TRY(c, cudaMalloc(&d_w, sizeof(double) * n));
+    CU_TRY(c, dalloc(c, &c->d_cfold64, sizeof(double2) * n));
+    CU_TRY(c, dalloc(c, &c->d_tfold, sizeof(double) * (n + 1)));
+    CU_TRY(c, dalloc(c, &d_w, sizeof(double) * n));
     CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 1, det, c->d_cfold64, d_w, s));
     CU_TRY(c, launch_prefix_rows(d_w, 1, n, c->d_tfold, s));
   } else {
-    CU_TRY(c, cudaMalloc(&c->d_cdet64, sizeof(double2) * (size_t)n * nd));
-    CU_TRY(c, cudaMalloc(&c->d_tdet, sizeof(double) * (size_t)(n + 1) * nd));
-    CU_TRY(c, cudaMalloc(&d_w, sizeof(double) * (size_t)n * nd));
+    CU_TRY(c, dalloc(c, &c->d_cdet64, sizeof(double2) * (size_t)n * nd));
+    CU_TRY(c, dalloc(c, &c->d_tdet, sizeof(double) * (size_t)(n + 1) * nd));
+    CU_TRY(c, dalloc(c, &d_w, sizeof(double) * (size_t)n * nd));
     CU_TRY(c, launch_event_tables(nd, n, c->f_lo, c->df, c->dtype, c->d_strain, c->d_psd64, 0, nullptr, c->d_cdet64,
                                   d_w, s));
     CU_TRY(c, launch_prefix_rows(d_w, nd, n, c->d_tdet, s));
@@ -140,24 +165,25 @@ mbis_status build_tables(mbis_ctx* c) {
     const double2* src = fold ? c->d_cfold64 : c->d_cdet64;
     const int32_t rows = fold ? 1 : nd;
     double* d_max = nullptr;
-    CU_TRY(c, cudaMalloc(&d_max, sizeof(double)));
+    CU_TRY(c, dalloc(c, &d_max, sizeof(double)));
     CU_TRY(c, launch_max_abs(src, n * rows, d_max, s));
     double mx = 0.0;
-    CU_TRY(c, cudaMemcpy(&mx, d_max, sizeof(double), cudaMemcpyDeviceToHost));
-    cudaFree(d_max);
+    CU_TRY(c, cudaMemcpyAsync(&mx, d_max, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU_TRY(c, cudaStreamSynchronize(s));
+    dfree(c, d_max);
     c->cscale = (mx > 0.0 && std::isfinite(mx)) ? std::ldexp(1.0, std::ilogb(mx) + 1) : 1.0;
     if (c->opts.marg & MBIS_MARG_TIME) {
       c->n_pad16 = (n + kKBlockBins - 1) / kKBlockBins * kKBlockBins;
       c->n_kb = c->n_pad16 / kKBlockBins;
-      CU_TRY(c, cudaMalloc(&c->d_cdet32, sizeof(float2) * (size_t)c->n_pad16 * rows));
+      CU_TRY(c, dalloc(c, &c->d_cdet32, sizeof(float2) * (size_t)c->n_pad16 * rows));
       CU_TRY(c, launch_rows_to_f32(src, rows, n, c->n_pad16, 1.0 / c->cscale, c->d_cdet32, s));
       if (c->opts.n_tshift == kTimeShifts) {
-        CU_TRY(c, cudaMalloc(&c->d_ttiles, sizeof(float) * (size_t)c->n_kb * 2 * 4096));
+        CU_TRY(c, dalloc(c, &c->d_ttiles, sizeof(float) * (size_t)c->n_kb * 2 * 4096));
         CU_TRY(c, launch_twiddle_tiles(n, c->f_lo, c->df, c->opts.dt_shift, c->n_kb, c->d_ttiles, s));
       }
     } else if (fold) {
       const int32_t n_pad = (n + kChunk - 1) / kChunk * kChunk;
-      CU_TRY(c, cudaMalloc(&c->d_cfold32, sizeof(float4) * (n_pad / 2)));
+      CU_TRY(c, dalloc(c, &c->d_cfold32, sizeof(float4) * (n_pad / 2)));
       CU_TRY(c, launch_to_f32(c->d_cfold64, n, n_pad, 1.0 / c->cscale, c->d_cfold32, s));
     }
     PlanInput pin;
@@ -170,15 +196,16 @@ mbis_status build_tables(mbis_ctx* c) {
     pin.max_block = 4096;
     const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
     c->n_blocks = (int32_t)plan.size();
-    CU_TRY(c, cudaMalloc(&c->d_plan, sizeof(AnchorBlock) * plan.size()));
-    CU_TRY(c, cudaMemcpy(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice));
+    CU_TRY(c, dalloc(c, &c->d_plan, sizeof(AnchorBlock) * plan.size()));
+    CU_TRY(c, cudaMemcpyAsync(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice, s));
+    CU_TRY(c, cudaStreamSynchronize(s));  // the host plan goes out of scope
   }
   if ((c->opts.marg & MBIS_MARG_TIME) && c->opts.precision == MBIS_FP64) {
-    CU_TRY(c, cudaMalloc(&c->d_twiddle, sizeof(double2) * (size_t)n * c->opts.n_tshift));
+    CU_TRY(c, dalloc(c, &c->d_twiddle, sizeof(double2) * (size_t)n * c->opts.n_tshift));
     CU_TRY(c, launch_twiddles(n, c->f_lo, c->df, c->opts.n_tshift, c->opts.dt_shift, c->d_twiddle, s));
   }
-  CU_TRY(c, cudaDeviceSynchronize());
-  cudaFree(d_w);
+  CU_TRY(c, c->pool ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+  dfree(c, d_w);
   c->tables_mode = fold ? 1 : 0;
   return MBIS_OK;
 }
@@ -284,14 +311,8 @@ LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, doubl
 }
 }  // namespace mbis
 
-extern "C" {
-
-const char* mbis_version(void) { return "mbis 0.1 (sm_103a)"; }
-
-const char* mbis_last_error(const mbis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
-
-mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_detector* dets, const mbis_freq_grid* grid,
-                        const mbis_options* opts, mbis_ctx** out) {
+mbis_status mbis::create_ctx(const mbis_event* ev, const double* psd, const mbis_detector* dets,
+                             const mbis_freq_grid* grid, const mbis_options* opts, const CtxEnv& env, mbis_ctx** out) {
   if (out) *out = nullptr;
   if (!ev || !psd || !dets || !grid || !opts || !out || !ev->strain)
     return fail(nullptr, MBIS_E_INVALID, "mbis_create: null argument");
@@ -320,6 +341,8 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
   std::memcpy(c->fixed, ev->fixed, sizeof(c->fixed));
   std::memcpy(c->dets, dets, sizeof(mbis_detector) * ev->n_det);
   c->opts = *opts;
+  c->stream = env.stream;
+  c->pool = env.pool;
   auto bail = [&](mbis_status st) {
     std::string m = c->err;
     mbis_destroy(c);
@@ -329,6 +352,7 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
   cudaGetDevice(&c->device);
   const size_t nb = (size_t)c->n_bins * c->n_det;
   const size_t csz = ev->dtype == MBIS_C128 ? 16 : 8;
+  cudaStream_t s = c->stream;
   cudaError_t e;
 #define CREATE_TRY(call)                                                                                 \
   if ((e = (call)) != cudaSuccess) {                                                                     \
@@ -336,55 +360,242 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
                                                                         cudaGetErrorString(e));          \
     return bail(e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA);                              \
   }
-  CREATE_TRY(cudaMalloc(&c->d_strain, csz * nb));
-  CREATE_TRY(cudaMemcpy(c->d_strain, ev->strain, csz * nb, cudaMemcpyHostToDevice));
+  CREATE_TRY(dalloc(c, &c->d_strain, csz * nb));
+  CREATE_TRY(cudaMemcpyAsync(c->d_strain, ev->strain, csz * nb, cudaMemcpyHostToDevice, s));
   for (size_t i = 0; i < nb; ++i)
     if (!(psd[i] > 0.0) || !std::isfinite(psd[i])) {
       fail(c, MBIS_E_INVALID, "mbis_create: PSD must be positive and finite");
       return bail(MBIS_E_INVALID);
     }
-  CREATE_TRY(cudaMalloc(&c->d_psd64, sizeof(double) * nb));
-  CREATE_TRY(cudaMemcpy(c->d_psd64, psd, sizeof(double) * nb, cudaMemcpyHostToDevice));
-  CREATE_TRY(cudaMalloc(&c->d_basis, sizeof(double) * kNumBasis * (size_t)c->n_bins));
-  CREATE_TRY(launch_basis_table(c->f_lo, c->df, c->n_bins, c->d_basis, nullptr));
+  CREATE_TRY(dalloc(c, &c->d_psd64, sizeof(double) * nb));
+  CREATE_TRY(cudaMemcpyAsync(c->d_psd64, psd, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  CREATE_TRY(dalloc(c, &c->d_basis, sizeof(double) * kNumBasis * (size_t)c->n_bins));
+  CREATE_TRY(launch_basis_table(c->f_lo, c->df, c->n_bins, c->d_basis, s));
   {
     double gl[kGLSize];
     fill_gauss_legendre(gl);
-    CREATE_TRY(cudaMalloc(&c->d_gl, sizeof(gl)));
-    CREATE_TRY(cudaMemcpy(c->d_gl, gl, sizeof(gl), cudaMemcpyHostToDevice));
+    CREATE_TRY(dalloc(c, &c->d_gl, sizeof(gl)));
+    CREATE_TRY(cudaMemcpyAsync(c->d_gl, gl, sizeof(gl), cudaMemcpyHostToDevice, s));
+    CREATE_TRY(cudaStreamSynchronize(s));  // gl is on this stack frame
   }
-  CREATE_TRY(cudaMalloc(&c->d_err, sizeof(int32_t)));
-  CREATE_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
-  CREATE_TRY(cudaMalloc(&c->red.partials, sizeof(double) * 2 * kReduceBlocks));
-  CREATE_TRY(cudaMalloc(&c->red.counter, sizeof(unsigned int)));
-  CREATE_TRY(cudaMemset(c->red.counter, 0, sizeof(unsigned int)));
-  CREATE_TRY(cudaMalloc(&c->red.result, sizeof(double) * 4));
-  CREATE_TRY(cudaMallocHost(&c->h_result, sizeof(double) * 5));
-  CREATE_TRY(cudaMalloc(&c->d_mom_partials, sizeof(double) * moments_partials_size(kMaxP)));
-  CREATE_TRY(cudaMalloc(&c->d_mom_counter, sizeof(unsigned int)));
-  CREATE_TRY(cudaMemset(c->d_mom_counter, 0, sizeof(unsigned int)));
-  CREATE_TRY(cudaMalloc(&c->d_mom_out, sizeof(double) * (1 + kMaxP + kMaxP * (kMaxP + 1) / 2)));
-  CREATE_TRY(cudaDeviceSynchronize());
+  CREATE_TRY(dalloc(c, &c->d_err, sizeof(int32_t)));
+  CREATE_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
+  CREATE_TRY(dalloc(c, &c->red.partials, sizeof(double) * 2 * kReduceBlocks));
+  CREATE_TRY(dalloc(c, &c->red.counter, sizeof(unsigned int)));
+  CREATE_TRY(cudaMemsetAsync(c->red.counter, 0, sizeof(unsigned int), s));
+  CREATE_TRY(dalloc(c, &c->red.result, sizeof(double) * 4));
+  if (env.h_scratch) {
+    c->h_result = env.h_scratch;
+    c->own_host = false;
+  } else {
+    CREATE_TRY(cudaMallocHost(&c->h_result, sizeof(double) * kHostScratch));
+  }
+  CREATE_TRY(dalloc(c, &c->d_mom_partials, sizeof(double) * moments_partials_size(kMaxP)));
+  CREATE_TRY(dalloc(c, &c->d_mom_counter, sizeof(unsigned int)));
+  CREATE_TRY(cudaMemsetAsync(c->d_mom_counter, 0, sizeof(unsigned int), s));
+  CREATE_TRY(dalloc(c, &c->d_mom_out, sizeof(double) * kMomentSums));
+  CREATE_TRY(c->pool ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
 #undef CREATE_TRY
   *out = c;
   return MBIS_OK;
 }
 
+
+namespace {
+
+MomentArgs moment_args(const mbis_ctx* c) {
+  MomentArgs ma = {};
+  for (int p = 0; p < c->P; ++p) {
+    ma.ref[p] = c->mean[p];
+    ma.period[p] = c->ids[p] == kPsi ? kPi : (c->ids[p] == kRa || c->ids[p] == kPhic) ? kTwoPi : 0.0;
+  }
+  return ma;
+}
+
+// mean and covariance from the weighted sums [sum w, sum w d_p, sum w d_p d_q (p <= q)] of the
+// offsets d from the reference point ma.ref; false when no weight is positive
+bool moments_from_sums(const mbis_ctx* c, const MomentArgs& ma, const double* h, double* mean_out, double* cov_out) {
+  const int32_t P = c->P;
+  const double wsum = h[0];
+  if (!(wsum > 0.0)) return false;
+  int m = 1;
+  double d[kMaxP];
+  for (int p = 0; p < P; ++p) d[p] = h[m++] / wsum;
+  for (int p = 0; p < P; ++p)
+    for (int q = p; q < P; ++q) {
+      const double v = h[m++] / wsum - d[p] * d[q];
+      cov_out[p * P + q] = v;
+      cov_out[q * P + p] = v;
+    }
+  for (int p = 0; p < P; ++p) {
+    double x = ma.ref[p] + d[p];
+    if (ma.period[p] > 0.0) x -= ma.period[p] * floor(x / ma.period[p]);
+    mean_out[p] = x;
+  }
+  return true;
+}
+
+// lower Cholesky factor (row-major P x P, upper part zero); false when cov is not positive definite
+bool host_cholesky(int32_t P, const double* cov, double* L) {
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double sum = cov[i * P + j];
+      for (int k = 0; k < j; ++k) sum -= L[i * P + k] * L[j * P + k];
+      if (i == j) {
+        if (!(sum > 0.0)) return false;
+        L[i * P + i] = sqrt(sum);
+      } else {
+        L[i * P + j] = sum / L[j * P + j];
+      }
+    }
+  for (int i = 0; i < P; ++i)
+    for (int j = i + 1; j < P; ++j) L[i * P + j] = 0.0;
+  return true;
+}
+
+size_t round_alloc(size_t b) { return (b + 511) / 512 * 512; }
+
+}  // namespace
+
+size_t mbis::ctx_footprint_bytes(int32_t n_det, int32_t n_bins, int32_t dtype, const mbis_options& opts, bool fold) {
+  const size_t n = (size_t)n_bins, nd = (size_t)n_det, nb = n * nd;
+  size_t t = 0;
+  t += round_alloc((dtype == MBIS_C128 ? 16 : 8) * nb) + round_alloc(8 * nb);  // strain, PSD
+  t += round_alloc(8 * kNumBasis * n) + round_alloc(8 * kGLSize) + round_alloc(4);
+  t += round_alloc(16 * kReduceBlocks) + round_alloc(4) + round_alloc(32);
+  t += round_alloc(8 * (size_t)moments_partials_size(kMaxP)) + round_alloc(4) + round_alloc(8 * kMomentSums);
+  const size_t rows = fold ? 1 : nd;
+  t += round_alloc(16 * n * rows) + round_alloc(8 * (n + 1) * rows) + round_alloc(8 * n * rows);  // C, T, scratch
+  if (opts.precision == MBIS_MIXED) {
+    t += round_alloc(8);
+    if (opts.marg & MBIS_MARG_TIME) {
+      const size_t pad16 = (n + kKBlockBins - 1) / kKBlockBins * kKBlockBins;
+      t += round_alloc(8 * pad16 * rows);
+      if (opts.n_tshift == kTimeShifts) t += round_alloc(4 * (pad16 / kKBlockBins) * 2 * 4096);
+    } else if (fold) {
+      t += round_alloc(8 * ((n + kChunk - 1) / kChunk * kChunk));
+    }
+    t += round_alloc(sizeof(AnchorBlock) * (n / 2 + 2));  // the planner's blocks hold at least two bins
+  }
+  if ((opts.marg & MBIS_MARG_TIME) && opts.precision == MBIS_FP64) t += round_alloc(16 * n * (size_t)opts.n_tshift);
+  return t;
+}
+
+mbis_status mbis::ess_begin(mbis_ctx* c, const mbis_ess_options* o, EssState* st) {
+  if (!c || !o || !st) return fail(c, MBIS_E_INVALID, "ess: null argument");
+  if (!c->has_metric) return fail(c, MBIS_E_STATE, "ess: call mbis_set_metric first");
+  if (o->batch < 1 || o->max_samples < 1) return fail(c, MBIS_E_INVALID, "ess: batch and max_samples must be >= 1");
+  mbis_reset_running(c);
+  *st = EssState{};
+  st->o = *o;
+  st->refits_left = o->refine > 0 ? o->refine : 0;
+  return MBIS_OK;
+}
+
+mbis_status mbis::ess_issue(mbis_ctx* c, EssState* st, const EssBuffers& buf, cudaStream_t s) {
+  if (st->done) return fail(c, MBIS_E_STATE, "ess: the loop has finished");
+  st->nb = std::min<int64_t>(st->o.batch, st->o.max_samples - st->drawn);
+  st->refit = st->refits_left > 0;
+  const int64_t nb = st->nb;
+  const DrawArgs da = make_draw_args(c, st->o.seed, (uint64_t)(st->b * st->o.batch), nb, buf.theta, buf.log_q,
+                                     buf.log_prior);
+  CU_TRY(c, launch_draw(da, s));
+  mbis_status r = mbis_loglike(c, nb, buf.theta, buf.loglike, s);
+  if (r != MBIS_OK) return r;
+  CU_TRY(c, launch_reduce(nb, buf.loglike, buf.log_prior, buf.log_q, st->refit ? buf.weights : nullptr, c->red, s));
+  CU_TRY(c, cudaMemcpyAsync(c->h_result, c->red.result, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  CU_TRY(c, cudaMemcpyAsync(c->h_result + 4, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (st->refit) {
+    const MomentArgs ma = moment_args(c);
+    const int nm = 1 + c->P + c->P * (c->P + 1) / 2;
+    CU_TRY(c, launch_moments(nb, c->P, buf.theta, buf.weights, ma, c->d_mom_partials, c->d_mom_counter,
+                             c->d_mom_out, s));
+    CU_TRY(c, cudaMemcpyAsync(c->h_result + 8, c->d_mom_out, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  }
+  return MBIS_OK;
+}
+
+mbis_status mbis::ess_complete(mbis_ctx* c, EssState* st) {
+  int32_t derr;
+  std::memcpy(&derr, c->h_result + 4, sizeof(int32_t));
+  if (derr != 0) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
+    st->done = true;
+    return fail(c, MBIS_E_TIMEOUT, "a device-side wait timed out in a kernel of this context");
+  }
+  const int64_t nb = st->nb;
+  mbis_summary batch;
+  summary_from_state(c->h_result[0], c->h_result[1], c->h_result[2], nb, &batch);
+  st->drawn += nb;
+  ++st->b;
+  if (st->refit) {
+    --st->refits_left;
+    if (batch.ess >= 2.0 * c->P + 1.0) {
+      const MomentArgs ma = moment_args(c);
+      double mean[kMaxP], cov[kMaxP * kMaxP], L[kMaxP * kMaxP];
+      if (moments_from_sums(c, ma, c->h_result + 8, mean, cov) && host_cholesky(c->P, cov, L)) {
+        const mbis_status r =
+            mbis_set_proposal(c, mean, L, st->o.refine_scale > 0.0 ? st->o.refine_scale : c->scale);
+        if (r != MBIS_OK) {
+          st->done = true;
+          return r;
+        }
+      }
+    }
+    mbis_reset_running(c);
+    st->used = 0;
+    st->cur = mbis_summary{};
+  } else {
+    if (c->has_running) {
+      mbis_summary merged;
+      mbis_merge_summaries(&c->running, &batch, &merged);
+      c->running = merged;
+    } else {
+      c->running = batch;
+      c->has_running = true;
+    }
+    st->cur = c->running;
+    st->used += nb;
+    if (st->cur.ess >= st->o.ess_target) st->done = true;
+  }
+  if (st->drawn >= st->o.max_samples) st->done = true;
+  return MBIS_OK;
+}
+
+void mbis::ess_result(const EssState& st, mbis_summary* out, int64_t* n_drawn, int64_t* n_used) {
+  mbis_summary cur = st.cur;
+  if (st.used == 0) summary_from_state(-INFINITY, 0.0, 0.0, 0, &cur);
+  if (out) *out = cur;
+  if (n_drawn) *n_drawn = st.drawn;
+  if (n_used) *n_used = st.used;
+}
+
+extern "C" {
+
+const char* mbis_version(void) { return "mbis 0.1 (sm_103a)"; }
+
+const char* mbis_last_error(const mbis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_detector* dets, const mbis_freq_grid* grid,
+                        const mbis_options* opts, mbis_ctx** out) {
+  return create_ctx(ev, psd, dets, grid, opts, CtxEnv{}, out);
+}
+
 void mbis_destroy(mbis_ctx* c) {
   if (!c) return;
   free_tables(c);
-  dfree(c->d_strain);
-  dfree(c->d_psd64);
-  dfree(c->d_basis);
-  dfree(c->d_gl);
-  dfree(c->d_err);
-  dfree(c->red.partials);
-  dfree(c->red.counter);
-  dfree(c->red.result);
-  if (c->h_result) cudaFreeHost(c->h_result);
-  dfree(c->d_mom_partials);
-  dfree(c->d_mom_counter);
-  dfree(c->d_mom_out);
+  dfree(c, c->d_strain);
+  dfree(c, c->d_psd64);
+  dfree(c, c->d_basis);
+  dfree(c, c->d_gl);
+  dfree(c, c->d_err);
+  dfree(c, c->red.partials);
+  dfree(c, c->red.counter);
+  dfree(c, c->red.result);
+  if (c->h_result && c->own_host) cudaFreeHost(c->h_result);
+  dfree(c, c->d_mom_partials);
+  dfree(c, c->d_mom_counter);
+  dfree(c, c->d_mom_out);
   delete c;
 }
 
@@ -654,11 +865,7 @@ mbis_status mbis_weighted_moments(mbis_ctx* c, int64_t n, const double* theta, c
   if (n < 0 || !mean_out || !cov_out || (n > 0 && (!theta || !weights)))
     return fail(c, MBIS_E_INVALID, "mbis_weighted_moments: bad n or null buffer");
   const int32_t P = c->P, nm = 1 + P + P * (P + 1) / 2;
-  MomentArgs ma = {};
-  for (int p = 0; p < P; ++p) {
-    ma.ref[p] = c->mean[p];
-    ma.period[p] = c->ids[p] == kPsi ? kPi : (c->ids[p] == kRa || c->ids[p] == kPhic) ? kTwoPi : 0.0;
-  }
+  const MomentArgs ma = moment_args(c);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<double> h(nm, 0.0);
   if (n > 0) {
@@ -666,23 +873,8 @@ mbis_status mbis_weighted_moments(mbis_ctx* c, int64_t n, const double* theta, c
     CU_TRY(c, cudaMemcpyAsync(h.data(), c->d_mom_out, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
     CU_TRY(c, cudaStreamSynchronize(s));
   }
-  // normalise by the sum of the weights
-  const double wsum = h[0];
-  if (!(wsum > 0.0)) return fail(c, MBIS_E_INVALID, "mbis_weighted_moments: no positive weight");
-  int m = 1;
-  double d[kMaxP];
-  for (int p = 0; p < P; ++p) d[p] = h[m++] / wsum;
-  for (int p = 0; p < P; ++p)
-    for (int q = p; q < P; ++q) {
-      const double v = h[m++] / wsum - d[p] * d[q];
-      cov_out[p * P + q] = v;
-      cov_out[q * P + p] = v;
-    }
-  for (int p = 0; p < P; ++p) {
-    double x = c->mean[p] + d[p];
-    if (ma.period[p] > 0.0) x -= ma.period[p] * floor(x / ma.period[p]);
-    mean_out[p] = x;
-  }
+  if (!moments_from_sums(c, ma, h.data(), mean_out, cov_out))
+    return fail(c, MBIS_E_INVALID, "mbis_weighted_moments: no positive weight");
   return MBIS_OK;
 }
 
@@ -708,66 +900,19 @@ mbis_status mbis_run_to_ess(mbis_ctx* c, const mbis_ess_options* o, double* thet
                             double* loglike, double* weights, mbis_summary* out, int64_t* n_drawn, int64_t* n_used,
                             void* stream) {
   if (!c || !o || !out) return fail(c, MBIS_E_INVALID, "mbis_run_to_ess: null argument");
-  if (!c->has_metric) return fail(c, MBIS_E_STATE, "mbis_run_to_ess: call mbis_set_metric first");
-  if (o->batch < 1 || o->max_samples < 1 || !theta || !log_q || !log_prior || !loglike || !weights)
-    return fail(c, MBIS_E_INVALID, "mbis_run_to_ess: batch and max_samples must be >= 1, buffers non-null");
-  const int32_t P = c->P;
-  mbis_reset_running(c);
-  int64_t drawn = 0, used = 0;
-  int refits_left = o->refine > 0 ? o->refine : 0;
-  mbis_summary cur = {};
-  for (int64_t b = 0; drawn < o->max_samples; ++b) {
-    const int64_t nb = std::min<int64_t>(o->batch, o->max_samples - drawn);
-    mbis_status st = mbis_draw(c, o->seed, (uint64_t)(b * o->batch), nb, theta, log_q, log_prior, stream);
-    if (st == MBIS_OK) st = mbis_loglike(c, nb, theta, loglike, stream);
-    if (st != MBIS_OK) return st;
-    drawn += nb;
-    if (refits_left > 0) {
-      mbis_summary bs;
-      st = mbis_reduce(c, nb, loglike, log_prior, log_q, weights, 0, &bs, stream);
-      if (st != MBIS_OK) return st;
-      --refits_left;
-      if (bs.ess >= 2.0 * P + 1.0) {
-        double mean[kMaxP], cov[kMaxP * kMaxP], L[kMaxP * kMaxP];
-        st = mbis_weighted_moments(c, nb, theta, weights, mean, cov, stream);
-        if (st != MBIS_OK) return st;
-        // Cholesky of the weighted covariance (a small diagonal jitter if it is not positive)
-        bool okc = true;
-        for (int i = 0; i < P && okc; ++i)
-          for (int j = 0; j <= i; ++j) {
-            double sum = cov[i * P + j];
-            for (int k = 0; k < j; ++k) sum -= L[i * P + k] * L[j * P + k];
-            if (i == j) {
-              if (!(sum > 0.0)) {
-                okc = false;
-                break;
-              }
-              L[i * P + i] = sqrt(sum);
-            } else {
-              L[i * P + j] = sum / L[j * P + j];
-            }
-          }
-        if (okc) {
-          for (int i = 0; i < P; ++i)
-            for (int j = i + 1; j < P; ++j) L[i * P + j] = 0.0;
-          st = mbis_set_proposal(c, mean, L, o->refine_scale > 0.0 ? o->refine_scale : c->scale);
-          if (st != MBIS_OK) return st;
-        }
-      }
-      mbis_reset_running(c);
-      used = 0;
-      cur = mbis_summary{};
-      continue;
-    }
-    st = mbis_reduce(c, nb, loglike, log_prior, log_q, nullptr, 1, &cur, stream);
-    if (st != MBIS_OK) return st;
-    used += nb;
-    if (cur.ess >= o->ess_target) break;
+  if (!theta || !log_q || !log_prior || !loglike || !weights)
+    return fail(c, MBIS_E_INVALID, "mbis_run_to_ess: null buffer");
+  EssState st;
+  mbis_status r = ess_begin(c, o, &st);
+  if (r != MBIS_OK) return r;
+  const EssBuffers buf = {theta, log_q, log_prior, loglike, weights};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  while (!st.done) {
+    if ((r = ess_issue(c, &st, buf, s)) != MBIS_OK) return r;
+    CU_TRY(c, cudaStreamSynchronize(s));
+    if ((r = ess_complete(c, &st)) != MBIS_OK) return r;
   }
-  if (used == 0) summary_from_state(-INFINITY, 0.0, 0.0, 0, &cur);
-  *out = cur;
-  if (n_drawn) *n_drawn = drawn;
-  if (n_used) *n_used = used;
+  ess_result(st, out, n_drawn, n_used);
   return MBIS_OK;
 }
 

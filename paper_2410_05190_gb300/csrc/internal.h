@@ -162,6 +162,39 @@ void set_last_error(const std::string& msg);
 
 struct mbis_ctx;
 namespace mbis {
+constexpr int kHostScratch = 8 + 1 + kMaxP + kMaxP * (kMaxP + 1) / 2;
+constexpr int kMomentSums = 1 + kMaxP + kMaxP * (kMaxP + 1) / 2;
+
+// where a context's memory comes from (defaults: plain cudaMalloc, legacy stream, own pinned scratch)
+struct CtxEnv {
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  double* h_scratch = nullptr;  // caller-owned pinned host memory of kHostScratch doubles, or null
+};
+mbis_status create_ctx(const mbis_event* ev, const double* psd, const mbis_detector* dets,
+                       const mbis_freq_grid* grid, const mbis_options* opts, const CtxEnv& env, mbis_ctx** out);
+// upper bound on the device bytes of a context (tables for a proposal over the given slots)
+size_t ctx_footprint_bytes(int32_t n_det, int32_t n_bins, int32_t dtype, const mbis_options& opts, bool fold);
+
+// The ESS-target loop as a state machine: issue() enqueues one batch (draws, likelihoods,
+// weights, and for refit batches the weighted moments) on a stream without waiting;
+// complete() reads its results once the stream has finished it.
+struct EssBuffers {
+  double *theta, *log_q, *log_prior, *loglike, *weights;
+};
+struct EssState {
+  mbis_ess_options o = {};
+  int64_t b = 0, drawn = 0, used = 0, nb = 0;
+  int refits_left = 0;
+  bool refit = false;  // the batch in flight adapts the proposal
+  bool done = false;
+  mbis_summary cur = {};
+};
+mbis_status ess_begin(mbis_ctx* c, const mbis_ess_options* o, EssState* st);
+mbis_status ess_issue(mbis_ctx* c, EssState* st, const EssBuffers& buf, cudaStream_t s);
+mbis_status ess_complete(mbis_ctx* c, EssState* st);
+void ess_result(const EssState& st, mbis_summary* out, int64_t* n_drawn, int64_t* n_used);
+
 DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
                         double* log_prior);
 LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, double* loglike);
@@ -175,6 +208,14 @@ struct mbis_ctx {
   mbis_detector dets[mbis::kMaxDet] = {};
   mbis_options opts = {};
   int device = 0;
+  // allocation environment: with a pool, device memory is stream-ordered on `stream` and
+  // nothing in the context's life synchronises the whole device
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  bool own_host = true;   // h_result allocated (pinned) by the context
+  size_t dev_bytes = 0;   // device bytes the context holds
+  size_t dev_peak = 0;    // high-water mark of dev_bytes
+  std::vector<std::pair<void*, size_t>> allocs;
   void* d_strain = nullptr;
   double* d_psd64 = nullptr;  // [n_det][n_bins]
   // proposal
@@ -205,7 +246,8 @@ struct mbis_ctx {
   double* d_gl = nullptr;
   // reduction scratch
   mbis::ReduceScratch red = {};
-  double* h_result = nullptr;  // pinned, 4 doubles
+  double* h_result = nullptr;  // pinned host scratch, kHostScratch doubles: [0..3] reduction, [4] error word,
+                               // [8..] weighted-moment sums
   // weighted-moment scratch (proposal refits)
   double* d_mom_partials = nullptr;
   unsigned int* d_mom_counter = nullptr;

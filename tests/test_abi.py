@@ -44,3 +44,33 @@ def test_binding_imports_and_reports_errors_without_a_device():
     assert e.value.status == m.MBIS_E_INVALID
     psd = m.mbis_psd_aligo(20.0, 0.25, 5)
     assert psd.shape == (5,) and (psd > 0).all()
+
+
+def test_binding_structures_match_the_header_layout():
+    """Every ctypes structure of the binding has the size and field offsets that the C
+    compiler gives the header's struct (compiled here with gcc; no device needed)."""
+    import paper_2410_05190_gb300 as m
+    pairs = {"mbis_freq_grid": m.FreqGrid, "mbis_detector": m.Detector, "mbis_event": m.Event,
+             "mbis_options": m.Options, "mbis_summary": m.Summary, "mbis_ess_options": m.EssOptions,
+             "mbis_server_options": m.ServerOptions, "mbis_request": m.Request, "mbis_result": m.Result,
+             "mbis_server_stats": m.ServerStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mbis.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    build = os.path.join(ROOT, "paper_2410_05190_gb300", "_build")
+    os.makedirs(build, exist_ok=True)
+    src, exe = os.path.join(build, "layout_probe.c"), os.path.join(build, "layout_probe")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    got = {}
+    for line in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
