@@ -98,7 +98,8 @@ class ClockSampler:
 # ------------------------------------------------------------------------- event set-up
 def event_setup(m, w, spec, dets_np):
     """Synthetic data and proposal for one event through the library's own helpers:
-    injection + noise (mbis_inject), Fisher matrix (mbis_fisher), Gaussian proposal."""
+    injection + noise (mbis_inject), Fisher-metric Gaussian proposal (mbis_fisher)."""
+    from paper_2410_05190_gb300.proposal import fisher_proposal
     n = w.n_bins
     psd1 = m.mbis_psd_aligo(w.f_lo, w.df, n)
     psd = np.tile(psd1, (w.n_det, 1))
@@ -113,41 +114,21 @@ def event_setup(m, w, spec, dets_np):
     th[DL] = math.sqrt(snr2) / spec.snr
     strain, _ = m.mbis_inject(w.f_lo, w.df, n, dets, psd, spec.gmst, th, spec.noise_seed or 0,
                               spec.noise_seed is not None)
-    strain = strain.astype(np.complex64)
+    strain = strain.astype(np.complex64 if w.complex_dtype == "c64" else np.complex128)
     ctx = m.mbis_create(strain, psd, dets, w.f_lo, w.df, th, gmst=spec.gmst, precision=m.FP64, marg=w.marg,
                         dmin=w.dmin, dmax=w.dmax)
-    sampled = list(w.sampled)
-    ids = sampled + [PHIC, DL]
-    steps = np.array([{MC: 1e-6 * th[MC], Q: 1e-6, CHI1: 1e-5, CHI2: 1e-5, TC: 1e-7, PHIC: 1e-6, DL: 1e-5 * th[DL]}[i]
-                      for i in ids])
-    G = m.mbis_fisher(ctx, th, ids, steps)
-    m.mbis_destroy(ctx)
-    P = len(sampled)
-    A, B, Cm = G[:P, :P], G[:P, P:], G[P:, P:]
-    G = A - B @ np.linalg.solve(Cm, B.T)
-    width = {Q: 2.0, CHI1: 2 * w.chi_max, CHI2: 2 * w.chi_max}
-    for p, i in enumerate(sampled):
-        if i in width:
-            G[p, p] += 12.0 / width[i] ** 2
-    cov = np.linalg.inv(G)
-    cov = 0.5 * (cov + cov.T)
-    L = np.linalg.cholesky(cov)
-    sig = np.sqrt(np.diag(cov)) * w.scale
-    mean = np.array([th[i] for i in sampled])
-    lo, hi = mean - w.box_sigmas * sig, mean + w.box_sigmas * sig
-    for p, i in enumerate(sampled):
-        if i in (CHI1, CHI2):
-            lo[p], hi[p] = -w.chi_max, w.chi_max
-        if i == Q:
-            lo[p] = max(1.0, lo[p])
-    prop = dict(ids=np.array(sampled, dtype=np.int32), mean=mean, chol=L, scale=w.scale, lo=lo, hi=hi,
-                flags=w.prior_flags)
-    return dict(spec=spec, th=th, strain=strain, psd=psd, dets=dets, prop=prop)
+    try:
+        prop = fisher_proposal(m, ctx, th, w.sampled, w.marg, scale=w.scale, box_sigmas=w.box_sigmas,
+                               chi_max=w.chi_max, dmin=w.dmin, dmax=w.dmax, prior_flags=w.prior_flags)
+    finally:
+        m.mbis_destroy(ctx)
+    return dict(spec=spec, th=th, strain=strain, psd=psd, dets=dets, prop=prop, w=w)
 
 
 def make_ctx(m, w, ev, precision):
     ctx = m.mbis_create(ev["strain"], ev["psd"], ev["dets"], w.f_lo, w.df, ev["th"], gmst=ev["spec"].gmst,
-                        precision=precision, marg=w.marg, dmin=w.dmin, dmax=w.dmax)
+                        precision=precision, marg=w.marg, n_tshift=w.n_tshift, dt_shift=w.dt_shift, dmin=w.dmin,
+                        dmax=w.dmax)
     p = ev["prop"]
     m.mbis_set_metric(ctx, p["ids"], p["mean"], p["chol"], p["scale"], p["lo"], p["hi"], p["flags"])
     return ctx
@@ -299,8 +280,8 @@ def run_gpu(args, rank, world):
                        "l2": "flushed between steps (256 MB write inside the timed region)",
                        "parallelism": f"replicas x{world} (events sharded, no collective on the data path)",
                        "setup_s": round(setup_s, 2)},
-            "seconds_to_1e4_ess": {"median": statistics.median(per_event_s), "max": max(per_event_s),
-                                   "efficiency_median": statistics.median(eff), "ess_median": statistics.median(ess)},
+            "fisher_proposal_efficiency": {"median": statistics.median(eff), "ess_median": statistics.median(ess),
+                                           "seconds_to_1e4_at_this_efficiency_median": statistics.median(per_event_s)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbin/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "loglike_mixed_fold_kernel", "launch_ms": statistics.mean(like_ms),
@@ -315,6 +296,195 @@ def run_gpu(args, rank, world):
     return out, w, evs
 
 
+# ------------------------------------------------------------------------- further measurements (N = 1)
+def ess_buffers(torch, P, batch):
+    return [torch.empty((P, batch), dtype=torch.float64, device="cuda")] + \
+           [torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(4)]
+
+
+def seconds_to_ess(m, torch, evs, precision, target=1e4, batch=1 << 16, max_samples=1 << 26, refine=4):
+    """Wall time of mbis_run_to_ess (refit after each of the first `refine` batches) per event."""
+    out = []
+    for ev in evs:
+        w = ev["w"]
+        ctx = make_ctx(m, w, ev, precision)
+        try:
+            bufs = ess_buffers(torch, len(ev["prop"]["ids"]), batch)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s, nd, nu = m.mbis_run_to_ess(ctx, *bufs, ess_target=target, batch=batch, max_samples=max_samples,
+                                          seed=ev["spec"].draw_seed, refine=refine, refine_scale=1.2)
+            out.append(dict(seconds=time.perf_counter() - t0, ess=s["ess"], drawn=nd, used=nu,
+                            reached=bool(s["ess"] >= target)))
+        finally:
+            m.mbis_destroy(ctx)
+    return out
+
+
+def likelihood_rate(m, torch, evs, precision, n, reps=3):
+    """Likelihood evaluations / s of mbis_loglike on n proposal samples per event (CUDA events)."""
+    times = []
+    stream = torch.cuda.current_stream()
+    for ev in evs:
+        w = ev["w"]
+        ctx = make_ctx(m, w, ev, precision)
+        try:
+            P = len(ev["prop"]["ids"])
+            theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+            lq, lp, ll = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+            m.mbis_draw(ctx, ev["spec"].draw_seed, 0, n, theta, lq, lp, stream)
+            m.mbis_loglike(ctx, n, theta, ll, stream)   # warm-up
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.mbis_loglike(ctx, n, theta, ll, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+        finally:
+            m.mbis_destroy(ctx)
+    return n / statistics.mean(times), statistics.mean(times)
+
+
+def bbh_measurement(m, torch, n_events=2, n=1 << 18):
+    w = workloads.bbh_population(n_events=n_events, n_samples=n)
+    dn = workloads.network(w.detectors)
+    evs = [event_setup(m, w, spec, dn) for spec in w.events]
+    mixed, t_mixed = likelihood_rate(m, torch, evs, m.MIXED, n)
+    fp64, t_fp64 = likelihood_rate(m, torch, evs, m.FP64, n, reps=1)
+    # tensor work of the time-shift contraction per likelihood: 3 split-TF32 products of
+    # (2 K_eff) x 256 real MACs over the padded live bins of the tile
+    return {"workload": "bbh_population: 2 events x 2^18 samples, H1+L1+V1, 8033 bins (df=1/8), 11 sampled "
+                        "parameters, time marginalised over 128 shifts of 0.1 ms",
+            "mixed_tcgen05": {"value": mixed, "unit": UNIT, "launch_ms": t_mixed * 1e3},
+            "fp64": {"value": fp64, "unit": UNIT, "launch_ms": t_fp64 * 1e3},
+            "speedup_vs_fp64": mixed / fp64}
+
+
+def batch_measurement(m, torch, steps=3, warmup=2):
+    ws = workloads.uneven_batch()
+    t0 = time.time()
+    evs = [event_setup(m, w, w.events[0], workloads.network(w.detectors)) for w in ws]
+    ctxs = [make_ctx(m, w, ev, m.MIXED) for w, ev in zip(ws, evs)]
+    setup_s = time.time() - t0
+    try:
+        b = m.mbis_batch_create(ctxs, [w.n_samples for w in ws], [w.events[0].draw_seed for w in ws])
+        try:
+            grid, tune_ms = m.mbis_batch_autotune(b)
+            for i in range(warmup):
+                m.mbis_batch_step(b, i, len(ws))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(steps):
+                m.mbis_batch_step(b, warmup + i, len(ws))
+            dt = (time.perf_counter() - t0) / steps
+        finally:
+            m.mbis_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            m.mbis_destroy(c)
+    n = sum(w.n_samples for w in ws)
+    return {"workload": "uneven batch: 64 events (heavy and BNS families), 1969-128513 bins, 2-3 detectors, "
+                        "2^14-2^20 samples each, one persistent likelihood launch per step, CUDA graph replay",
+            "value": n / dt, "unit": UNIT, "ms_per_step": dt * 1e3, "samples_per_step": n, "grid": grid,
+            "autotune_launch_ms": tune_ms, "setup_s": round(setup_s, 2)}
+
+
+SERVE_SEED = 0x5E12E
+
+
+def serve_requests(m, n_req, rate_hz, seed=SERVE_SEED):
+    """The served stream's requests: kind (0 plain-method tiny event, FP64; 1 BNS, mixed;
+    2 BBH with full extrinsics, mixed), event set-up, ESS-loop options, Poisson arrival time."""
+    rng = np.random.default_rng(seed)
+    kinds = rng.integers(0, 3, size=n_req)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_req))
+    tiny = workloads.tiny()
+    bns = workloads.bns_population(n_events=8)
+    bbh = workloads.bbh_population(n_events=8)
+    cache, reqs = {}, []
+    for i, k in enumerate(kinds):
+        w = (tiny, bns, bbh)[k]
+        e = 0 if k == 0 else int(rng.integers(0, len(w.events)))
+        if (k, e) not in cache:
+            cache[(k, e)] = event_setup(m, w, w.events[e], workloads.network(w.detectors))
+        ev = cache[(k, e)]
+        ess = dict(ess_target=1e4, batch=(1 << 20) if k == 2 else (1 << 16),
+                   max_samples=(1 << 25) if k == 2 else (1 << 24), seed=ev["spec"].draw_seed + 1000 * i,
+                   refine=4, refine_scale=1.2)
+        reqs.append(dict(kind=int(k), ev=ev, w=w, ess=ess, arrival=float(arrivals[i]),
+                         precision=m.FP64 if k == 0 else m.MIXED))
+    return reqs
+
+
+def submit_request(m, srv, r, precision=None, tag=0):
+    ev, w, p = r["ev"], r["w"], r["ev"]["prop"]
+    return m.mbis_server_submit(srv, ev["strain"], ev["psd"], ev["dets"], w.f_lo, w.df, ev["th"], p["ids"], p["mean"],
+                                p["chol"], p["scale"], p["lo"], p["hi"], prior_flags=p["flags"],
+                                gmst=ev["spec"].gmst, precision=r["precision"] if precision is None else precision,
+                                marg=w.marg, n_tshift=w.n_tshift, dt_shift=w.dt_shift, dmin=w.dmin, dmax=w.dmax,
+                                tag=tag, **r["ess"])
+
+
+def percentile(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def serve_measurement(m, torch, n_req=48, rate_hz=2.0, max_active=8, cap=150 * 10**9):
+    reqs = serve_requests(m, n_req, rate_hz)
+    srv = m.mbis_server_create(hbm_cap_bytes=cap, max_active=max_active)
+    try:
+        t0 = time.perf_counter()
+        ids = []
+        for k, r in enumerate(reqs):
+            delay = r["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(submit_request(m, srv, r, tag=k)[0])
+        res = [m.mbis_server_wait(srv, i, 600.0) for i in ids]
+        wall = time.perf_counter() - t0
+        st = m.mbis_server_stats_get(srv)
+    finally:
+        m.mbis_server_destroy(srv)
+    ttr = [x["t_done"] - x["t_submit"] for x in res]
+    names = ["plain_fp64", "bns_mixed", "bbh_mixed"]
+    by_kind = {}
+    for k, name in enumerate(names):
+        sel = [i for i, r in enumerate(reqs) if r["kind"] == k]
+        if sel:
+            by_kind[name] = {"n": len(sel), "p50_s": percentile([ttr[i] for i in sel], 50),
+                             "p99_s": percentile([ttr[i] for i in sel], 99),
+                             "reached_1e4": sum(res[i]["summary"]["ess"] >= 1e4 for i in sel)}
+    return {"workload": f"{n_req} requests, Poisson arrivals at {rate_hz}/s, kinds drawn uniformly from the "
+                        "plain-method tiny event (FP64), the BNS population and the BBH population (mixed), "
+                        "each run to ESS >= 1e4 with 4 proposal refits (sample caps 2^24, BBH 2^25)",
+            "p50_s": percentile(ttr, 50), "p99_s": percentile(ttr, 99), "mean_s": statistics.mean(ttr),
+            "throughput_req_s": n_req / wall, "evals_per_s": sum(x["n_drawn"] for x in res) / wall,
+            "wall_s": wall, "failed": sum(x["status"] != 0 for x in res), "by_kind": by_kind,
+            "max_active": max_active, "max_active_seen": st["max_active_seen"], "hbm_cap_bytes": cap,
+            "bytes_peak": st["bytes_peak"]}, reqs, res
+
+
+def serial_fp64(m, torch, reqs, n_first):
+    """Serial FP64 processing of the stream's first n_first requests (each alone, in arrival
+    order); time-to-result from the FIFO queue over the measured service times."""
+    done, ttr = 0.0, []
+    for r in reqs[:n_first]:
+        ev, w = r["ev"], r["w"]
+        ctx = make_ctx(m, w, ev, m.FP64)
+        try:
+            bufs = ess_buffers(torch, len(ev["prop"]["ids"]), r["ess"]["batch"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.mbis_run_to_ess(ctx, *bufs, **r["ess"])
+            service = time.perf_counter() - t0
+        finally:
+            m.mbis_destroy(ctx)
+        done = max(done, r["arrival"]) + service
+        ttr.append(done - r["arrival"])
+    return ttr
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,6 +495,10 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--extras", type=int, default=1, help="seconds-to-ESS, BBH, uneven batch and served stream (N=1)")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-compare", type=int, default=0,
+                    help="also process the stream's first K requests serially in FP64 (slow)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -342,6 +516,31 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
     out, w, evs = run_gpu(args, rank, world)
+    if rank == 0 and world == 1 and args.extras:
+        import torch
+        import paper_2410_05190_gb300 as m
+        mixed = seconds_to_ess(m, torch, evs, m.MIXED)
+        fp64 = seconds_to_ess(m, torch, evs[:2], m.FP64, max_samples=1 << 24)
+        out["seconds_to_1e4_ess"] = {
+            "measured": "mbis_run_to_ess wall time per event (batches of 2^16, proposal refit after each of the "
+                        "first 4 batches, ESS target 1e4)",
+            "mixed": {"median": statistics.median(x["seconds"] for x in mixed),
+                      "max": max(x["seconds"] for x in mixed), "reached": sum(x["reached"] for x in mixed),
+                      "events": len(mixed), "per_event": mixed},
+            "fp64_gpu": {"median": statistics.median(x["seconds"] for x in fp64),
+                         "max": max(x["seconds"] for x in fp64), "reached": sum(x["reached"] for x in fp64),
+                         "events": len(fp64), "per_event": fp64}}
+        out["bbh"] = bbh_measurement(m, torch)
+        out["uneven_batch"] = batch_measurement(m, torch)
+        served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
+        if args.serve_compare > 0:
+            k = min(args.serve_compare, len(reqs))
+            ser = serial_fp64(m, torch, reqs, k)
+            mix = [res[i]["t_done"] - res[i]["t_submit"] for i in range(k)]
+            served["vs_serial_fp64_first_k"] = {"k": k, "serial_fp64_p50_s": percentile(ser, 50),
+                                                "serial_fp64_p99_s": percentile(ser, 99),
+                                                "served_p50_s": percentile(mix, 50), "served_p99_s": percentile(mix, 99)}
+        out["served"] = served
     if rank == 0:
         if world == 1 and args.cpu_budget > 0:
             leg = OracleLeg(w, w.events[:1])
