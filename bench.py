@@ -495,7 +495,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--extras", type=int, default=1, help="seconds-to-ESS, BBH, uneven batch and served stream (N=1)")
+    ap.add_argument("--extras", default="ess,bbh,batch,serve",
+                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-compare", type=int, default=0,
                     help="also process the stream's first K requests serially in FP64 (slow)")
@@ -516,31 +517,37 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
     out, w, evs = run_gpu(args, rank, world)
-    if rank == 0 and world == 1 and args.extras:
+    extras = set(x for x in args.extras.split(",") if x and x != "none")
+    if rank == 0 and world == 1 and extras:
         import torch
         import paper_2410_05190_gb300 as m
-        mixed = seconds_to_ess(m, torch, evs, m.MIXED)
-        fp64 = seconds_to_ess(m, torch, evs[:2], m.FP64, max_samples=1 << 24)
-        out["seconds_to_1e4_ess"] = {
-            "measured": "mbis_run_to_ess wall time per event (batches of 2^16, proposal refit after each of the "
-                        "first 4 batches, ESS target 1e4)",
-            "mixed": {"median": statistics.median(x["seconds"] for x in mixed),
-                      "max": max(x["seconds"] for x in mixed), "reached": sum(x["reached"] for x in mixed),
-                      "events": len(mixed), "per_event": mixed},
-            "fp64_gpu": {"median": statistics.median(x["seconds"] for x in fp64),
-                         "max": max(x["seconds"] for x in fp64), "reached": sum(x["reached"] for x in fp64),
-                         "events": len(fp64), "per_event": fp64}}
-        out["bbh"] = bbh_measurement(m, torch)
-        out["uneven_batch"] = batch_measurement(m, torch)
-        served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
-        if args.serve_compare > 0:
-            k = min(args.serve_compare, len(reqs))
-            ser = serial_fp64(m, torch, reqs, k)
-            mix = [res[i]["t_done"] - res[i]["t_submit"] for i in range(k)]
-            served["vs_serial_fp64_first_k"] = {"k": k, "serial_fp64_p50_s": percentile(ser, 50),
-                                                "serial_fp64_p99_s": percentile(ser, 99),
-                                                "served_p50_s": percentile(mix, 50), "served_p99_s": percentile(mix, 99)}
-        out["served"] = served
+        if "ess" in extras:
+            mixed = seconds_to_ess(m, torch, evs, m.MIXED)
+            fp64 = seconds_to_ess(m, torch, evs[:2], m.FP64, max_samples=1 << 24)
+            out["seconds_to_1e4_ess"] = {
+                "measured": "mbis_run_to_ess wall time per event (batches of 2^16, proposal refit after each of "
+                            "the first 4 batches, ESS target 1e4)",
+                "mixed": {"median": statistics.median(x["seconds"] for x in mixed),
+                          "max": max(x["seconds"] for x in mixed), "reached": sum(x["reached"] for x in mixed),
+                          "events": len(mixed), "per_event": mixed},
+                "fp64_gpu": {"median": statistics.median(x["seconds"] for x in fp64),
+                             "max": max(x["seconds"] for x in fp64), "reached": sum(x["reached"] for x in fp64),
+                             "events": len(fp64), "per_event": fp64}}
+        if "bbh" in extras:
+            out["bbh"] = bbh_measurement(m, torch)
+        if "batch" in extras:
+            out["uneven_batch"] = batch_measurement(m, torch)
+        if "serve" in extras:
+            served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
+            if args.serve_compare > 0:
+                k = min(args.serve_compare, len(reqs))
+                ser = serial_fp64(m, torch, reqs, k)
+                mix = [res[i]["t_done"] - res[i]["t_submit"] for i in range(k)]
+                served["vs_serial_fp64_first_k"] = {"k": k, "serial_fp64_p50_s": percentile(ser, 50),
+                                                    "serial_fp64_p99_s": percentile(ser, 99),
+                                                    "served_p50_s": percentile(mix, 50),
+                                                    "served_p99_s": percentile(mix, 99)}
+            out["served"] = served
     if rank == 0:
         if world == 1 and args.cpu_budget > 0:
             leg = OracleLeg(w, w.events[:1])

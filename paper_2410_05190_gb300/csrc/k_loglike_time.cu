@@ -83,6 +83,8 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
 
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 // turns t -> 64-bit fixed point of frac(t)
 __device__ __forceinline__ uint64_t frac64(double t) {
   const double x = (t - floor(t)) * 4294967296.0;  // [0, 2^32)
@@ -114,34 +116,41 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   PhaseCoeffs pc;
   int32_t kcut = 0;
   double amp = 0.0, H = 0.0;
-  float pr[kMaxDet], pim[kMaxDet];
+  // Detector d enters as |P_d| c_dk e^{-i (Psi_k + 2 pi f_k dt_d - arg P_d)}: the argument of
+  // the response and the delay share one 64-bit fixed-point turn counter (off, stp per bin).
+  float pmag[kMaxDet];
   uint64_t off[kMaxDet], stp[kMaxDet];
 #pragma unroll
   for (int d = 0; d < kMaxDet; ++d) {
-    pr[d] = 0.f;
-    pim[d] = 0.f;
+    pmag[d] = 0.f;
     off[d] = 0;
     stp[d] = 0;
   }
   if (valid) {
-    pc = phase_coeffs(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic]);
-    kcut = live_bins(par[kMc], par[kQ], a.f_lo, a.df, a.n_bins);
+    const double m_sec = total_mass_seconds(par[kMc], par[kQ]);
+    pc = phase_coeffs_m(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], m_sec);
+    kcut = live_bins_m(m_sec, a.f_lo, a.df, a.n_bins);
     amp = amplitude(par[kMc], par[kDl]);
     if (a.fold) {
-      pr[0] = 1.f;
+      pmag[0] = 1.f;
       H = amp * amp * a.tfold[kcut];
     } else {
+      double sp, cp, sd, cd, ss, cs;
+      sincos(par[kRa] - a.gmst, &sp, &cp);
+      sincos(par[kDec], &sd, &cd);
+      sincos(par[kPsi], &ss, &cs);
       const double ci = cos(par[kIota]);
       for (int d = 0; d < a.n_det; ++d) {
         double fp, fc;
-        antenna(a.det_x[d], a.det_y[d], par[kRa], par[kDec], par[kPsi], a.gmst, &fp, &fc);
+        antenna_trig(a.det_x[d], a.det_y[d], sp, cp, sd, cd, ss, cs, &fp, &fc);
         const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
-        const double dt = geocentre_delay(a.det_vertex[d], par[kRa], par[kDec], a.gmst);
-        pr[d] = (float)p_re;
-        pim[d] = (float)p_im;
-        off[d] = frac64(a.f_lo * dt);
+        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
+        const double p2 = p_re * p_re + p_im * p_im;
+        pmag[d] = (float)sqrt(p2);
+        const double arg_turns = atan2(p_im, p_re) * (1.0 / kTwoPi);
+        off[d] = frac64(a.f_lo * dt - arg_turns);
         stp[d] = frac64(a.df * dt);
-        H += amp * amp * (p_re * p_re + p_im * p_im) * a.tdet[(int64_t)d * (a.n_bins + 1) + kcut];
+        H += amp * amp * p2 * a.tdet[(int64_t)d * (a.n_bins + 1) + kcut];
       }
     }
   } else {
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
 
   unsigned char* sA = sm + kOffA;
   unsigned char* sB = sm + kOffB;
-  float2* sCd = reinterpret_cast<float2*>(sm + kOffC);
+  float4* sCd = reinterpret_cast<float4*>(sm + kOffC);
   const float* tiles = a.ttiles;
   int issued_b[2] = {0, 0}, issued_m[2] = {0, 0};  // thread 0's bookkeeping
   if (tid == 0) {
@@ -214,56 +223,66 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         ++issued_b[b];
       }
     }
-    // data tables of this K-block
-    float2* cst = sCd + b * kMaxDet * kKBlockBins;
-    if (tid < nrow * kKBlockBins) {
-      const int d = tid / kKBlockBins, kk = tid % kKBlockBins;
-      cst[d * kKBlockBins + kk] = a.cdet32[(int64_t)d * a.n_pad16 + kb * kKBlockBins + kk];
+    // data tables of this K-block, per detector and bin pair: (re_k, re_k+1, im_k, im_k+1)
+    float4* cst = sCd + b * kMaxDet * (kKBlockBins / 2);
+    if (tid < nrow * (kKBlockBins / 2)) {
+      const int d = tid / (kKBlockBins / 2), pp = tid % (kKBlockBins / 2);
+      const float4 c = reinterpret_cast<const float4*>(a.cdet32)[((int64_t)d * a.n_pad16 + kb * kKBlockBins) / 2 + pp];
+      cst[d * (kKBlockBins / 2) + pp] = make_float4(c.x, c.z, c.y, c.w);
     }
     __syncthreads();
-    // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes
+    // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes.
+    // Bins go in pairs (plan blocks have even starts), two lanes of f32x2 arithmetic.
     unsigned char* rowA = sA + (b * kTilesPerCta + tile) * 2 * kTileBytes + row * 128;
 #pragma unroll 1
     for (int kk = 0; kk < kKBlockBins; kk += 2) {
-      float v[4];
+      const int32_t k = kb * kKBlockBins + kk;
+      if (k < kcut && k == blk_end) {
+        ++blk;
+        enter_block(a.plan, blk, pc, cf, st);
+        blk_end = a.plan[blk].k1;
+      }
+      float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
+      if (k < kcut) {
+        const float2 w = make_float2(st.w, st.w + 1.0f);
+        float2 R = __ffma2_rn(f2(st.c[5]), w, f2(st.c[4]));
+        R = __ffma2_rn(R, w, f2(st.c[3]));
+        R = __ffma2_rn(R, w, f2(st.c[2]));
+        R = __ffma2_rn(R, w, f2(st.c[1]));
+        R = __ffma2_rn(R, w, f2(st.c[0]));
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int32_t k = kb * kKBlockBins + kk + e;
-        if (k == blk_end) {
-          ++blk;
-          if (k < kcut) enter_block(a.plan, blk, pc, cf, st);
-          blk_end = a.plan[blk].k1;
-        }
-        float re = 0.f, im = 0.f;
-        if (k < kcut) {
-          const float R = fmaf(fmaf(fmaf(fmaf(fmaf(st.c[5], st.w, st.c[4]), st.w, st.c[3]), st.w, st.c[2]), st.w,
-                                    st.c[1]),
-                               st.w, st.c[0]);
-#pragma unroll
-          for (int d = 0; d < kMaxDet; ++d) {
-            if (d < nrow) {
-              const float ang = fmaf(mantissa_turn(st.acc + (uint32_t)(off[d] >> 32)), kTwoPiF, R);
-              float sn, cs;
-              __sincosf(ang, &sn, &cs);
-              const float2 c = cst[d * kKBlockBins + kk + e];
-              const float xr = fmaf(c.x, cs, c.y * sn), xi = fmaf(c.y, cs, -c.x * sn);
-              re = fmaf(pr[d], xr, fmaf(-pim[d], xi, re));
-              im = fmaf(pr[d], xi, fmaf(pim[d], xr, im));
-            }
+        for (int d = 0; d < kMaxDet; ++d) {
+          if (d < nrow) {
+            const uint32_t o0 = (uint32_t)(off[d] >> 32), o1 = (uint32_t)((off[d] + stp[d]) >> 32);
+            const float2 f1 = make_float2(mantissa_turn(st.acc + o0), mantissa_turn(st.acc + st.step + o1));
+            const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), R);
+            float2 sn, cs;
+            __sincosf(ang.x, &sn.x, &cs.x);
+            __sincosf(ang.y, &sn.y, &cs.y);
+            const float4 c = cst[d * (kKBlockBins / 2) + (kk >> 1)];
+            const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
+            const float2 q = __fmul2_rn(f2(pmag[d]), cs), r = __fmul2_rn(f2(pmag[d]), sn);
+            re = __ffma2_rn(cx, q, __ffma2_rn(cy, r, re));
+            imc = __ffma2_rn(cy, q, imc);
+            ims = __ffma2_rn(cx, r, ims);
           }
         }
-        st.acc += st.step;
-        st.w += 1.0f;
-#pragma unroll
-        for (int d = 0; d < kMaxDet; ++d) off[d] += stp[d];
-        v[2 * e] = re;
-        v[2 * e + 1] = im;
+        if (k + 1 >= kcut) {  // odd cut: the second bin of the pair is beyond the ISCO
+          re.y = 0.f;
+          imc.y = 0.f;
+          ims.y = 0.f;
+        }
       }
+      st.acc += 2u * st.step;
+      st.w += 2.0f;
+#pragma unroll
+      for (int d = 0; d < kMaxDet; ++d) off[d] += 2 * stp[d];
+      const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
       float4 hi, lo;
-      hi.x = tc::tf32_round(v[0]); lo.x = v[0] - hi.x;
-      hi.y = tc::tf32_round(v[1]); lo.y = v[1] - hi.y;
-      hi.z = tc::tf32_round(v[2]); lo.z = v[2] - hi.z;
-      hi.w = tc::tf32_round(v[3]); lo.w = v[3] - hi.w;
+      hi.x = tc::tf32_round(re.x); lo.x = re.x - hi.x;
+      hi.y = tc::tf32_round(im.x); lo.y = im.x - hi.y;
+      hi.z = tc::tf32_round(re.y); lo.z = re.y - hi.z;
+      hi.w = tc::tf32_round(im.y); lo.w = im.y - hi.w;
       const int chunk = (kk >> 1) ^ (row & 7);
       *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
       *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;

@@ -45,7 +45,9 @@ MBIS_HD double total_mass_seconds(double mc, double q) {
   return mc * kTsun * pow(1.0 + q, 1.2) * pow(q, -0.6);
 }
 
-MBIS_HD PhaseCoeffs phase_coeffs(double mc, double q, double chi1, double chi2, double tc, double phic) {
+// m_sec: total mass in seconds, total_mass_seconds(mc, q)
+MBIS_HD PhaseCoeffs phase_coeffs_m(double mc, double q, double chi1, double chi2, double tc, double phic,
+                                   double m_sec) {
   const double eta = q / ((1.0 + q) * (1.0 + q));
   const double dm = (q - 1.0) / (q + 1.0);  // (m1 - m2) / M
   const double xs = 0.5 * (chi1 + chi2), xa = 0.5 * (chi1 - chi2);
@@ -74,7 +76,7 @@ MBIS_HD PhaseCoeffs phase_coeffs(double mc, double q, double chi1, double chi2, 
                       dm * (-25150083775.0 / 3048192.0 + 26804935.0 / 6048.0 * eta - 1985.0 / 48.0 * e2) * xa;
 
   // v = (a f)^(1/3) with a = pi M;  v^n = a^(n/3) f^(n/3);  3 ln v = ln a + ln f
-  const double a = kPi * total_mass_seconds(mc, q);
+  const double a = kPi * m_sec;
   const double la = log(a);
   const double a13 = cbrt(a), a23 = a13 * a13;
   const double pre = 3.0 / (128.0 * eta) / kTwoPi;  // turns
@@ -90,6 +92,10 @@ MBIS_HD PhaseCoeffs phase_coeffs(double mc, double q, double chi1, double chi2, 
   pc.C[8] = tc;                                      // f
   pc.cst = -phic / kTwoPi - 0.125 + pre * c5 * (1.0 + la);
   return pc;
+}
+
+MBIS_HD PhaseCoeffs phase_coeffs(double mc, double q, double chi1, double chi2, double tc, double phic) {
+  return phase_coeffs_m(mc, q, chi1, chi2, tc, phic, total_mass_seconds(mc, q));
 }
 
 MBIS_HD double basis(int j, double f) {
@@ -123,14 +129,14 @@ MBIS_HD double basis_deriv(int j, double f) {
   }
 }
 
-MBIS_HD double f_isco(double mc, double q) {
-  // 1 / (6^(3/2) pi M)
-  return 1.0 / (14.696938456699067 * kPi * total_mass_seconds(mc, q));
-}
+// 1 / (6^(3/2) pi M), M in seconds
+MBIS_HD double f_isco_m(double m_sec) { return 1.0 / (14.696938456699067 * kPi * m_sec); }
 
-// number of grid points f_lo + k df (k < n_bins) strictly below the ISCO
-MBIS_HD int32_t live_bins(double mc, double q, double f_lo, double df, int32_t n_bins) {
-  const double fi = f_isco(mc, q);
+MBIS_HD double f_isco(double mc, double q) { return f_isco_m(total_mass_seconds(mc, q)); }
+
+// number of grid points f_lo + k df (k < n_bins) strictly below the ISCO of total mass m_sec
+MBIS_HD int32_t live_bins_m(double m_sec, double f_lo, double df, int32_t n_bins) {
+  const double fi = f_isco_m(m_sec);
   double kk = ceil((fi - f_lo) / df);
   if (!(kk > 0.0)) return 0;
   if (kk > (double)n_bins) kk = (double)n_bins;
@@ -138,6 +144,10 @@ MBIS_HD int32_t live_bins(double mc, double q, double f_lo, double df, int32_t n
   while (k > 0 && f_lo + (double)(k - 1) * df >= fi) --k;
   while (k < n_bins && f_lo + (double)k * df < fi) ++k;
   return k;
+}
+
+MBIS_HD int32_t live_bins(double mc, double q, double f_lo, double df, int32_t n_bins) {
+  return live_bins_m(total_mass_seconds(mc, q), f_lo, df, n_bins);
 }
 
 // A = sqrt(5/24) pi^(-2/3) (Mc T_sun)^(5/6) / (d_L / c)
@@ -160,6 +170,22 @@ MBIS_HD void antenna(const double* x, const double* y, double ra, double dec, do
   const double yX = y[0] * X0 + y[1] * X1 + y[2] * X2, yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
   *fp = 0.5 * (xX * xX - xY * xY - yX * yX + yY * yY);
   *fc = xX * xY - yX * yY;
+}
+
+// The same two quantities from the sines and cosines of (ra - gmst), dec and psi, so that a
+// network evaluates them once per sample.
+MBIS_HD void antenna_trig(const double* x, const double* y, double sp, double cp, double sd, double cd, double ss,
+                          double cs, double* fp, double* fc) {
+  const double X0 = sp * cs - ss * cp * sd, X1 = -cp * cs - ss * sp * sd, X2 = ss * cd;
+  const double Y0 = -sp * ss - cs * cp * sd, Y1 = cp * ss - cs * sp * sd, Y2 = cs * cd;
+  const double xX = x[0] * X0 + x[1] * X1 + x[2] * X2, xY = x[0] * Y0 + x[1] * Y1 + x[2] * Y2;
+  const double yX = y[0] * X0 + y[1] * X1 + y[2] * X2, yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
+  *fp = 0.5 * (xX * xX - xY * xY - yX * yX + yY * yY);
+  *fc = xX * xY - yX * yY;
+}
+
+MBIS_HD double delay_trig(const double* r, double sp, double cp, double sd, double cd) {
+  return -(r[0] * cd * cp + r[1] * cd * sp + r[2] * sd) / kClight;
 }
 
 // arrival-time offset relative to the geocentre, -r . n / c
