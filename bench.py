@@ -321,8 +321,30 @@ def seconds_to_ess(m, torch, evs, precision, target=1e4, batch=1 << 16, max_samp
     return out
 
 
-def likelihood_rate(m, torch, evs, precision, n, reps=3):
-    """Likelihood evaluations / s of mbis_loglike on n proposal samples per event (CUDA events)."""
+T_SUN = 4.925490947641267e-6
+
+
+def live_bins(mc, q, f_lo, df, n_bins):
+    """Bins f_lo + k df below the Schwarzschild ISCO of the total mass, per sample (the
+    work a likelihood does; bins above the cut are not counted)."""
+    m_sec = mc * T_SUN * (1.0 + q) ** 1.2 * q ** -0.6
+    f_isco = 1.0 / (6.0 ** 1.5 * math.pi * m_sec)
+    k = np.ceil((f_isco - f_lo) / df)
+    return np.clip(np.nan_to_num(k, nan=0.0), 0, n_bins)
+
+
+def sample_bins(theta, ids, fixed, w):
+    """Sum over samples of the live bins (theta: host [P][n])."""
+    ids = list(ids)
+    mc = theta[ids.index(MC)] if MC in ids else np.full(theta.shape[1], fixed[MC])
+    q = theta[ids.index(Q)] if Q in ids else np.full(theta.shape[1], fixed[Q])
+    ok = (mc > 0) & (q > 0)
+    return float(live_bins(np.where(ok, mc, 1.0), np.where(ok, q, 1.0), w.f_lo, w.df, w.n_bins)[ok].sum())
+
+
+def likelihood_rate(m, torch, evs, precision, n, reps=3, units=None):
+    """Likelihood evaluations / s of mbis_loglike on n proposal samples per event (CUDA
+    events); units (list, optional) receives each event's live sample-bins."""
     times = []
     stream = torch.cuda.current_stream()
     for ev in evs:
@@ -333,6 +355,8 @@ def likelihood_rate(m, torch, evs, precision, n, reps=3):
             theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
             lq, lp, ll = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
             m.mbis_draw(ctx, ev["spec"].draw_seed, 0, n, theta, lq, lp, stream)
+            if units is not None:
+                units.append(sample_bins(theta.cpu().numpy(), ev["prop"]["ids"], ev["th"], w))
             m.mbis_loglike(ctx, n, theta, ll, stream)   # warm-up
             for _ in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -350,13 +374,22 @@ def bbh_measurement(m, torch, n_events=2, n=1 << 18):
     w = workloads.bbh_population(n_events=n_events, n_samples=n)
     dn = workloads.network(w.detectors)
     evs = [event_setup(m, w, spec, dn) for spec in w.events]
-    mixed, t_mixed = likelihood_rate(m, torch, evs, m.MIXED, n)
+    units = []
+    mixed, t_mixed = likelihood_rate(m, torch, evs, m.MIXED, n, units=units)
     fp64, t_fp64 = likelihood_rate(m, torch, evs, m.FP64, n, reps=1)
+    pk = peaks()
+    peak = N_SM * SFU_PER_SM_PER_CLK * pk.get("sm_max_mhz", 2070.0) * 1e6 / SFU_PER_BIN / 1e9
+    bin_det = statistics.mean(units) * w.n_det        # per launch: live (sample, bin, detector) triples
+    achieved = bin_det / t_mixed / 1e9
     # tensor work of the time-shift contraction per likelihood: 3 split-TF32 products of
     # (2 K_eff) x 256 real MACs over the padded live bins of the tile
     return {"workload": "bbh_population: 2 events x 2^18 samples, H1+L1+V1, 8033 bins (df=1/8), 11 sampled "
                         "parameters, time marginalised over 128 shifts of 0.1 ms",
-            "mixed_tcgen05": {"value": mixed, "unit": UNIT, "launch_ms": t_mixed * 1e3},
+            "mixed_tcgen05": {"value": mixed, "unit": UNIT, "launch_ms": t_mixed * 1e3,
+                              "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbin/s",
+                                           "frac": achieved / peak,
+                                           "note": "live (sample, bin, detector) triples per launch / launch time "
+                                                   "against 2 MUFU per triple"}},
             "fp64": {"value": fp64, "unit": UNIT, "launch_ms": t_fp64 * 1e3},
             "speedup_vs_fp64": mixed / fp64}
 
@@ -378,16 +411,35 @@ def batch_measurement(m, torch, steps=3, warmup=2):
             for i in range(steps):
                 m.mbis_batch_step(b, warmup + i, len(ws))
             dt = (time.perf_counter() - t0) / steps
+            # the persistent likelihood launch alone (CUDA events on its stream), and its
+            # live sample-bins from the samples of the last step
+            units = sum(sample_bins(m.mbis_batch_copy_out(b, i, len(ev["prop"]["ids"]), w.n_samples)[0],
+                                    ev["prop"]["ids"], ev["th"], w) for i, (w, ev) in enumerate(zip(ws, evs)))
+            stream = torch.cuda.Stream()
+            launch = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.mbis_batch_loglike(b, stream)
+                e1.record(stream)
+                stream.synchronize()
+                launch.append(e0.elapsed_time(e1) / 1e3)
         finally:
             m.mbis_batch_destroy(b)
     finally:
         for c in ctxs:
             m.mbis_destroy(c)
     n = sum(w.n_samples for w in ws)
-    return {"workload": "uneven batch: 64 events (heavy and BNS families), 1969-128513 bins, 2-3 detectors, "
+    out = {"workload": "uneven batch: 64 events (heavy and BNS families), 1969-128513 bins, 2-3 detectors, "
                         "2^14-2^20 samples each, one persistent likelihood launch per step, CUDA graph replay",
             "value": n / dt, "unit": UNIT, "ms_per_step": dt * 1e3, "samples_per_step": n, "grid": grid,
+            "launch_ms": statistics.mean(launch) * 1e3,
+            "roofline": {"bound": "alu", "achieved": units / statistics.mean(launch) / 1e9,
+                         "peak": N_SM * SFU_PER_SM_PER_CLK * peaks().get("sm_max_mhz", 2070.0) * 1e6 / SFU_PER_BIN / 1e9,
+                         "unit": "Gbin/s", "note": "live (sample, bin) pairs per persistent launch / launch time"},
             "autotune_launch_ms": tune_ms, "setup_s": round(setup_s, 2)}
+    out["roofline"]["frac"] = out["roofline"]["achieved"] / out["roofline"]["peak"]
+    return out
 
 
 SERVE_SEED = 0x5E12E

@@ -196,6 +196,16 @@ mbis_status build_tables(mbis_ctx* c) {
     pin.max_block = 4096;
     const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
     c->n_blocks = (int32_t)plan.size();
+    // float-float block entry when every phase term, its per-bin slope times the block
+    // length, the t_c term and the constant stay below kFloatFloatMaxTurns
+    double tc_max = std::fabs(c->fixed[kTc]);
+    for (int p = 0; p < c->P; ++p)
+      if (c->ids[p] == kTc) tc_max = std::max(std::fabs(c->lo[p]), std::fabs(c->hi[p]));
+    double term_max = tc_max * (c->f_lo + c->df * n) + 1024.0;
+    for (const AnchorBlock& b : plan)
+      for (int j = 0; j < kNumBasis - 1; ++j)
+        term_max = std::max(term_max, pin.cmax[j] * (std::fabs(b.B[j]) + std::fabs(b.dB[j]) * (b.k1 - b.k0)));
+    c->ff_phase = term_max < kFloatFloatMaxTurns ? 1 : 0;
     CU_TRY(c, dalloc(c, &c->d_plan, sizeof(AnchorBlock) * plan.size()));
     CU_TRY(c, cudaMemcpyAsync(c->d_plan, plan.data(), sizeof(AnchorBlock) * plan.size(), cudaMemcpyHostToDevice, s));
     CU_TRY(c, cudaStreamSynchronize(s));  // the host plan goes out of scope
@@ -305,6 +315,7 @@ LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, doubl
   a.n_pad16 = c->n_pad16;
   a.ttiles = c->d_ttiles;
   a.n_kb = c->n_kb;
+  a.ff_phase = c->ff_phase;
   a.err = c->d_err;
   a.gl = c->d_gl;
   return a;

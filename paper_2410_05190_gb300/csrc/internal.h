@@ -27,7 +27,13 @@ struct AnchorBlock {
   double B[kNumBasis];     // basis_j(f_kc)
   double dB[kNumBasis];    // basis_j'(f_kc) * df
   float E[kNumBasis - 1][kRemDeg + 1];  // basis 8 (f) is linear: no remainder
+  // B and dB as unevaluated float pairs (hi + lo) for the float-float block entry
+  float Bh[kNumBasis], Bl[kNumBasis], dBh[kNumBasis], dBl[kNumBasis];
 };
+
+// Events whose phase terms stay below this many turns may enter anchor blocks in float-float
+// arithmetic (~2^-44 relative) instead of FP64.
+constexpr double kFloatFloatMaxTurns = 65536.0;
 
 struct DetResponse {
   double pre, pim;  // P_det = F+ (1 + cos^2 i)/2 - i Fx cos i
@@ -64,10 +70,12 @@ struct LikeArgs {
   double cscale;
   const AnchorBlock* plan;
   int32_t n_blocks;
-  const float2* cdet32;       // TIME, mixed: [n_rows][n_pad16] per-detector (or folded) tables / cscale
+  const float2* cdet32;       // TIME, mixed: [n_rows][n_pad16] per-detector (or folded) tables / cscale,
+                              // bin pairs interleaved (re_k, re_k+1, im_k, im_k+1)
   int32_t n_pad16;            // row length of cdet32 (multiple of 16)
   const float* ttiles;        // TIME, mixed: [n_kb][2][4096] swizzled twiddle head / tail tiles
   int32_t n_kb;               // K-blocks of 16 bins covering n_bins
+  int32_t ff_phase;           // block entry in float-float (phase terms below kFloatFloatMaxTurns)
   int32_t* err;               // device error word (timeouts)
   const double* gl;           // Gauss-Legendre nodes / weights (marg.cuh layout)
 };
@@ -239,6 +247,7 @@ struct mbis_ctx {
   float2* d_cdet32 = nullptr;    // TIME marginalisation, mixed: FP32 tables
   float* d_ttiles = nullptr;     // TIME marginalisation, mixed: twiddle tiles
   int32_t n_pad16 = 0, n_kb = 0;
+  int32_t ff_phase = 0;
   double cscale = 1.0;
   mbis::AnchorBlock* d_plan = nullptr;
   int32_t n_blocks = 0;

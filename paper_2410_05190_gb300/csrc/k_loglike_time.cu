@@ -7,11 +7,12 @@
 //
 // The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA of 256
 // threads owns two tiles of 128 samples.  Per K-block of 16 bins:
-//   * every thread computes its sample's a_k for the 16 bins (mixed-precision phase as in
-//     the folded kernel: FP64 anchors, 32-bit fixed-point turns, FP32 remainder, MUFU
-//     sin/cos per detector; detector delays as 64-bit fixed-point turn counters) and writes
-//     them, split into a TF32 head and an FP32 tail, into its row of a 128-byte-swizzled
-//     K-major shared-memory tile;
+//   * every thread computes its sample's a_k for the 16 bins, two bins at a time in f32x2
+//     (mixed-precision phase as in the folded kernel: anchors entered in float-float when
+//     the event's phase terms allow it, FP64 otherwise; 32-bit fixed-point turns; FP32
+//     remainder; MUFU sin/cos per detector; each detector's delay and response argument as
+//     one 64-bit fixed-point turn counter) and writes them, split into a TF32 head and an
+//     FP32 tail, into its row of a 128-byte-swizzled K-major shared-memory tile;
 //   * the pre-swizzled twiddle tiles (head, tail) of the block arrive by cp.async.bulk;
 //   * one thread issues 3 x 4 x 2 tcgen05.mma.kind::tf32 (head.head + head.tail + tail.head
 //     for each 8-wide K step and both tiles) accumulating in TMEM and commits to an mbarrier
@@ -26,19 +27,22 @@
 namespace mbis {
 namespace {
 
-constexpr int kTT = 256;
+constexpr int kCompute = 256;  // two tiles of 128 samples, one per thread
+constexpr int kTT = kCompute;
 constexpr int kTilesPerCta = 2;
 constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
 constexpr uint32_t kOffA = 0;           // [2 buf][2 tile][2 head/tail][tile]
 constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [2 buf][2 head/tail][tile]
-constexpr uint32_t kOffC = kOffB + 2 * 2 * kTileBytes;                 // [2 buf][kMaxDet][16] float2
-constexpr uint32_t kSmemBytes = kOffC + 2 * kMaxDet * kKBlockBins * 8 + 1024;
+constexpr uint32_t kSmemBytes = kOffB + 2 * 2 * kTileBytes + 1024;
 constexpr uint32_t kIdesc = tc::idesc_tf32(128, kTimeShifts);
 // The tensor core aligns and truncates when it accumulates, which biases a long FP32
-// accumulation toward zero by a fraction of an ulp per step.  Each accumulator therefore
-// takes at most kSegBlocks K-blocks (4 MMA steps each for the main term) before it is drained
-// into FP32 registers with round-to-nearest adds; the split corrections, ~2^-11 smaller,
-// accumulate separately.  TMEM: per tile [main 128 | correction 128] columns.
+// accumulation toward zero by a fraction of an ulp per step.  The head.head products
+// therefore accumulate in a "main" TMEM accumulator over segments of kSegBlocks K-blocks
+// only; a segment is drained into FP32 registers with round-to-nearest adds one block after
+// its last MMA (after the threads computed the next block's A rows, so the MMA has long
+// finished), before the next segment's first MMA overwrites it.  The two split corrections,
+// ~2^-11 smaller, accumulate over the whole K range in a second accumulator.
+// TMEM: per tile [main 128 | correction 128] columns.
 constexpr int kSegBlocks = 4;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
@@ -81,9 +85,107 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.w = (float)w0;
 }
 
+// ---- float-float block entry (events whose phase terms stay below kFloatFloatMaxTurns).
+// A value is an unevaluated pair hi + lo of floats.  Sums use Knuth's two-sum (exact), the
+// product of a pair by a pair Dekker's product with the FMA giving the rounding error of
+// hi*hi exactly; explicit _rn intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += (ch, cl) * (bh, bl)
+__device__ __forceinline__ void ff_mac(float ch, float cl, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ch, bh);
+  const float e = __fmaf_rn(ch, bl, __fmaf_rn(cl, bh, __fmaf_rn(ch, bh, -p)));
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// frac(h + l) as a 32-bit fixed-point turn count; resid (turns) is what the count rounds off
+__device__ __forceinline__ uint32_t ff_frac32(float h, float l, float& resid) {
+  const float fh = __fsub_rn(h, floorf(h));           // exact: a multiple of ulp(h) below one
+  const float xh = __fmul_rn(fh, 4294967296.0f);      // exact scalings by 2^32
+  const float xl = __fmul_rn(l, 4294967296.0f);
+  const float rh = rintf(xh), rl = rintf(xl);
+  resid = __fmul_rn(__fadd_rn(__fsub_rn(xh, rh), __fsub_rn(xl, rl)), 2.3283064365386963e-10f);
+  return (uint32_t)__float2ull_rn(rh) + (uint32_t)__float2int_rn(rl);
+}
+
+// Per-sample phase coefficients as float pairs, kept in shared memory (one column per
+// thread): pf[j * kCompute] = hi of C_j, pf[(kNumBasis + j) * kCompute] = lo, then cst hi, lo.
+constexpr int kPhaseFF = 2 * kNumBasis + 2;
+
+__device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ plan, int blk, const float* pf,
+                                               State& st) {
+  const AnchorBlock& B = plan[blk];
+  float xh = pf[2 * kNumBasis * kCompute], xl = pf[(2 * kNumBasis + 1) * kCompute], yh = 0.f, yl = 0.f;
+#pragma unroll
+  for (int j = 0; j < kNumBasis; ++j) {
+    const float ch = pf[j * kCompute], cl = pf[(kNumBasis + j) * kCompute];
+    ff_mac(ch, cl, B.Bh[j], B.Bl[j], xh, xl);
+    ff_mac(ch, cl, B.dBh[j], B.dBl[j], yh, yl);
+  }
+  two_sum(yh, yl, yh, yl);
+  const float w0 = (float)(B.k0 - B.kc);
+  ff_mac(w0, 0.f, yh, yl, xh, xl);  // phase at the block's first bin
+  two_sum(xh, xl, xh, xl);
+  float r0, r1;
+  st.acc = ff_frac32(xh, xl, r0) + 256u;
+  st.step = ff_frac32(yh, yl, r1);
+#pragma unroll
+  for (int m = 0; m <= kRemDeg; ++m) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * kCompute], B.E[j][m], s);
+    st.c[m] = s;
+  }
+  st.c[0] += r0 - w0 * r1;
+  st.c[1] += r1;
+#pragma unroll
+  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  st.c[0] -= kTwoPiF;
+  st.w = w0;
+}
+
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Mass-dependent set-up with few FP64 operations (the GB300 runs FP64 at ~1/64 of FP32):
+// a power or root is seeded in FP32 and refined by one FP64 Newton step, which squares the
+// seed's ~1e-7 relative error; only ln(pi M) is an FP64 library call.
+//   M = Mc T_sun u^(3/5), u = (1 + q)^2 / q:  y = u^(3/5) solves y^5 = u^3
+//   a = pi M, a^(1/3) solves y^3 = a
+//   A = K (Mc T_sun)^(5/6) / d_L:  y = x^(5/6) solves y^6 = x^5
+// (log L of a poor sample can reach 10^4 in magnitude, so A and H keep ~1e-15 accuracy).
+struct MassSetup {
+  double m_sec, a, la, a13, amp;
+};
+
+__device__ __forceinline__ MassSetup mass_setup(double mc, double q, double dl_mpc) {
+  MassSetup o;
+  const double u = (1.0 + q) * (1.0 + q) / q, u3 = u * u * u;
+  double y = (double)powf((float)u, 0.6f);
+  const double y4 = (y * y) * (y * y);
+  y = 0.8 * y + u3 / (5.0 * y4);
+  o.m_sec = mc * kTsun * y;
+  o.a = kPi * o.m_sec;
+  o.la = log(o.a);
+  double c = (double)cbrtf((float)o.a);
+  c = (2.0 * c + o.a / (c * c)) * (1.0 / 3.0);
+  o.a13 = c;
+  // (Mc T_sun)^(5/6) solves y^6 = x^5
+  const double x = mc * kTsun, x5 = (x * x) * (x * x) * x;
+  double z = (double)powf((float)x, 5.0f / 6.0f);
+  const double z5 = (z * z) * (z * z) * z;
+  z = (5.0 / 6.0) * z + x5 / (6.0 * z5);
+  o.amp = 0.45643546458763845 * 0.46619407703541166 * z / (dl_mpc * kMpcSeconds);
+  return o;
+}
 
 // turns t -> 64-bit fixed point of frac(t)
 __device__ __forceinline__ uint64_t frac64(double t) {
@@ -94,14 +196,26 @@ __device__ __forceinline__ uint64_t frac64(double t) {
   return (hi << 32) + lo;
 }
 
+// kFF: anchor blocks entered in float-float (events whose phase terms stay below
+// kFloatFloatMaxTurns), otherwise in FP64.  kRows: detector rows of the table (1 when the
+// detectors are folded), a compile-time count so the detectors' chains interleave.
+template <bool kFF, int kRows>
 __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bbar[2], mbar[2];
+  // bbar[b]: twiddle tiles of buffer b landed; full[b]: the 256 threads wrote A[b]; mbar[b]:
+  // the MMAs reading buffer b completed.  The last thread to finish a block's A rows issues
+  // its MMAs (and the next block's twiddle copies), so the other warps run on while the
+  // tensor core works.  Decisions taken on a wait's outcome are warp-uniform, since TMEM
+  // loads are warp-collective.
+  __shared__ __align__(8) uint64_t bbar[2], full[2], mbar[2];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_kmax, s_bad;
+  __shared__ int s_kmax, s_done[2];
+  __shared__ int s_issued_b[2], s_issued_m[2];
+  __shared__ volatile int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
-  const int64_t s = (int64_t)blockIdx.x * kTT + tid;
+  constexpr int nrow = kRows;
+  const int64_t s = (int64_t)blockIdx.x * kCompute + tid;
   const bool active = s < a.n;
 
   // ---- per-sample set-up (FP64)
@@ -112,42 +226,44 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   const bool valid = active && par[kMc] > 0.0 && par[kQ] > 0.0 && fabs(par[kChi1]) < 1.0 &&
                      fabs(par[kChi2]) < 1.0 && par[kDl] > 0.0 && isfinite(par[kTc]) && isfinite(par[kPhic]) &&
                      isfinite(par[kRa]) && isfinite(par[kDec]) && isfinite(par[kPsi]) && isfinite(par[kIota]);
-  const int nrow = a.fold ? 1 : a.n_det;
   PhaseCoeffs pc;
   int32_t kcut = 0;
   double amp = 0.0, H = 0.0;
   // Detector d enters as |P_d| c_dk e^{-i (Psi_k + 2 pi f_k dt_d - arg P_d)}: the argument of
   // the response and the delay share one 64-bit fixed-point turn counter (off, stp per bin).
-  float pmag[kMaxDet];
-  uint64_t off[kMaxDet], stp[kMaxDet];
+  float pmag[nrow];
+  uint64_t off[nrow], stp[nrow];
 #pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) {
+  for (int d = 0; d < nrow; ++d) {
     pmag[d] = 0.f;
     off[d] = 0;
     stp[d] = 0;
   }
   if (valid) {
-    const double m_sec = total_mass_seconds(par[kMc], par[kQ]);
-    pc = phase_coeffs_m(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], m_sec);
-    kcut = live_bins_m(m_sec, a.f_lo, a.df, a.n_bins);
-    amp = amplitude(par[kMc], par[kDl]);
+    const MassSetup ms = mass_setup(par[kMc], par[kQ], par[kDl]);
+    pc = phase_coeffs_a(par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], ms.a, ms.la, ms.a13);
+    kcut = live_bins_m(ms.m_sec, a.f_lo, a.df, a.n_bins);
+    amp = ms.amp;
     if (a.fold) {
       pmag[0] = 1.f;
       H = amp * amp * a.tfold[kcut];
     } else {
+      // FP64 for the delays (2 pi f dt to ~1e-7 rad) and for |P|^2 (H scales with it); the
+      // response argument enters the phase at FP32 accuracy
       double sp, cp, sd, cd, ss, cs;
       sincos(par[kRa] - a.gmst, &sp, &cp);
       sincos(par[kDec], &sd, &cd);
       sincos(par[kPsi], &ss, &cs);
       const double ci = cos(par[kIota]);
-      for (int d = 0; d < a.n_det; ++d) {
+#pragma unroll
+      for (int d = 0; d < nrow; ++d) {
         double fp, fc;
         antenna_trig(a.det_x[d], a.det_y[d], sp, cp, sd, cd, ss, cs, &fp, &fc);
         const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
-        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
         const double p2 = p_re * p_re + p_im * p_im;
+        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
         pmag[d] = (float)sqrt(p2);
-        const double arg_turns = atan2(p_im, p_re) * (1.0 / kTwoPi);
+        const double arg_turns = (double)atan2f((float)p_im, (float)p_re) * (1.0 / kTwoPi);
         off[d] = frac64(a.f_lo * dt - arg_turns);
         stp[d] = frac64(a.df * dt);
         H += amp * amp * p2 * a.tdet[(int64_t)d * (a.n_bins + 1) + kcut];
@@ -159,15 +275,33 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     pc.cst = 0.0;
   }
   float cf[kNumBasis - 1];
+  __shared__ float s_pf[kFF ? kPhaseFF * kCompute : 1];
+  float* pf = s_pf + tid;
+  if constexpr (kFF) {
 #pragma unroll
-  for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = (float)pc.C[j];
+    for (int j = 0; j < kNumBasis; ++j) {
+      const float h = (float)pc.C[j];
+      pf[j * kCompute] = h;
+      pf[(kNumBasis + j) * kCompute] = (float)(pc.C[j] - (double)h);
+    }
+    const float h = (float)pc.cst;
+    pf[2 * kNumBasis * kCompute] = h;
+    pf[(2 * kNumBasis + 1) * kCompute] = (float)(pc.cst - (double)h);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = (float)pc.C[j];
+  }
 
   if (tid == 0) {
     s_kmax = 0;
     s_bad = 0;
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&bbar[b], 1);
+      tc::mbar_init(&full[b], kCompute);
       tc::mbar_init(&mbar[b], 1);
+      s_done[b] = 0;
+      s_issued_b[b] = 0;
+      s_issued_m[b] = 0;
     }
     tc::mbar_fence_init();
   }
@@ -182,18 +316,32 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
 
   unsigned char* sA = sm + kOffA;
   unsigned char* sB = sm + kOffB;
-  float4* sCd = reinterpret_cast<float4*>(sm + kOffC);
   const float* tiles = a.ttiles;
-  int issued_b[2] = {0, 0}, issued_m[2] = {0, 0};  // thread 0's bookkeeping
-  if (tid == 0) {
-    for (int kb = 0; kb < 2 && kb < nkb; ++kb) {
-      tc::mbar_expect_tx(&bbar[kb], 2 * kTileBytes);
-      tc::bulk_g2s(sB + kb * 2 * kTileBytes, tiles + (int64_t)kb * 2 * 4096, kTileBytes, &bbar[kb]);
-      tc::bulk_g2s(sB + kb * 2 * kTileBytes + kTileBytes, tiles + (int64_t)kb * 2 * 4096 + 4096, kTileBytes,
-                   &bbar[kb]);
-      ++issued_b[kb];
+  // twiddle tiles of block kb into buffer kb & 1 (one thread)
+  auto load_b = [&](int kb) {
+    const int b = kb & 1;
+    tc::mbar_expect_tx(&bbar[b], 2 * kTileBytes);
+    tc::bulk_g2s(sB + b * 2 * kTileBytes, tiles + (int64_t)kb * 2 * 4096, kTileBytes, &bbar[b]);
+    tc::bulk_g2s(sB + b * 2 * kTileBytes + kTileBytes, tiles + (int64_t)kb * 2 * 4096 + 4096, kTileBytes, &bbar[b]);
+    ++s_issued_b[b];
+  };
+  if (tid == 0 && nkb > 0) load_b(0);
+  bool bad = false;
+  float zacc[kTimeShifts];  // this sample's Re z_j, summed over drained segments (round to nearest)
+#pragma unroll
+  for (int j = 0; j < kTimeShifts; ++j) zacc[j] = 0.f;
+  // this thread's row (its tile, its warp's lane quarter): main at column 0, correction at 128
+  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(tile * 2 * kTimeShifts);
+  auto drain = [&](int which) {
+    const uint32_t base = tbase + (uint32_t)(which * kTimeShifts);
+#pragma unroll
+    for (int c0 = 0; c0 < kTimeShifts; c0 += 32) {
+      uint32_t r[32];
+      tc::tmem_ld32(base + c0, r);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) zacc[c0 + i] += __uint_as_float(r[i]);
     }
-  }
+  };
 
   State st;
   st.acc = 0;
@@ -203,96 +351,114 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] = 0.f;
   int blk = -1;
   int32_t blk_end = 0;
-  bool bad = false;
-  float zacc[kTimeShifts];  // this sample's Re z_j, summed over drained segments (round to nearest)
+  uint32_t cnt[nrow], stepd[nrow];
+  float epsd[nrow];
+  float2 u2 = make_float2(0.f, 1.f);
 #pragma unroll
-  for (int j = 0; j < kTimeShifts; ++j) zacc[j] = 0.f;
+  for (int d = 0; d < nrow; ++d) {
+    cnt[d] = 0;
+    stepd[d] = 0;
+    epsd[d] = 0.f;
+  }
   for (int32_t kb = 0; kb < nkb; ++kb) {
     const int b = kb & 1;
     if (kb >= 2) {
+      // A[b] is free once the MMAs of block kb - 2 completed
       const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)(((kb - 2) >> 1) & 1));
-      if (__syncthreads_or(!ok || s_bad)) {
+      if (__any_sync(0xffffffffu, !ok || s_bad)) {
         bad = true;
         break;
       }
-      if (tid == 0) {
-        tc::mbar_expect_tx(&bbar[b], 2 * kTileBytes);
-        tc::bulk_g2s(sB + b * 2 * kTileBytes, tiles + (int64_t)kb * 2 * 4096, kTileBytes, &bbar[b]);
-        tc::bulk_g2s(sB + b * 2 * kTileBytes + kTileBytes, tiles + (int64_t)kb * 2 * 4096 + 4096, kTileBytes,
-                     &bbar[b]);
-        ++issued_b[b];
-      }
     }
-    // data tables of this K-block, per detector and bin pair: (re_k, re_k+1, im_k, im_k+1)
-    float4* cst = sCd + b * kMaxDet * (kKBlockBins / 2);
-    if (tid < nrow * (kKBlockBins / 2)) {
-      const int d = tid / (kKBlockBins / 2), pp = tid % (kKBlockBins / 2);
-      const float4 c = reinterpret_cast<const float4*>(a.cdet32)[((int64_t)d * a.n_pad16 + kb * kKBlockBins) / 2 + pp];
-      cst[d * (kKBlockBins / 2) + pp] = make_float4(c.x, c.z, c.y, c.w);
-    }
-    __syncthreads();
-    // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes.
-    // Bins go in pairs (plan blocks have even starts), two lanes of f32x2 arithmetic.
-    unsigned char* rowA = sA + (b * kTilesPerCta + tile) * 2 * kTileBytes + row * 128;
+    const float4* tab = reinterpret_cast<const float4*>(a.cdet32) + (int64_t)kb * (kKBlockBins / 2);
+      // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes.
+      // Bins go in pairs (plan blocks have even starts), two lanes of f32x2 arithmetic.
+      unsigned char* rowA = sA + (b * kTilesPerCta + tile) * 2 * kTileBytes + row * 128;
 #pragma unroll 1
-    for (int kk = 0; kk < kKBlockBins; kk += 2) {
-      const int32_t k = kb * kKBlockBins + kk;
-      if (k < kcut && k == blk_end) {
-        ++blk;
-        enter_block(a.plan, blk, pc, cf, st);
-        blk_end = a.plan[blk].k1;
-      }
-      float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
-      if (k < kcut) {
-        const float2 w = make_float2(st.w, st.w + 1.0f);
-        float2 R = __ffma2_rn(f2(st.c[5]), w, f2(st.c[4]));
-        R = __ffma2_rn(R, w, f2(st.c[3]));
-        R = __ffma2_rn(R, w, f2(st.c[2]));
-        R = __ffma2_rn(R, w, f2(st.c[1]));
-        R = __ffma2_rn(R, w, f2(st.c[0]));
+      for (int kk = 0; kk < kKBlockBins; kk += 2) {
+        const int32_t k = kb * kKBlockBins + kk;
+        if (k < kcut && k == blk_end) {
+          ++blk;
+          if constexpr (kFF)
+            enter_block_ff(a.plan, blk, pf, st);
+          else
+            enter_block(a.plan, blk, pc, cf, st);
+          blk_end = a.plan[blk].k1;
+          // per-detector 32-bit turn counters from the block's first bin; the fraction of a
+          // counter unit they drop per bin enters the angle as a small FP32 slope
 #pragma unroll
-        for (int d = 0; d < kMaxDet; ++d) {
-          if (d < nrow) {
-            const uint32_t o0 = (uint32_t)(off[d] >> 32), o1 = (uint32_t)((off[d] + stp[d]) >> 32);
-            const float2 f1 = make_float2(mantissa_turn(st.acc + o0), mantissa_turn(st.acc + st.step + o1));
-            const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), R);
-            float2 sn, cs;
-            __sincosf(ang.x, &sn.x, &cs.x);
-            __sincosf(ang.y, &sn.y, &cs.y);
-            const float4 c = cst[d * (kKBlockBins / 2) + (kk >> 1)];
-            const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
-            const float2 q = __fmul2_rn(f2(pmag[d]), cs), r = __fmul2_rn(f2(pmag[d]), sn);
-            re = __ffma2_rn(cx, q, __ffma2_rn(cy, r, re));
-            imc = __ffma2_rn(cy, q, imc);
-            ims = __ffma2_rn(cx, r, ims);
+          for (int d = 0; d < nrow; ++d) {
+            const uint64_t od = off[d] + (uint64_t)(uint32_t)k * stp[d];
+            cnt[d] = st.acc + (uint32_t)(od >> 32);
+            stepd[d] = st.step + (uint32_t)(stp[d] >> 32);
+            epsd[d] = (float)(uint32_t)stp[d] * (kTwoPiF * 5.421010862427522e-20f);  // 2 pi 2^-64
+          }
+          u2 = make_float2(0.f, 1.f);
+        }
+        float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
+        if (k < kcut) {
+          const float2 w = make_float2(st.w, st.w + 1.0f);
+          float2 R = __ffma2_rn(f2(st.c[5]), w, f2(st.c[4]));
+          R = __ffma2_rn(R, w, f2(st.c[3]));
+          R = __ffma2_rn(R, w, f2(st.c[2]));
+          R = __ffma2_rn(R, w, f2(st.c[1]));
+          R = __ffma2_rn(R, w, f2(st.c[0]));
+#pragma unroll
+          for (int d = 0; d < nrow; ++d) {
+            {
+              const float2 f1 = make_float2(mantissa_turn(cnt[d]), mantissa_turn(cnt[d] + stepd[d]));
+              const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), __ffma2_rn(f2(epsd[d]), u2, R));
+              cnt[d] += 2u * stepd[d];
+              float2 sn, cs;
+              __sincosf(ang.x, &sn.x, &cs.x);
+              __sincosf(ang.y, &sn.y, &cs.y);
+              const float4 c = __ldg(tab + (int64_t)d * (a.n_pad16 / 2) + (kk >> 1));  // re_k, re_k+1, im_k, im_k+1
+              const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
+              const float2 q = __fmul2_rn(f2(pmag[d]), cs), r = __fmul2_rn(f2(pmag[d]), sn);
+              re = __ffma2_rn(cx, q, __ffma2_rn(cy, r, re));
+              imc = __ffma2_rn(cy, q, imc);
+              ims = __ffma2_rn(cx, r, ims);
+            }
+          }
+          if (k + 1 >= kcut) {  // odd cut: the second bin of the pair is beyond the ISCO
+            re.y = 0.f;
+            imc.y = 0.f;
+            ims.y = 0.f;
           }
         }
-        if (k + 1 >= kcut) {  // odd cut: the second bin of the pair is beyond the ISCO
-          re.y = 0.f;
-          imc.y = 0.f;
-          ims.y = 0.f;
-        }
+        st.w += 2.0f;
+        u2 = __fadd2_rn(u2, f2(2.0f));
+        const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
+        float4 hi, lo;
+        hi.x = tc::tf32_round(re.x); lo.x = re.x - hi.x;
+        hi.y = tc::tf32_round(im.x); lo.y = im.x - hi.y;
+        hi.z = tc::tf32_round(re.y); lo.z = re.y - hi.z;
+        hi.w = tc::tf32_round(im.y); lo.w = im.y - hi.w;
+        const int chunk = (kk >> 1) ^ (row & 7);
+        *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
+        *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;
       }
-      st.acc += 2u * st.step;
-      st.w += 2.0f;
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) off[d] += 2 * stp[d];
-      const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
-      float4 hi, lo;
-      hi.x = tc::tf32_round(re.x); lo.x = re.x - hi.x;
-      hi.y = tc::tf32_round(im.x); lo.y = im.x - hi.y;
-      hi.z = tc::tf32_round(re.y); lo.z = re.y - hi.z;
-      hi.w = tc::tf32_round(im.y); lo.w = im.y - hi.w;
-      const int chunk = (kk >> 1) ^ (row & 7);
-      *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
-      *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;
+    if (kb >= 1 && kb % kSegBlocks == 0) {
+      // the segment that ended with block kb - 1: drain the main accumulator before the MMAs
+      // of block kb start it afresh
+      const bool ok = tc::mbar_wait(&mbar[(kb - 1) & 1], (uint32_t)(((kb - 1) >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok || s_bad)) {
+        bad = true;
+        break;
+      }
+      tc::fence_after_sync();
+      drain(0);
+      tc::fence_before_sync();
     }
     tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      if (!tc::mbar_wait(&bbar[b], (uint32_t)((kb >> 1) & 1))) {
-        s_bad = 1;
-      } else {
+    tc::mbar_arrive(&full[b]);
+    if (atomicAdd(&s_done[b], 1) == kCompute - 1) {
+      // last thread of this block: issue its MMAs, then the next block's twiddle copies
+      atomicExch(&s_done[b], 0);
+      __threadfence_block();
+      const uint32_t par = (uint32_t)((kb >> 1) & 1);
+      bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar[b], par);
+      if (ok) {
         tc::fence_after_sync();
         const uint32_t a_base = tc::smem_addr(sA + b * kTilesPerCta * 2 * kTileBytes);
         const uint32_t b_base = tc::smem_addr(sB + b * 2 * kTileBytes);
@@ -303,35 +469,49 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
           for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
             for (int term = 0; term < 3; ++term) {
-              // head.head into the main accumulator, the two correction terms into their own
+              // head.head into the main accumulator, head.tail and tail.head into the correction
               const uint32_t aa = a_base + t * 2 * kTileBytes + (term == 2 ? kTileBytes : 0) + ks * 32;
               const uint32_t bb = b_base + (term == 1 ? kTileBytes : 0) + ks * 32;
               const uint32_t d = tmem + t * 2 * kTimeShifts + (term == 0 ? 0 : kTimeShifts);
-              const bool fresh = seg_first && ks == 0 && term <= 1;
+              const bool fresh = ks == 0 && (term == 0 ? seg_first : (kb == 0 && term == 1));
               tc::mma_tf32(d, tc::desc_k_sw128(aa), tc::desc_k_sw128(bb), kIdesc, fresh ? 0u : 1u);
             }
         tc::commit(&mbar[b]);
-        ++issued_m[b];
+        ++s_issued_m[b];
+        // buffer b ^ 1 is free once the MMAs of block kb - 1 completed
+        if (kb + 1 < nkb) {
+          ok = kb < 1 || tc::mbar_wait(&mbar[b ^ 1], (uint32_t)(((kb - 1) >> 1) & 1));
+          if (ok) load_b(kb + 1);
+        }
+      }
+      if (!ok) {
+        s_bad = 1;
+        atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
       }
     }
-    // drain the TMEM accumulators into FP32 registers every kSegBlocks blocks (and at the end)
-    if ((kb + 1) % kSegBlocks == 0 || kb == nkb - 1) {
-      const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)((kb >> 1) & 1));
-      if (__syncthreads_or(!ok || s_bad)) {
-        bad = true;
-        break;
-      }
+  }
+  if (!bad && nkb > 0) {
+    // the last segment and the corrections, once the last MMAs (and so all) completed
+    const bool ok = tc::mbar_wait(&mbar[(nkb - 1) & 1], (uint32_t)(((nkb - 1) >> 1) & 1));
+    if (__any_sync(0xffffffffu, !ok || s_bad)) {
+      bad = true;
+    } else {
       tc::fence_after_sync();
-      const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(tile * 2 * kTimeShifts);
-#pragma unroll
-      for (int c0 = 0; c0 < kTimeShifts; c0 += 32) {
-        uint32_t rm[32], rc[32];
-        tc::tmem_ld32(base + c0, rm);
-        tc::tmem_ld32(base + kTimeShifts + c0, rc);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) zacc[c0 + i] += __uint_as_float(rm[i]) + __uint_as_float(rc[i]);
-      }
+      drain(0);
+      drain(1);
       tc::fence_before_sync();
+    }
+  }
+  if (bad) {
+    s_bad = 1;
+    atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
+  }
+  __syncthreads();
+  if (tid == 0 && s_bad) {
+    // let every copy and MMA issued land (bounded) before the CTA releases its memory
+    for (int b = 0; b < 2; ++b) {
+      if (s_issued_b[b] > 0) (void)tc::mbar_wait(&bbar[b], (uint32_t)((s_issued_b[b] - 1) & 1), 1000000000ull);
+      if (s_issued_m[b] > 0) (void)tc::mbar_wait(&mbar[b], (uint32_t)((s_issued_m[b] - 1) & 1), 1000000000ull);
     }
   }
   double ll = 0.0;
@@ -348,34 +528,41 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   } else if (!bad) {
     ll = -0.5 * H;
   }
-  if (bad && tid == 0) {
-    atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
-    // let outstanding copies and MMAs finish (bounded) before the CTA releases its memory
-    for (int b = 0; b < 2; ++b) {
-      if (issued_b[b] > 0) (void)tc::mbar_wait(&bbar[b], (uint32_t)((issued_b[b] - 1) & 1), 1000000000ull);
-      if (issued_m[b] > 0) (void)tc::mbar_wait(&mbar[b], (uint32_t)((issued_m[b] - 1) & 1), 1000000000ull);
-    }
-  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc<512>(tmem);
-  if (active) a.out[s] = bad ? NAN : (valid ? ll : -INFINITY);
+  if (active) a.out[s] = (bad || s_bad) ? NAN : (valid ? ll : -INFINITY);
+}
+
+template <bool kFF, int kRows>
+cudaError_t launch_time(const LikeArgs& a, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(loglike_mixed_time_kernel<kFF, kRows>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t blocks = (a.n + kCompute - 1) / kCompute;
+  loglike_mixed_time_kernel<kFF, kRows><<<(unsigned)blocks, kTT, kSmemBytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool kFF>
+cudaError_t launch_time_rows(const LikeArgs& a, cudaStream_t s) {
+  switch (a.fold ? 1 : a.n_det) {
+    case 1: return launch_time<kFF, 1>(a, s);
+    case 2: return launch_time<kFF, 2>(a, s);
+    case 3: return launch_time<kFF, 3>(a, s);
+    default: return launch_time<kFF, 4>(a, s);
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_loglike_mixed_time(const LikeArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(loglike_mixed_time_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int64_t blocks = (a.n + kTT - 1) / kTT;
-  loglike_mixed_time_kernel<<<(unsigned)blocks, kTT, kSmemBytes, s>>>(a);
-  return cudaGetLastError();
+  return a.ff_phase ? launch_time_rows<true>(a, s) : launch_time_rows<false>(a, s);
 }
 
 }  // namespace mbis

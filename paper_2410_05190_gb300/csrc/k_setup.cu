@@ -130,13 +130,18 @@ __global__ void twiddle_kernel(int32_t n, double f_lo, double df, int32_t J, dou
 }
 
 // per-detector FP32 tables, scaled, zero-padded to n_pad: [rows][n_pad]
+// rows of n complex values -> FP32, padded to n_pad (even) bins, bin pairs interleaved as
+// (re_k, re_k+1, im_k, im_k+1) so that a pair loads as one 16-byte vector of two f32x2 lanes
 __global__ void rows_to_f32_kernel(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
                                    float2* out) {
   const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t r = blockIdx.y;
   if (k >= n_pad || r >= rows) return;
   const double2 v = k < n ? c[(int64_t)r * n + k] : make_double2(0.0, 0.0);
-  out[(int64_t)r * n_pad + k] = make_float2((float)(v.x * inv_scale), (float)(v.y * inv_scale));
+  float* row = reinterpret_cast<float*>(out + (int64_t)r * n_pad);
+  const int32_t p = k >> 1, e = k & 1;
+  row[4 * p + e] = (float)(v.x * inv_scale);
+  row[4 * p + 2 + e] = (float)(v.y * inv_scale);
 }
 
 __device__ __forceinline__ float tf32_round(float x) {

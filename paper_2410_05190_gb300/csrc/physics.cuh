@@ -45,9 +45,9 @@ MBIS_HD double total_mass_seconds(double mc, double q) {
   return mc * kTsun * pow(1.0 + q, 1.2) * pow(q, -0.6);
 }
 
-// m_sec: total mass in seconds, total_mass_seconds(mc, q)
-MBIS_HD PhaseCoeffs phase_coeffs_m(double mc, double q, double chi1, double chi2, double tc, double phic,
-                                   double m_sec) {
+// a = pi M (M the total mass in seconds), la = ln a, a13 = a^(1/3), taken by the caller
+MBIS_HD PhaseCoeffs phase_coeffs_a(double q, double chi1, double chi2, double tc, double phic, double a, double la,
+                                   double a13) {
   const double eta = q / ((1.0 + q) * (1.0 + q));
   const double dm = (q - 1.0) / (q + 1.0);  // (m1 - m2) / M
   const double xs = 0.5 * (chi1 + chi2), xa = 0.5 * (chi1 - chi2);
@@ -76,9 +76,7 @@ MBIS_HD PhaseCoeffs phase_coeffs_m(double mc, double q, double chi1, double chi2
                       dm * (-25150083775.0 / 3048192.0 + 26804935.0 / 6048.0 * eta - 1985.0 / 48.0 * e2) * xa;
 
   // v = (a f)^(1/3) with a = pi M;  v^n = a^(n/3) f^(n/3);  3 ln v = ln a + ln f
-  const double a = kPi * m_sec;
-  const double la = log(a);
-  const double a13 = cbrt(a), a23 = a13 * a13;
+  const double a23 = a13 * a13;
   const double pre = 3.0 / (128.0 * eta) / kTwoPi;  // turns
   PhaseCoeffs pc;
   pc.C[0] = pre / (a23 * a23 * a13);                 // a^(-5/3)   f^(-5/3)
@@ -92,6 +90,14 @@ MBIS_HD PhaseCoeffs phase_coeffs_m(double mc, double q, double chi1, double chi2
   pc.C[8] = tc;                                      // f
   pc.cst = -phic / kTwoPi - 0.125 + pre * c5 * (1.0 + la);
   return pc;
+}
+
+// m_sec: total mass in seconds, total_mass_seconds(mc, q)
+MBIS_HD PhaseCoeffs phase_coeffs_m(double mc, double q, double chi1, double chi2, double tc, double phic,
+                                   double m_sec) {
+  (void)mc;
+  const double a = kPi * m_sec;
+  return phase_coeffs_a(q, chi1, chi2, tc, phic, a, log(a), cbrt(a));
 }
 
 MBIS_HD PhaseCoeffs phase_coeffs(double mc, double q, double chi1, double chi2, double tc, double phic) {

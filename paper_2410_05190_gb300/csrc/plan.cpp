@@ -59,6 +59,10 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
   for (int j = 0; j < kNumBasis; ++j) {
     b.B[j] = basis(j, fc);
     b.dB[j] = basis_deriv(j, fc) * in.df;
+    b.Bh[j] = (float)b.B[j];
+    b.Bl[j] = (float)(b.B[j] - (double)b.Bh[j]);
+    b.dBh[j] = (float)b.dB[j];
+    b.dBl[j] = (float)(b.dB[j] - (double)b.dBh[j]);
   }
   const double wa = (double)(k0 - b.kc), wb = (double)(k0 + S - 1 - b.kc);
   const double h = std::max(1.0, std::max(std::fabs(wa), std::fabs(wb)));

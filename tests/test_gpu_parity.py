@@ -301,6 +301,9 @@ def test_bbh_time_marginalised_tensor_core_matches_oracle(m, torch, bbh):
         logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
         ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], theta, th))
         got = gpu_loglike(m, torch, ctx, theta)
+        inside = np.isfinite(logp)
+        print(f"tensor-core time marginalisation: max |delta log L| = {np.abs(got - ref)[inside].max():.2e}, "
+              f"mean signed {np.mean((got - ref)[inside]):+.2e}")
         compare_loglike(got, ref, logp)
     finally:
         m.mbis_destroy(ctx)
