@@ -209,8 +209,9 @@ mbis_status mbis_run_to_ess(mbis_ctx* ctx, const mbis_ess_options* opts, double*
 
 typedef struct mbis_batch mbis_batch;
 
-/* A batch of events whose likelihoods run in one persistent launch: the 128-sample tiles of
- * every event form one work list, longest first, consumed by a persistent grid; a step
+/* A batch of events whose likelihoods run in one persistent launch (one per block-entry
+ * arithmetic, float-float or FP64): the 128-sample tiles of every event form a work list,
+ * longest first, consumed by a persistent grid; a step
  * (draws, likelihoods, reductions, summaries of every event) is one CUDA graph replay.
  * ctxs: n_ctx contexts with a metric set, MBIS_MIXED, fixed sky/orientation, PHASE or
  * PHASE|DISTANCE marginalisation (they stay owned by the caller and must outlive the

@@ -1,13 +1,15 @@
 // batch.cu -- many events in one persistent likelihood launch, one CUDA graph per step.
 //
 // Events of uneven size (frequency grids of 2k-128k bins, 2 or 3 detectors, 2^14-2^20
-// samples) share the GPU in a single launch: their 128-sample tiles form one work list,
-// ordered longest first (estimated live bins), that a persistent grid of CTAs consumes
-// through a device counter.  One step -- upload of the Philox counters, the draws of every
+// samples) share the GPU in one persistent launch per block-entry arithmetic (float-float
+// or FP64; most events take the first): their 128-sample tiles form a work list, ordered
+// longest first (estimated live bins), that a persistent grid of CTAs consumes through a
+// device counter.  One step -- upload of the Philox counters, the draws of every
 // event, the persistent likelihood launch, the two-pass reduction of every event and the
 // copy of the summaries to pinned host memory -- is captured once in a CUDA graph and
 // replayed.  The size of the persistent grid is picked by timing candidates (autotuner).
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <new>
 #include <string>
@@ -25,9 +27,9 @@ struct mbis_batch {
   std::vector<uint64_t> seeds;
   std::vector<double*> theta, logq, logp, ll;
   LikeArgs* d_args = nullptr;
-  BatchItem* d_items = nullptr;
-  int32_t n_items = 0;
-  int32_t* d_next = nullptr;
+  BatchItem* d_items = nullptr;  // float-float-entry events' tiles first, then FP64-entry ones
+  int32_t n_items = 0, n_ff = 0;
+  int32_t* d_next = nullptr;     // one work counter per group
   uint64_t* d_ctr = nullptr;
   uint64_t* h_ctr = nullptr;  // pinned
   double* h_res = nullptr;    // pinned, 4 per event
@@ -52,6 +54,45 @@ mbis_status berr(mbis_status st, const std::string& m) {
                   std::string("mbis_batch: ") + #call + ": " + cudaGetErrorString(e_));        \
   } while (0)
 
+// The work list: every event's 128-sample tiles, longest first (live bins at the proposal
+// mean), in two groups by block-entry arithmetic -- each group runs in its own persistent
+// launch.  Rebuilt when a context is re-targeted.
+mbis_status build_items(mbis_batch* b) {
+  struct Cost {
+    double cost;
+    BatchItem item;
+  };
+  std::vector<Cost> g[2];
+  for (int i = 0; i < b->n; ++i) {
+    const mbis_ctx* c = b->ctx[i];
+    double mc = c->fixed[kMc], q = c->fixed[kQ];
+    for (int p = 0; p < c->P; ++p) {
+      if (c->ids[p] == kMc) mc = c->mean[p];
+      if (c->ids[p] == kQ) q = c->mean[p];
+    }
+    const double live = (double)live_bins(mc, q > 0 ? q : 1.0, c->f_lo, c->df, c->n_bins);
+    const int32_t tiles = (int32_t)((b->ns[i] + kMixedThreads - 1) / kMixedThreads);
+    for (int32_t t = 0; t < tiles; ++t) g[c->ff_phase ? 0 : 1].push_back({live, {i, t}});
+  }
+  std::vector<BatchItem> list;
+  for (auto& v : g) {
+    std::stable_sort(v.begin(), v.end(), [](const Cost& x, const Cost& y) { return x.cost > y.cost; });
+    for (const Cost& c : v) list.push_back(c.item);
+  }
+  b->n_ff = (int32_t)g[0].size();
+  if ((int32_t)list.size() != b->n_items) return berr(MBIS_E_STATE, "mbis_batch: work list size changed");
+  B_TRY(cudaMemcpy(b->d_items, list.data(), sizeof(BatchItem) * list.size(), cudaMemcpyHostToDevice));
+  return MBIS_OK;
+}
+
+cudaError_t launch_items(mbis_batch* b, cudaStream_t s) {
+  cudaError_t e = launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_ff, b->d_next, b->grid, true, s);
+  if (e == cudaSuccess)
+    e = launch_loglike_mixed_batch(b->d_args, b->d_items + b->n_ff, b->n_items - b->n_ff, b->d_next + 1, b->grid,
+                                   false, s);
+  return e;
+}
+
 // enqueue one step on b->stream (also used inside stream capture)
 mbis_status enqueue_step(mbis_batch* b) {
   B_TRY(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(uint64_t) * b->n, cudaMemcpyHostToDevice, b->stream));
@@ -60,7 +101,7 @@ mbis_status enqueue_step(mbis_batch* b) {
     da.d_ctr0 = b->d_ctr + i;
     B_TRY(launch_draw(da, b->stream));
   }
-  B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid, b->stream));
+  B_TRY(launch_items(b, b->stream));
   for (int i = 0; i < b->n; ++i) {
     B_TRY(launch_reduce(b->ns[i], b->ll[i], b->logp[i], b->logq[i], nullptr, b->ctx[i]->red, b->stream));
     B_TRY(cudaMemcpyAsync(b->h_res + 4 * i, b->ctx[i]->red.result, sizeof(double) * 4, cudaMemcpyDeviceToHost,
@@ -111,6 +152,7 @@ mbis_status refresh(mbis_batch* b) {
   B_TRY(cudaStreamSynchronize(b->stream));
   B_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * b->n, cudaMemcpyHostToDevice));
   for (int i = 0; i < b->n; ++i) b->gen[i] = b->ctx[i]->gen;
+  if (const mbis_status st = build_items(b); st != MBIS_OK) return st;
   return capture(b);
 }
 
@@ -153,11 +195,7 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
   } while (0)
   C_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
   std::vector<LikeArgs> args(n_ctx);
-  struct Cost {
-    double cost;
-    BatchItem item;
-  };
-  std::vector<Cost> items;
+  int64_t total_tiles = 0;
   for (int i = 0; i < n_ctx; ++i) {
     const mbis_ctx* c = ctxs[i];
     const int64_t n = n_samples[i];
@@ -166,31 +204,25 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
     C_TRY(cudaMalloc(&b->logp[i], sizeof(double) * n));
     C_TRY(cudaMalloc(&b->ll[i], sizeof(double) * n));
     args[i] = make_like_args(c, n, b->theta[i], b->ll[i]);
-    // estimated work of a tile: live bins at the proposal mean
-    double mc = c->fixed[kMc], q = c->fixed[kQ];
-    for (int p = 0; p < c->P; ++p) {
-      if (c->ids[p] == kMc) mc = c->mean[p];
-      if (c->ids[p] == kQ) q = c->mean[p];
-    }
-    const double live = (double)live_bins(mc, q > 0 ? q : 1.0, c->f_lo, c->df, c->n_bins);
-    const int32_t tiles = (int32_t)((n + kMixedThreads - 1) / kMixedThreads);
-    for (int32_t t = 0; t < tiles; ++t) items.push_back({live, {i, t}});
+    total_tiles += (n + kMixedThreads - 1) / kMixedThreads;
   }
-  std::stable_sort(items.begin(), items.end(), [](const Cost& x, const Cost& y) { return x.cost > y.cost; });
-  std::vector<BatchItem> list(items.size());
-  for (size_t k = 0; k < items.size(); ++k) list[k] = items[k].item;
-  b->n_items = (int32_t)list.size();
+  if (total_tiles > INT32_MAX) {
+    berr(MBIS_E_INVALID, "mbis_batch_create: more than 2^31 sample tiles");
+    return fail(MBIS_E_INVALID);
+  }
+  b->n_items = (int32_t)total_tiles;
   C_TRY(cudaMalloc(&b->d_args, sizeof(LikeArgs) * n_ctx));
   C_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * n_ctx, cudaMemcpyHostToDevice));
-  C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * list.size()));
-  C_TRY(cudaMemcpy(b->d_items, list.data(), sizeof(BatchItem) * list.size(), cudaMemcpyHostToDevice));
-  C_TRY(cudaMalloc(&b->d_next, sizeof(int32_t)));
+  C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)b->n_items));
+  C_TRY(cudaMalloc(&b->d_next, 2 * sizeof(int32_t)));
   C_TRY(cudaMalloc(&b->d_ctr, sizeof(uint64_t) * n_ctx));
   C_TRY(cudaMallocHost(&b->h_ctr, sizeof(uint64_t) * n_ctx));
   C_TRY(cudaMallocHost(&b->h_res, sizeof(double) * 4 * n_ctx));
   std::memset(b->h_ctr, 0, sizeof(uint64_t) * n_ctx);
 #undef C_TRY
-  const mbis_status st = capture(b);
+  mbis_status st = build_items(b);
+  if (st != MBIS_OK) return fail(st);
+  st = capture(b);
   if (st != MBIS_OK) return fail(st);
   *out = b;
   return MBIS_OK;
@@ -240,8 +272,7 @@ mbis_status mbis_batch_step(mbis_batch* b, uint64_t step, mbis_summary* out) {
 mbis_status mbis_batch_loglike(mbis_batch* b, void* stream) {
   if (!b) return berr(MBIS_E_INVALID, "mbis_batch_loglike: null batch");
   if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
-  B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid,
-                                   static_cast<cudaStream_t>(stream)));
+  B_TRY(launch_items(b, static_cast<cudaStream_t>(stream)));
   return MBIS_OK;
 }
 
@@ -282,7 +313,7 @@ mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out)
     float t = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
       B_TRY(cudaEventRecord(e0, b->stream));
-      B_TRY(launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_items, b->d_next, b->grid, b->stream));
+      B_TRY(launch_items(b, b->stream));
       B_TRY(cudaEventRecord(e1, b->stream));
       B_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;

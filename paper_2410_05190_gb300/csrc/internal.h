@@ -131,8 +131,9 @@ cudaError_t launch_to_f32(const double2* c, int32_t n, int32_t n_pad, double inv
 cudaError_t launch_draw(const DrawArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_fp64(const LikeArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s);
+// items of events that all enter anchor blocks in float-float (ff) or all in FP64
 cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
-                                      int32_t grid, cudaStream_t s);
+                                      int32_t grid, bool ff, cudaStream_t s);
 
 // two-pass weight reduction; partials / counter / result are device scratch
 struct ReduceScratch {

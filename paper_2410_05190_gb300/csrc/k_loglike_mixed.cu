@@ -9,7 +9,8 @@
 // same pair at the same time (one LDS.128 broadcast per two bins).
 //
 // Phase per bin (anchor blocks, see plan.cpp): at the start of a block each thread forms,
-// in FP64, the linear phase X + (k - kc) Y, reduces it modulo one turn and keeps it as a
+// in FP64 (or in float-float arithmetic when the event's phase terms stay below
+// kFloatFloatMaxTurns), the linear phase X + (k - kc) Y, reduces it modulo one turn and keeps it as a
 // 32-bit fixed-point turn count (exact wrap-around on integer add), and forms in FP32 the
 // coefficients of the degree-5 remainder polynomial.  The FP64 rounding residuals of the
 // fixed-point value and slope are folded into that polynomial.  Bins are taken in pairs
@@ -18,6 +19,7 @@
 // a complex multiply-accumulate with C_k.  Per-chunk FP32 partial sums are accumulated in
 // FP64.  The per-sample FP64 phase coefficients wait in shared memory between blocks so
 // the loop keeps few registers (two CTAs more per SM).
+#include "ffloat.cuh"
 #include "internal.h"
 #include "marg.cuh"
 
@@ -120,16 +122,63 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.w = (float)w0;
 }
 
+// The same entry in float-float arithmetic (events whose phase terms stay below
+// kFloatFloatMaxTurns; no FP64).  pf is this thread's column (stride kMixedThreads): C_j hi
+// at row j, cst hi at row kNumBasis, C_j lo at row kNumBasis + 1 + j, cst lo at the last.
+__device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ plan, int blk, const float* pf,
+                                               BlockState& st) {
+  constexpr int S = kMixedThreads, L = kNumBasis + 1;
+  const AnchorBlock& B = plan[blk];
+  float xh = pf[kNumBasis * S], xl = pf[(L + kNumBasis) * S], yh = 0.f, yl = 0.f;
+#pragma unroll
+  for (int j = 0; j < kNumBasis; ++j) {
+    const float ch = pf[j * S], cl = pf[(L + j) * S];
+    ff_mac(ch, cl, B.Bh[j], B.Bl[j], xh, xl);
+    ff_mac(ch, cl, B.dBh[j], B.dBl[j], yh, yl);
+  }
+  two_sum(yh, yl, yh, yl);
+  const float w0 = (float)(B.k0 - B.kc);
+  ff_mac(w0, 0.f, yh, yl, xh, xl);  // linear phase at the first bin of the block, turns
+  two_sum(xh, xl, xh, xl);
+  float r0, r1;
+  st.acc = ff_frac32(xh, xl, r0) + 256u;
+  st.step = ff_frac32(yh, yl, r1);
+#pragma unroll
+  for (int m = 0; m <= kRemDeg; ++m) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * S], B.E[j][m], s);
+    st.c[m] = s;
+  }
+  st.c[0] += r0 - w0 * r1;
+  st.c[1] += r1;
+#pragma unroll
+  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  st.c[0] -= kTwoPiF;
+  st.w = w0;
+}
+
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
+
+// Shared memory of one CTA (declared once per kernel, so the persistent launch's two
+// instantiations of fold_tile share it).
+struct FoldSmem {
+  __align__(128) float4 sC[kNbuf][kChunk / 2];
+  __align__(8) uint64_t bar[kNbuf];
+  double sPC[(kNumBasis + 1) * kMixedThreads];  // C_j and cst per thread (float pairs when kFF)
+  float sCF[(kNumBasis - 1) * kMixedThreads];   // FP32 copies of C_0..C_7 (FP64 entry only)
+  int s_kmax;
+};
 
 // One tile of 128 samples of one event.  `first` is false when the CTA has already run a
 // tile (persistent launch): the mbarriers are then invalidated and initialised afresh.
-__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first) {
-  __shared__ __align__(128) float4 sC[kNbuf][kChunk / 2];
-  __shared__ __align__(8) uint64_t bar[kNbuf];
-  __shared__ double sPC[(kNumBasis + 1) * kMixedThreads];  // C_j and cst per thread
-  __shared__ float sCF[(kNumBasis - 1) * kMixedThreads];   // FP32 copies of C_0..C_7
-  __shared__ int s_kmax;
+template <bool kFF>
+__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first, FoldSmem& sm) {
+  float4 (&sC)[kNbuf][kChunk / 2] = sm.sC;
+  uint64_t* bar = sm.bar;
+  double* sPC = sm.sPC;
+  float* sCF = sm.sCF;
+  int& s_kmax = sm.s_kmax;
   const int tid = threadIdx.x;
   const int64_t s = tile * kMixedThreads + tid;
   const bool active = s < a.n;
@@ -155,14 +204,28 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
       for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
       pc.cst = 0.0;
     }
+    if constexpr (kFF) {
+      float* pf = reinterpret_cast<float*>(sPC) + tid;
 #pragma unroll
-    for (int j = 0; j < kNumBasis; ++j) sPC[j * kMixedThreads + tid] = pc.C[j];
-    sPC[kNumBasis * kMixedThreads + tid] = pc.cst;
+      for (int j = 0; j < kNumBasis; ++j) {
+        const float h = (float)pc.C[j];
+        pf[j * kMixedThreads] = h;
+        pf[(kNumBasis + 1 + j) * kMixedThreads] = (float)(pc.C[j] - (double)h);
+      }
+      const float h = (float)pc.cst;
+      pf[kNumBasis * kMixedThreads] = h;
+      pf[(2 * kNumBasis + 1) * kMixedThreads] = (float)(pc.cst - (double)h);
+    } else {
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) sCF[j * kMixedThreads + tid] = (float)pc.C[j];
+      for (int j = 0; j < kNumBasis; ++j) sPC[j * kMixedThreads + tid] = pc.C[j];
+      sPC[kNumBasis * kMixedThreads + tid] = pc.cst;
+#pragma unroll
+      for (int j = 0; j < kNumBasis - 1; ++j) sCF[j * kMixedThreads + tid] = (float)pc.C[j];
+    }
   }
   const double* my_pc = sPC + tid;
   const float* my_cf = sCF + tid;
+  const float* my_pf = reinterpret_cast<const float*>(sPC) + tid;
 
   if (tid == 0) {
     s_kmax = 0;
@@ -206,7 +269,12 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
     while (k < ke) {
       if (k == blk_end) {
         ++blk;
-        if (k < kcut) enter_block(a.plan, blk, my_pc, my_cf, st);
+        if (k < kcut) {
+          if constexpr (kFF)
+            enter_block_ff(a.plan, blk, my_pf, st);
+          else
+            enter_block(a.plan, blk, my_pc, my_cf, st);
+        }
         blk_end = a.plan[blk].k1;
       }
       const int32_t seg_end = min(ke, blk_end);
@@ -300,17 +368,22 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   a.out[s] = ll;
 }
 
+template <bool kFF>
 __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
-  fold_tile(a, blockIdx.x, true);
+  __shared__ FoldSmem sm;
+  fold_tile<kFF>(a, blockIdx.x, true, sm);
 }
 
 // Persistent launch over the tiles of many events: each CTA takes (event, tile) items from a
 // device counter until the list is exhausted.  The host orders the list longest first, so
-// uneven events (2k-128k bins, 2^14-2^20 samples) balance across the SMs.
+// uneven events (2k-128k bins, 2^14-2^20 samples) balance across the SMs.  One launch
+// takes the events of one block-entry arithmetic (kFF), so each keeps its own registers.
+template <bool kFF>
 __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_batch_kernel(const LikeArgs* __restrict__ args,
                                                                                const BatchItem* __restrict__ items,
                                                                                int32_t n_items, int32_t* next) {
   __shared__ int s_item;
+  __shared__ FoldSmem sm;
   bool first = true;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
@@ -319,7 +392,7 @@ __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_batch_kernel(c
     __syncthreads();
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    fold_tile(args[item.ev], item.tile, first);
+    fold_tile<kFF>(args[item.ev], item.tile, first, sm);
     first = false;
     __syncthreads();
   }
@@ -328,18 +401,24 @@ __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_batch_kernel(c
 }  // namespace
 
 cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
-                                      int32_t grid, cudaStream_t s) {
+                                      int32_t grid, bool ff, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  loglike_mixed_batch_kernel<<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
+  if (ff)
+    loglike_mixed_batch_kernel<true><<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
+  else
+    loglike_mixed_batch_kernel<false><<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
   return cudaGetLastError();
 }
 
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const int64_t blocks = (a.n + kMixedThreads - 1) / kMixedThreads;
-  loglike_mixed_fold_kernel<<<(unsigned)blocks, kMixedThreads, 0, s>>>(a);
+  if (a.ff_phase)
+    loglike_mixed_fold_kernel<true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(a);
+  else
+    loglike_mixed_fold_kernel<false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@
 // the log-mean-exp.
 #include "internal.h"
 #include "marg.cuh"
+#include "ffloat.cuh"
 #include "tc.cuh"
 
 namespace mbis {
@@ -43,7 +44,7 @@ constexpr uint32_t kIdesc = tc::idesc_tf32(128, kTimeShifts);
 // finished), before the next segment's first MMA overwrites it.  The two split corrections,
 // ~2^-11 smaller, accumulate over the whole K range in a second accumulator.
 // TMEM: per tile [main 128 | correction 128] columns.
-constexpr int kSegBlocks = 4;
+constexpr int kSegBlocks = 2;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 struct State {
@@ -83,36 +84,6 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
   st.c[0] -= kTwoPiF;
   st.w = (float)w0;
-}
-
-// ---- float-float block entry (events whose phase terms stay below kFloatFloatMaxTurns).
-// A value is an unevaluated pair hi + lo of floats.  Sums use Knuth's two-sum (exact), the
-// product of a pair by a pair Dekker's product with the FMA giving the rounding error of
-// hi*hi exactly; explicit _rn intrinsics keep the compiler from contracting them.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (sh, sl) += (ch, cl) * (bh, bl)
-__device__ __forceinline__ void ff_mac(float ch, float cl, float bh, float bl, float& sh, float& sl) {
-  const float p = __fmul_rn(ch, bh);
-  const float e = __fmaf_rn(ch, bl, __fmaf_rn(cl, bh, __fmaf_rn(ch, bh, -p)));
-  float s, t;
-  two_sum(sh, p, s, t);
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(t, e));
-}
-
-// frac(h + l) as a 32-bit fixed-point turn count; resid (turns) is what the count rounds off
-__device__ __forceinline__ uint32_t ff_frac32(float h, float l, float& resid) {
-  const float fh = __fsub_rn(h, floorf(h));           // exact: a multiple of ulp(h) below one
-  const float xh = __fmul_rn(fh, 4294967296.0f);      // exact scalings by 2^32
-  const float xl = __fmul_rn(l, 4294967296.0f);
-  const float rh = rintf(xh), rl = rintf(xl);
-  resid = __fmul_rn(__fadd_rn(__fsub_rn(xh, rh), __fsub_rn(xl, rl)), 2.3283064365386963e-10f);
-  return (uint32_t)__float2ull_rn(rh) + (uint32_t)__float2int_rn(rl);
 }
 
 // Per-sample phase coefficients as float pairs, kept in shared memory (one column per
@@ -453,7 +424,10 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     tc::fence_proxy_async();
     tc::mbar_arrive(&full[b]);
     if (atomicAdd(&s_done[b], 1) == kCompute - 1) {
-      // last thread of this block: issue its MMAs, then the next block's twiddle copies
+      // The last thread done with this block issues its MMAs (issuing blocks the thread for
+      // about as long as the tensor core works on them, ~1.6k cycles; a first-finisher
+      // issuer, which has to wait for the others, measured slower), then the next block's
+      // twiddle copies.
       atomicExch(&s_done[b], 0);
       __threadfence_block();
       const uint32_t par = (uint32_t)((kb >> 1) & 1);
