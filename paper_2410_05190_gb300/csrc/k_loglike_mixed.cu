@@ -28,6 +28,11 @@ namespace {
 
 constexpr int kNbuf = 2;
 constexpr float kTwoPiF = 6.28318530717958647692f;
+// Added to the 32-bit turn count: 256 rounds (rather than truncates) when its top 23 bits
+// become a float mantissa f1 in [1, 2); 2^31 (half a turn) with the -3 pi in the remainder's
+// constant puts the angle 2 pi f1 - 3 pi + ... in [-pi, pi), where the MUFU sine and cosine
+// carry no mean phase error (over [0, 2 pi) they lag by ~1.7e-7 rad on average).
+constexpr uint32_t kTurnOffset = 0x80000000u + 256u;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -103,8 +108,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   const unsigned long long p1 = __double2ull_rn(fy * 4294967296.0);
   const double r0 = f0 - (double)p0 * 2.3283064365386963e-10;  // rounding residuals, turns
   const double r1 = fy - (double)p1 * 2.3283064365386963e-10;
-  // +256: round rather than truncate when the top 23 bits become the float mantissa
-  st.acc = (uint32_t)p0 + 256u;
+  st.acc = (uint32_t)p0 + kTurnOffset;
   st.step = (uint32_t)p1;
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) {
@@ -115,10 +119,10 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   }
   st.c[0] += (float)(r0 - w0 * r1);
   st.c[1] += (float)r1;
-  // angle = 2 pi (acc / 2^32) + 2 pi R = 2 pi f1 + (2 pi R - 2 pi), f1 = 1 + acc / 2^32
+  // angle = 2 pi (acc / 2^32) + 2 pi R = 2 pi f1 + (2 pi R - 3 pi), f1 = 1 + (acc + 2^31) / 2^32
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
-  st.c[0] -= kTwoPiF;
+  st.c[0] -= 1.5f * kTwoPiF;
   st.w = (float)w0;
 }
 
@@ -141,7 +145,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   ff_mac(w0, 0.f, yh, yl, xh, xl);  // linear phase at the first bin of the block, turns
   two_sum(xh, xl, xh, xl);
   float r0, r1;
-  st.acc = ff_frac32(xh, xl, r0) + 256u;
+  st.acc = ff_frac32(xh, xl, r0) + kTurnOffset;
   st.step = ff_frac32(yh, yl, r1);
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) {
@@ -154,7 +158,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.c[1] += r1;
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
-  st.c[0] -= kTwoPiF;
+  st.c[0] -= 1.5f * kTwoPiF;
   st.w = w0;
 }
 

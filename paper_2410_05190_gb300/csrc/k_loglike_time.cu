@@ -44,8 +44,13 @@ constexpr uint32_t kIdesc = tc::idesc_tf32(128, kTimeShifts);
 // finished), before the next segment's first MMA overwrites it.  The two split corrections,
 // ~2^-11 smaller, accumulate over the whole K range in a second accumulator.
 // TMEM: per tile [main 128 | correction 128] columns.
-constexpr int kSegBlocks = 2;
+constexpr int kSegBlocks = 1;
 constexpr float kTwoPiF = 6.28318530717958647692f;
+// Added to the 32-bit turn count: 256 rounds (rather than truncates) when its top 23 bits
+// become a float mantissa f1 in [1, 2); 2^31 (half a turn) with the -3 pi in the remainder's
+// constant puts the angle 2 pi f1 - 3 pi + ... in [-pi, pi), where the MUFU sine and cosine
+// carry no mean phase error (over [0, 2 pi) they lag by ~1.7e-7 rad on average).
+constexpr uint32_t kTurnOffset = 0x80000000u + 256u;
 
 struct State {
   uint32_t acc, step;
@@ -69,7 +74,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   const unsigned long long p1 = __double2ull_rn(fy * 4294967296.0);
   const double r0 = f0 - (double)p0 * 2.3283064365386963e-10;
   const double r1 = fy - (double)p1 * 2.3283064365386963e-10;
-  st.acc = (uint32_t)p0 + 256u;
+  st.acc = (uint32_t)p0 + kTurnOffset;
   st.step = (uint32_t)p1;
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) {
@@ -82,7 +87,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.c[1] += (float)r1;
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
-  st.c[0] -= kTwoPiF;
+  st.c[0] -= 1.5f * kTwoPiF;
   st.w = (float)w0;
 }
 
@@ -105,7 +110,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   ff_mac(w0, 0.f, yh, yl, xh, xl);  // phase at the block's first bin
   two_sum(xh, xl, xh, xl);
   float r0, r1;
-  st.acc = ff_frac32(xh, xl, r0) + 256u;
+  st.acc = ff_frac32(xh, xl, r0) + kTurnOffset;
   st.step = ff_frac32(yh, yl, r1);
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) {
@@ -118,7 +123,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.c[1] += r1;
 #pragma unroll
   for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
-  st.c[0] -= kTwoPiF;
+  st.c[0] -= 1.5f * kTwoPiF;
   st.w = w0;
 }
 
@@ -401,10 +406,12 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         u2 = __fadd2_rn(u2, f2(2.0f));
         const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
         float4 hi, lo;
-        hi.x = tc::tf32_round(re.x); lo.x = re.x - hi.x;
-        hi.y = tc::tf32_round(im.x); lo.y = im.x - hi.y;
-        hi.z = tc::tf32_round(re.y); lo.z = re.y - hi.z;
-        hi.w = tc::tf32_round(im.y); lo.w = im.y - hi.w;
+        // head and tail both rounded to TF32: the tensor core reads a TF32 operand by
+        // truncating an FP32 one, which would bias the tails toward zero
+        hi.x = tc::tf32_round(re.x); lo.x = tc::tf32_round(re.x - hi.x);
+        hi.y = tc::tf32_round(im.x); lo.y = tc::tf32_round(im.x - hi.y);
+        hi.z = tc::tf32_round(re.y); lo.z = tc::tf32_round(re.y - hi.z);
+        hi.w = tc::tf32_round(im.y); lo.w = tc::tf32_round(im.y - hi.w);
         const int chunk = (kk >> 1) ^ (row & 7);
         *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
         *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;

@@ -152,7 +152,8 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // Twiddle operand of the time-shift contraction, one 16-bin K-block per CTA, one shift per
 // thread: row j holds (cos, sin)(2 pi f_k tau_j) for the block's 16 bins, split into a TF32
-// head and an FP32 tail, each in the 128-byte-swizzled K-major layout that the tensor core
+// head and a tail (the remainder, rounded to TF32 as well), each in the 128-byte-swizzled
+// K-major layout that the tensor core
 // reads (16-byte chunk c of row j at byte j*128 + ((c ^ (j & 7)) << 4)).
 // out: [n_kb][2 (head, tail)][128 rows x 128 bytes].
 __global__ void twiddle_tiles_kernel(int32_t n, double f_lo, double df, double dt, int32_t n_kb, float* out) {
@@ -172,7 +173,7 @@ __global__ void twiddle_tiles_kernel(int32_t n, double f_lo, double df, double d
       const int word = j * 32 + (((chunk ^ (j & 7)) << 2) | pos);
       const float h = tf32_round(v[e]);
       head[word] = h;
-      tail[word] = v[e] - h;
+      tail[word] = tf32_round(v[e] - h);  // the tensor core would truncate an unrounded tail
     }
   }
 }

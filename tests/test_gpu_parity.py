@@ -307,3 +307,36 @@ def test_bbh_time_marginalised_tensor_core_matches_oracle(m, torch, bbh):
         compare_loglike(got, ref, logp)
     finally:
         m.mbis_destroy(ctx)
+
+
+def test_bbh_full_size_tensor_core_launch_sampled_outputs(m, torch, bbh):
+    """The benchmark's BBH launch: 2^18 samples of one event (11 parameters, 128 shifts) in
+    one call of the tcgen05 kernel; 200 sampled outputs (in and out of the prior box)
+    against the oracle, and no NaN anywhere."""
+    w, spec, ev, th, prop = bbh
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        n, P = 1 << 18, len(prop["ids"])
+        theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+        lq = torch.empty(n, dtype=torch.float64, device="cuda")
+        lp = torch.empty(n, dtype=torch.float64, device="cuda")
+        ll = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.mbis_draw(ctx, spec.draw_seed, 0, n, theta, lq, lp)
+        m.mbis_loglike(ctx, n, theta, ll)
+        torch.cuda.synchronize()
+        llh = ll.cpu().numpy()
+        assert not np.any(np.isnan(llh))
+        idx = np.random.default_rng(11).choice(n, 200, replace=False)
+        idx[0] = n - 1
+        th_s = theta.cpu().numpy()[:, idx]
+        ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], th_s, th))
+        logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], th_s)
+        # every sample with a physical parameter set, in or out of the prior box
+        phys = np.isfinite(ref)
+        d = np.abs(llh[idx] - ref)[phys]
+        print(f"full-size tensor-core launch: max |delta log L| = {d.max():.2e} over {phys.sum()} samples")
+        compare_loglike(llh[idx], ref, logp)
+        assert d.max() <= 2e-3
+    finally:
+        m.mbis_destroy(ctx)
