@@ -181,7 +181,8 @@ def run_gpu(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     w = workloads.bns_population(n_events=max(args.events * world, 1), n_samples=args.samples)
-    my_events = w.events[rank::world][: args.events]
+    from paper_2410_05190_gb300.dist import shard, max_over_ranks
+    my_events = shard(w.events, rank, world)[: args.events]
     dets_np = workloads.network(w.detectors)
     t_setup = time.time()
     evs = [event_setup(m, w, spec, dets_np) for spec in my_events]
@@ -229,10 +230,7 @@ def run_gpu(args, rank, world):
     clocks = clk.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
     like_ms = [a.elapsed_time(b) for a, b in like_events]
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda")
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(elapsed, device="cuda")
     evals = args.steps * n * world
     value = evals / elapsed
 

@@ -359,6 +359,14 @@ mbis_status mbis_inject(const mbis_freq_grid* grid, int32_t n_det, const mbis_de
 mbis_status mbis_fisher(mbis_ctx* ctx, const double* theta, int32_t P, const int32_t* ids, const double* steps,
                         double* gamma_out);
 
+/* Self-test of the bounded device-side wait that every kernel uses on its mbarriers (not
+ * in the paper): one thread waits on a barrier that nothing completes, gives up after
+ * limit_ns (0 < limit_ns <= 2e9) of GPU wall time and reports *status_out = MBIS_E_TIMEOUT
+ * (host), *waited_ns_out (host, nullable) the time it waited.  The context stays usable --
+ * this is how a stuck copy or MMA surfaces in the other kernels (as MBIS_E_TIMEOUT from the
+ * next mbis_reduce) instead of a hang.  Returns MBIS_E_INVALID or MBIS_E_CUDA on failure. */
+mbis_status mbis_debug_wait_timeout(uint64_t limit_ns, int32_t* status_out, uint64_t* waited_ns_out);
+
 /* Library build/version string. */
 const char* mbis_version(void);
 

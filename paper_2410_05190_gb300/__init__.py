@@ -129,6 +129,7 @@ def _load():
         "mbis_server_wait": [p, u64, d, p],
         "mbis_server_poll": [p, p, i32, p],
         "mbis_server_stats_get": [p, p],
+        "mbis_debug_wait_timeout": [u64, p, p],
     }
     lib.mbis_server_destroy.restype = None
     lib.mbis_server_destroy.argtypes = [p]
@@ -370,6 +371,13 @@ def mbis_server_stats_get(server):
 
 def mbis_server_destroy(server):
     _lib.mbis_server_destroy(server)
+
+
+def mbis_debug_wait_timeout(limit_ns):
+    """Returns (status, waited_ns) of a device wait on a barrier that never completes."""
+    st, ns = C.c_int32(), C.c_uint64()
+    _check(_lib.mbis_debug_wait_timeout(int(limit_ns), C.byref(st), C.byref(ns)))
+    return st.value, ns.value
 
 
 NOALLOC_MAX_SAMPLES = 16777216
