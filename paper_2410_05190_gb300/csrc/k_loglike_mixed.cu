@@ -200,9 +200,10 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   {
     PhaseCoeffs pc;
     if (valid) {
-      pc = phase_coeffs(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic]);
-      kcut = live_bins(par[kMc], par[kQ], a.f_lo, a.df, a.n_bins);
-      A = amplitude(par[kMc], par[kDl]);
+      const MassSetup ms = mass_setup(par[kMc], par[kQ], par[kDl]);
+      pc = phase_coeffs_a(par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], ms.a, ms.la, ms.a13);
+      kcut = live_bins_m(ms.m_sec, a.f_lo, a.df, a.n_bins);
+      A = ms.amp;
     } else {
 #pragma unroll
       for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
@@ -292,7 +293,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
         float2 w = make_float2(st.w, st.w + 1.0f);
         const int32_t npair = (my_end - k) >> 1;
         const float4* cp = cb + ((k - kb) >> 1);
-#pragma unroll 2
+#pragma unroll 1
         for (int32_t p = 0; p < npair; ++p) {
           float2 R = __ffma2_rn(c5, w, c4);
           R = __ffma2_rn(R, w, c3);

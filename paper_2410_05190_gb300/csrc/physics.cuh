@@ -178,6 +178,38 @@ MBIS_HD void antenna(const double* x, const double* y, double ra, double dec, do
   *fc = xX * xY - yX * yY;
 }
 
+// Mass-dependent set-up with few FP64 operations (the GB300 runs FP64 at ~1/64 of FP32):
+// a power or root is seeded in FP32 and refined by one FP64 Newton step, which squares the
+// seed's ~1e-7 relative error; only ln(pi M) is an FP64 library call.
+//   M = Mc T_sun u^(3/5), u = (1 + q)^2 / q:  y = u^(3/5) solves y^5 = u^3
+//   a = pi M, a^(1/3) solves y^3 = a
+//   A = K (Mc T_sun)^(5/6) / d_L:  y = x^(5/6) solves y^6 = x^5
+// (log L of a poor sample can reach 10^4 in magnitude, so A and H keep ~1e-15 accuracy).
+struct MassSetup {
+  double m_sec, a, la, a13, amp;
+};
+
+MBIS_HD MassSetup mass_setup(double mc, double q, double dl_mpc) {
+  MassSetup o;
+  const double u = (1.0 + q) * (1.0 + q) / q, u3 = u * u * u;
+  double y = (double)powf((float)u, 0.6f);
+  const double y4 = (y * y) * (y * y);
+  y = 0.8 * y + u3 / (5.0 * y4);
+  o.m_sec = mc * kTsun * y;
+  o.a = kPi * o.m_sec;
+  o.la = log(o.a);
+  double c = (double)cbrtf((float)o.a);
+  c = (2.0 * c + o.a / (c * c)) * (1.0 / 3.0);
+  o.a13 = c;
+  // (Mc T_sun)^(5/6) solves y^6 = x^5
+  const double x = mc * kTsun, x5 = (x * x) * (x * x) * x;
+  double z = (double)powf((float)x, 5.0f / 6.0f);
+  const double z5 = (z * z) * (z * z) * z;
+  z = (5.0 / 6.0) * z + x5 / (6.0 * z5);
+  o.amp = 0.45643546458763845 * 0.46619407703541166 * z / (dl_mpc * kMpcSeconds);
+  return o;
+}
+
 // The same two quantities from the sines and cosines of (ra - gmst), dec and psi, so that a
 // network evaluates them once per sample.
 MBIS_HD void antenna_trig(const double* x, const double* y, double sp, double cp, double sd, double cd, double ss,
