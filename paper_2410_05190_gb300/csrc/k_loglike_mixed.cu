@@ -22,6 +22,7 @@
 #include "ffloat.cuh"
 #include "internal.h"
 #include "marg.cuh"
+#include "tc.cuh"
 
 namespace mbis {
 namespace {
@@ -33,53 +34,6 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 // constant puts the angle 2 pi f1 - 3 pi + ... in [-pi, pi), where the MUFU sine and cosine
 // carry no mean phase error (over [0, 2 pi) they lag by ~1.7e-7 rad on average).
 constexpr uint32_t kTurnOffset = 0x80000000u + 256u;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for a phase of the barrier; give up after ~2 s of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > 2000000000ull) return false;
-  }
-}
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
@@ -235,9 +189,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   if (tid == 0) {
     s_kmax = 0;
     if (!first)
-      for (int b = 0; b < kNbuf; ++b) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar[b])) : "memory");
-    for (int b = 0; b < kNbuf; ++b) mbar_init(&bar[b], 1);
-    mbar_fence_init();
+      for (int b = 0; b < kNbuf; ++b) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(&bar[b])) : "memory");
+    for (int b = 0; b < kNbuf; ++b) tc::mbar_init(&bar[b], 1);
+    tc::mbar_fence_init();
   }
   __syncthreads();
   atomicMax(&s_kmax, kcut);
@@ -248,8 +202,8 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   int issued[kNbuf] = {};  // copies issued per buffer (thread 0)
   if (tid == 0) {
     for (int b = 0; b < kNbuf && b < nch; ++b) {
-      mbar_expect_tx(&bar[b], kBytes);
-      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)b * (kChunk / 2), kBytes, &bar[b]);
+      tc::mbar_expect_tx(&bar[b], kBytes);
+      tc::bulk_g2s(sC[b], a.cfold32 + (int64_t)b * (kChunk / 2), kBytes, &bar[b]);
       ++issued[b];
     }
   }
@@ -262,7 +216,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   bool timed_out = false;
   for (int32_t ch = 0; ch < nch; ++ch) {
     const int b = ch % kNbuf;
-    const bool got = mbar_wait_bounded(&bar[b], (uint32_t)((ch / kNbuf) & 1));
+    const bool got = tc::mbar_wait(&bar[b], (uint32_t)((ch / kNbuf) & 1));
     if (__syncthreads_or(!got)) {
       timed_out = true;
       break;
@@ -338,8 +292,8 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
     __syncthreads();  // every thread is done with buffer b
     if (tid == 0 && ch + kNbuf < nch) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bar[b], kBytes);
-      bulk_copy_g2s(sC[b], a.cfold32 + (int64_t)(ch + kNbuf) * (kChunk / 2), kBytes, &bar[b]);
+      tc::mbar_expect_tx(&bar[b], kBytes);
+      tc::bulk_g2s(sC[b], a.cfold32 + (int64_t)(ch + kNbuf) * (kChunk / 2), kBytes, &bar[b]);
       ++issued[b];
     }
   }
@@ -349,7 +303,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
       // let the last copy issued into each buffer land (bounded) before the CTA's shared
       // memory is released
       for (int bb = 0; bb < kNbuf; ++bb)
-        if (issued[bb] > 0) (void)mbar_wait_bounded(&bar[bb], (uint32_t)((issued[bb] - 1) & 1));
+        if (issued[bb] > 0) (void)tc::mbar_wait(&bar[bb], (uint32_t)((issued[bb] - 1) & 1));
     }
     if (active) a.out[s] = NAN;
     return;
