@@ -100,6 +100,15 @@ def lib():
             "or_draw": (None, [u64, u64, i64, i32, p, p, p, d, p, p]),
             "or_reduce": (None, [i64, p, p, p, p, p]),
             "or_weighted_moments": (None, [i64, i32, p, p, p, p, p, p]),
+            "or_tiling_physical": (None, [p, d, d, p, p]),
+            "or_tiling_waveform": (i32, [p, d, d, p]),
+            "or_tiling_overlap": (d, [i32, p, p]),
+            "or_tiling_match": (d, [p, d, d, d, d]),
+            "or_tiling_bank": (i32, [p, i64, p, d, i64, i32, p, p, p]),
+            "or_tiling_assign": (None, [p, i64, p, i32, p, p, p, p]),
+            "or_tiling_lists": (None, [i64, p, i32, p, p, p]),
+            "or_tiling_mixture": (d, [i32, p, p, p]),
+            "or_tiling_draw": (None, [u64, u64, i64, i32, p, d, p, p, p, p, i64, p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -346,3 +355,87 @@ def full_params(ids, theta_cols, fixed):
     for p, i in enumerate(ids):
         out[:, i] = theta_cols[p]
     return out
+
+
+# ------------------------------------------------------------------------------------------
+# Tiled proposal (Sec. II; App. A)
+class _TilingStruct(C.Structure):
+    _fields_ = [("x_lo", C.c_double), ("x_hi", C.c_double), ("mc_period", C.c_double), ("mc_base", C.c_double),
+                ("q_lo", C.c_double), ("q_hi", C.c_double), ("chi1", C.c_double), ("chi2", C.c_double),
+                ("f_lo", C.c_double), ("df", C.c_double), ("n_bins", C.c_int32), ("psd", C.c_void_p)]
+
+
+class Tiling:
+    """The sampled space of the tiled proposal and the noise weighting of its match."""
+
+    def __init__(self, f_lo, df, n_bins, psd, x_lo, x_hi, mc_period, mc_base, q_lo, q_hi, chi1=0.0, chi2=0.0):
+        self.psd = _f64(psd).reshape(-1)
+        assert len(self.psd) == n_bins
+        self.s = _TilingStruct(x_lo, x_hi, mc_period, mc_base, q_lo, q_hi, chi1, chi2, f_lo, df, n_bins,
+                               self.psd.ctypes.data)
+
+    @property
+    def n_bins(self):
+        return self.s.n_bins
+
+    def physical(self, x, q):
+        mc, qp = C.c_double(), C.c_double()
+        lib().or_tiling_physical(C.byref(self.s), float(x), float(q), C.byref(mc), C.byref(qp))
+        return mc.value, qp.value
+
+    def waveform(self, x, q):
+        u = np.zeros(self.n_bins, dtype=np.complex128)
+        live = lib().or_tiling_waveform(C.byref(self.s), float(x), float(q), _ptr(u))
+        return u, live
+
+    def match(self, xa, qa, xb, qb):
+        return lib().or_tiling_match(C.byref(self.s), float(xa), float(qa), float(xb), float(qb))
+
+    def bank(self, cand, min_match, stop_after, max_templates):
+        """Stochastic placement over the candidates [2][n]; returns (indices, n_used, margin)."""
+        cand = np.ascontiguousarray(_f64(cand).reshape(2, -1))
+        n = cand.shape[1]
+        idx = np.zeros(max_templates, dtype=np.int32)
+        used, margin = C.c_int64(), C.c_double()
+        T = lib().or_tiling_bank(C.byref(self.s), n, _ptr(cand), min_match, stop_after, max_templates, _ptr(idx),
+                                 C.byref(used), C.byref(margin))
+        return idx[:T].copy(), used.value, margin.value
+
+    def assign(self, pts, templates):
+        """Best template of each point [2][n] among templates [2][T]: (tile, match, runner-up)."""
+        pts = np.ascontiguousarray(_f64(pts).reshape(2, -1))
+        tpl = np.ascontiguousarray(_f64(templates).reshape(2, -1))
+        n, T = pts.shape[1], tpl.shape[1]
+        tile = np.zeros(n, dtype=np.int32)
+        match, second = np.zeros(n), np.zeros(n)
+        lib().or_tiling_assign(C.byref(self.s), n, _ptr(pts), T, _ptr(tpl), _ptr(tile), _ptr(match), _ptr(second))
+        return tile, match, second
+
+
+def tiling_lists(tile, T):
+    tile = np.ascontiguousarray(tile, dtype=np.int32)
+    n = len(tile)
+    count, offset = np.zeros(T, dtype=np.int64), np.zeros(T, dtype=np.int64)
+    members = np.zeros(max(n, 1), dtype=np.int64)
+    lib().or_tiling_lists(n, _ptr(tile), T, _ptr(count), _ptr(offset), _ptr(members))
+    return count, offset, members[:int(count.sum())]
+
+
+def tiling_mixture(count, loglike_tpl):
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    ll = _f64(loglike_tpl)
+    c = np.zeros(len(count))
+    m = lib().or_tiling_mixture(len(count), _ptr(count), _ptr(ll), _ptr(c))
+    return c, m
+
+
+def tiling_draw(seed, ctr0, n, c, m, loglike_tpl, count, offset, members, n_pool):
+    """Draws of the tiled mixture: (pool index, tile, ln g - ln pi) per draw."""
+    c, ll = _f64(c), _f64(loglike_tpl)
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    offset = np.ascontiguousarray(offset, dtype=np.int64)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    idx, tile, lr = np.zeros(n, dtype=np.int64), np.zeros(n, dtype=np.int32), np.zeros(n)
+    lib().or_tiling_draw(seed, ctr0, n, len(c), _ptr(c), m, _ptr(ll), _ptr(count), _ptr(offset), _ptr(members),
+                         n_pool, _ptr(idx), _ptr(tile), _ptr(lr))
+    return idx, tile, lr

@@ -32,6 +32,12 @@
  *   weights / ESS / log Z ...... equal weights, single weight, Gaussian target with
  *                                proposal == target (ESS = N, closed-form evidence)
  *   Fisher matrix .............. closed forms for ln d_L, phi_c and their cross term
+ *   tiling match ............... the normalised overlap of the likelihood's inner product
+ *                                of detector strains; the phase-projected Fisher metric
+ *   bank / tiles ............... packing and covering invariants; brute-force argmax;
+ *                                images of one binary share a tile
+ *   mixture / draws ............ E_g[w] = mean prior likelihood exactly; equal weights
+ *                                (ESS = n) when L is constant per tile; frequencies
  * Parity unpinned: the physical values of the 2.5PN, 3PN and 3.5PN aligned-spin
  * coefficients (only their test-mass limit and label symmetry are pinned).
  */
@@ -691,4 +697,235 @@ void or_reduce(int64_t n, const double* loglike, const double* logp, const doubl
   out[3] = (double)n;
   out[4] = (double)s1;
   out[5] = (double)s2;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Tiled proposal (Sec. II; App. A): a template bank spans the space of waveforms, every
+ * prior sample belongs to the tile of the template it matches best, and the proposal
+ * draws a tile with probability proportional to its share of the prior volume times the
+ * likelihood at its template, then a prior sample of that tile.
+ *
+ * The space is the two-parameter demonstration of App. A: a sampled chirp-mass coordinate
+ * x, mapped to the chirp mass mc_base + mod(x, mc_period) (the "cyclic chirp mass"; a
+ * period <= 0 keeps Mc = x), and a sampled mass ratio q that may fall below one, q and 1/q
+ * naming the same binary; spins are fixed.  Readings where the paper is silent: the match
+ * is the normalised overlap maximised over phase at a common coalescence time (the 2-D
+ * likelihood it tiles samples neither time nor phase); the noise weighting is one PSD; a
+ * waveform is zero at and above its ISCO as in the likelihood. */
+typedef struct {
+  double x_lo, x_hi;
+  double mc_period, mc_base;
+  double q_lo, q_hi;
+  double chi1, chi2;
+  double f_lo, df;
+  int32_t n_bins;
+  const double* psd; /* [n_bins] */
+} or_tiling;
+
+/* Physical chirp mass and mass ratio (>= 1) of a point of the sampled space. */
+void or_tiling_physical(const or_tiling* t, double x, double q, double* mc, double* qp) {
+  if (t->mc_period > 0.0) {
+    double r = fmod(x, t->mc_period);
+    if (r < 0.0) r += t->mc_period;
+    *mc = t->mc_base + r;
+  } else {
+    *mc = x;
+  }
+  *qp = (q >= 1.0) ? q : 1.0 / q;
+}
+
+/* Whitened, unit-norm waveform of one point: u_k = f_k^(-7/6) e^(-i Psi(f_k)) / sqrt(S_k),
+ * divided by sqrt(sum_k |.|^2), zero at and above the ISCO.  Returns the number of live
+ * bins (0: no bin below the ISCO, u is all zero). */
+int32_t or_tiling_waveform(const or_tiling* t, double x, double q, double complex* u) {
+  double par[OR_NPAR];
+  memset(par, 0, sizeof par);
+  or_tiling_physical(t, x, q, &par[OR_MC], &par[OR_Q]);
+  par[OR_CHI1] = t->chi1;
+  par[OR_CHI2] = t->chi2;
+  par[OR_DL] = 1.0;
+  double fi = or_f_isco(par[OR_MC], par[OR_Q]), norm2 = 0.0;
+  int32_t live = 0;
+  for (int32_t k = 0; k < t->n_bins; ++k) {
+    double f = or_freq(t->f_lo, t->df, k);
+    if (f >= fi) {
+      u[k] = 0.0;
+      continue;
+    }
+    double a = pow(f, -7.0 / 6.0) / sqrt(t->psd[k]);
+    u[k] = a * cexp(-I * or_taylorf2_phase(f, par));
+    norm2 += a * a;
+    ++live;
+  }
+  if (live == 0) return 0;
+  double inv = 1.0 / sqrt(norm2);
+  for (int32_t k = 0; k < t->n_bins; ++k) u[k] *= inv;
+  return live;
+}
+
+/* |sum_k conj(u_a,k) u_b,k| of two unit-norm waveforms: the overlap (a|b) / sqrt((a|a)(b|b))
+ * of Eq. 1's inner product maximised over a constant phase (the maximum over phi of
+ * Re(e^(i phi) z) is |z|). */
+double or_tiling_overlap(int32_t n_bins, const double complex* ua, const double complex* ub) {
+  double complex z = 0.0;
+  for (int32_t k = 0; k < n_bins; ++k) z += conj(ua[k]) * ub[k];
+  return cabs(z);
+}
+
+double or_tiling_match(const or_tiling* t, double xa, double qa, double xb, double qb) {
+  double complex* ua = (double complex*)malloc(sizeof(double complex) * (size_t)t->n_bins);
+  double complex* ub = (double complex*)malloc(sizeof(double complex) * (size_t)t->n_bins);
+  double m = 0.0;
+  if (or_tiling_waveform(t, xa, qa, ua) > 0 && or_tiling_waveform(t, xb, qb, ub) > 0)
+    m = or_tiling_overlap(t->n_bins, ua, ub);
+  free(ua);
+  free(ub);
+  return m;
+}
+
+/* Stochastic template placement (App. A "Template bank generation"; the stochastic
+ * method the paper adopts): candidates are visited in the given order; one joins the bank
+ * when its match with every template already in the bank is below min_match.  Placement
+ * stops after stop_after consecutive rejections, at max_templates, or when the candidates
+ * run out.  Candidates without a live bin are skipped (counted as rejections).
+ * cand is [2][n_cand] (x row, q row).  Writes the indices of the accepted candidates to
+ * idx_out, the number of candidates visited to *n_used and, when margin is non-null, the
+ * smallest |match - min_match| of any decision taken.  Returns the bank size. */
+int32_t or_tiling_bank(const or_tiling* t, int64_t n_cand, const double* cand, double min_match, int64_t stop_after,
+                       int32_t max_templates, int32_t* idx_out, int64_t* n_used, double* margin) {
+  const size_t nb = (size_t)t->n_bins;
+  double complex* bank =
+      (double complex*)malloc(sizeof(double complex) * nb * (size_t)(max_templates > 0 ? max_templates : 1));
+  double complex* u = (double complex*)malloc(sizeof(double complex) * nb);
+  int32_t T = 0;
+  int64_t run = 0, i = 0;
+  double mg = INFINITY;
+  for (; i < n_cand && T < max_templates && run < stop_after; ++i) {
+    if (or_tiling_waveform(t, cand[i], cand[n_cand + i], u) == 0) {
+      ++run;
+      continue;
+    }
+    double best = 0.0;
+    for (int32_t j = 0; j < T; ++j) {
+      double m = or_tiling_overlap(t->n_bins, bank + (size_t)j * nb, u);
+      if (m > best) best = m;
+    }
+    if (T > 0 && fabs(best - min_match) < mg) mg = fabs(best - min_match);
+    if (T == 0 || best < min_match) {
+      memcpy(bank + (size_t)T * nb, u, sizeof(double complex) * nb);
+      idx_out[T++] = (int32_t)i;
+      run = 0;
+    } else {
+      ++run;
+    }
+  }
+  *n_used = i;
+  if (margin) *margin = mg;
+  free(bank);
+  free(u);
+  return T;
+}
+
+/* Tile of each point (App. A "Tiling the prior volume"): the template of highest match,
+ * the lowest index among equal matches; -1 for a point without a live bin.  pts is [2][n],
+ * tpl is [2][T].  match_out gets the best match, second_out (nullable) the runner-up. */
+void or_tiling_assign(const or_tiling* t, int64_t n, const double* pts, int32_t T, const double* tpl,
+                      int32_t* tile_out, double* match_out, double* second_out) {
+  const size_t nb = (size_t)t->n_bins;
+  double complex* tw = (double complex*)malloc(sizeof(double complex) * nb * (size_t)(T > 0 ? T : 1));
+  int32_t* tlive = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T > 0 ? T : 1));
+  for (int32_t j = 0; j < T; ++j) tlive[j] = or_tiling_waveform(t, tpl[j], tpl[T + j], tw + (size_t)j * nb);
+#pragma omp parallel
+  {
+    double complex* u = (double complex*)malloc(sizeof(double complex) * nb);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t best_j = -1;
+      double best = -1.0, second = -1.0;
+      if (or_tiling_waveform(t, pts[i], pts[n + i], u) > 0) {
+        for (int32_t j = 0; j < T; ++j) {
+          double m = tlive[j] > 0 ? or_tiling_overlap(t->n_bins, tw + (size_t)j * nb, u) : 0.0;
+          if (m > best) {
+            second = best;
+            best = m;
+            best_j = j;
+          } else if (m > second) {
+            second = m;
+          }
+        }
+      }
+      tile_out[i] = best_j;
+      match_out[i] = best_j >= 0 ? best : 0.0;
+      if (second_out) second_out[i] = second > 0.0 ? second : 0.0;
+    }
+    free(u);
+  }
+  free(tw);
+  free(tlive);
+}
+
+/* Tiles as lists: count of each tile, exclusive offsets and the members of every tile in
+ * increasing sample order.  tile has n entries in [-1, T); -1 belongs to no tile. */
+void or_tiling_lists(int64_t n, const int32_t* tile, int32_t T, int64_t* count, int64_t* offset, int64_t* members) {
+  for (int32_t j = 0; j < T; ++j) count[j] = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (tile[i] >= 0) ++count[tile[i]];
+  int64_t o = 0;
+  for (int32_t j = 0; j < T; ++j) {
+    offset[j] = o;
+    o += count[j];
+  }
+  int64_t* fill = (int64_t*)calloc((size_t)(T > 0 ? T : 1), sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i)
+    if (tile[i] >= 0) members[offset[tile[i]] + fill[tile[i]]++] = i;
+  free(fill);
+}
+
+/* Mixture over tiles (Sec. II; App. A "Generation of the posterior distribution"): tile j
+ * is drawn with probability p_j proportional to (n_j / N) L_j, its share of the prior
+ * volume (n_j of the N prior samples) times the likelihood ratio at its template.  Kept
+ * unnormalised and shifted: c_j = sum_{i <= j} n_i exp(lnL_i - m), m = max over tiles with
+ * n_i > 0 of lnL_i.  Returns m; c has T entries (the last one is the total). */
+double or_tiling_mixture(int32_t T, const int64_t* count, const double* loglike_tpl, double* c) {
+  double m = -INFINITY;
+  for (int32_t j = 0; j < T; ++j)
+    if (count[j] > 0 && loglike_tpl[j] > m) m = loglike_tpl[j];
+  double s = 0.0;
+  for (int32_t j = 0; j < T; ++j) {
+    if (count[j] > 0) s += (double)count[j] * exp(loglike_tpl[j] - m);
+    c[j] = s;
+  }
+  return m;
+}
+
+/* Draws from the mixture.  Draw i takes the Philox4x32-10 block of counter
+ * (lo g, hi g, 3, 0), g = ctr0 + i, under the key (seed lo, seed hi).  Words (r0, r1) give
+ * u = ((r0 2^32 + r1) >> 11) 2^-53 in [0, 1), and the tile is the first j with
+ * c_j > u c_(T-1).  Words (r2, r3) give a 64-bit integer r, and the member is the
+ * ((r n_j) >> 64)-th of the tile's list (multiply-shift: uniform up to n_j / 2^64).  For
+ * the drawn prior sample,
+ *   ln g = ln pi + ln p_j - ln(n_j / N) = ln pi + lnL_j - m - ln c_(T-1) + ln N,
+ * the proposal density being the prior density scaled by p_j / (n_j / N) inside tile j.
+ * Writes the pool index and tile of every draw and ln g - ln pi. */
+void or_tiling_draw(uint64_t seed, uint64_t ctr0, int64_t n, int32_t T, const double* c, double m,
+                    const double* loglike_tpl, const int64_t* count, const int64_t* offset, const int64_t* members,
+                    int64_t n_pool, int64_t* pool_idx, int32_t* tile_out, double* log_ratio) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const double total = c[T - 1];
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t g = ctr0 + (uint64_t)i;
+    const uint32_t ctr[4] = {(uint32_t)g, (uint32_t)(g >> 32), 3u, 0u};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    const uint64_t w0 = ((uint64_t)r[0] << 32) | r[1];
+    const double u = (double)(w0 >> 11) * (1.0 / 9007199254740992.0);
+    const double target = u * total;
+    int32_t j = 0;
+    while (j < T - 1 && !(c[j] > target)) ++j;
+    const uint64_t w1 = ((uint64_t)r[2] << 32) | r[3];
+    const uint64_t k = (uint64_t)(((unsigned __int128)w1 * (unsigned __int128)(uint64_t)count[j]) >> 64);
+    pool_idx[i] = members[offset[j] + (int64_t)k];
+    tile_out[i] = j;
+    log_ratio[i] = loglike_tpl[j] - m - log(total) + log((double)n_pool);
+  }
 }

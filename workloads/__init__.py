@@ -208,6 +208,56 @@ def uneven_batch(n_events=64, seed=POPULATION_SEED + 4):
     return out
 
 
+@dataclass
+class TiledDemo:
+    """The two-parameter demonstration of the tiled proposal (App. A): one BBH event whose
+    sampled coordinates are a cyclic chirp mass x (chirp mass mc_base + mod(x, mc_period),
+    over two periods) and a mass ratio q over [1/q_max, q_max] (q and 1/q are the same
+    binary), so the posterior has four modes.  Prior uniform in (x, q)."""
+    workload: Workload       # the event: sampled slots (Mc, q) of the physical space
+    x_lo: float
+    x_hi: float
+    mc_period: float
+    mc_base: float
+    q_lo: float
+    q_hi: float
+    min_match: float
+    stop_after: int
+    max_templates: int
+    n_candidates: int
+    candidate_seed: int
+    n_pool: int
+    pool_seed: int
+    draw_seed: int
+
+
+def tiled_demo(n_pool=1 << 22, snr=15.0, seed=POPULATION_SEED + 5):
+    """Source at Mc = 25, q = 3.5 (m1 = 55.75, m2 = 15.93 Msun), zero spins, fixed sky and
+    orientation, H1+L1, 20-512 Hz at 1/4 Hz (1969 bins), coloured Gaussian noise at network
+    SNR 15, phase marginalised; x in [20, 28) with Mc = 24 + mod(x, 4), q in [1/6, 6]; bank
+    at minimal match 0.996, stopping after 2000 consecutive rejections; a prior pool of
+    2^22 points."""
+    mc, q = 25.0, 3.5
+    m1 = mc * (1.0 + q) ** 0.2 * q ** 0.4
+    m2 = m1 / q
+    spec = EventSpec(m1, m2, dict(chi1=0.0, chi2=0.0, ra=1.0, dec=0.5, psi=0.3, iota=0.4, tc=0.0, phic=0.0),
+                     gmst=0.0, snr=snr, noise_seed=(seed << 8) + 1, draw_seed=(seed << 8) + 2)
+    w = Workload("tiled_demo", ["H1", "L1"], 20.0, 512.0, 0.25, [MC, Q], MARG_PHASE, 1 << 16, "mixed", "c64",
+                 1.0, 0, 0.0, [spec])
+    return TiledDemo(w, 20.0, 28.0, 4.0, 24.0, 1.0 / 6.0, 6.0, 0.996, 2000, 4096, 1 << 17, (seed << 8) + 3,
+                     n_pool, (seed << 8) + 4, (seed << 8) + 5)
+
+
+def uniform_points(n, x_lo, x_hi, q_lo, q_hi, seed):
+    """n points uniform in the box [x_lo, x_hi) x [q_lo, q_hi] as a [2][n] array (x row, q
+    row): candidates of the template placement and the prior pool of the tiles."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((2, n))
+    out[0] = rng.uniform(x_lo, x_hi, n)
+    out[1] = rng.uniform(q_lo, q_hi, n)
+    return out
+
+
 def scaled(w: Workload, n_events=None, n_samples=None, f_hi=None):
     """A copy of a workload with fewer events, fewer samples or a shorter band (for the
     oracle-sized parity cases)."""
