@@ -326,6 +326,104 @@ mbis_status mbis_server_stats_get(mbis_server* s, mbis_server_stats* out);
  * are released; then the worker stops and every resource is freed. */
 void mbis_server_destroy(mbis_server* s);
 
+/* ---- tiled proposal: template bank, prior-volume tiles, mixture draws --------------- */
+
+typedef struct mbis_tiling mbis_tiling;
+
+/* The sampled space of the tiled proposal (App. A): a chirp-mass coordinate x in
+ * [x_lo, x_hi), mapped to the chirp mass mc_base + mod(x, mc_period) (the "cyclic chirp
+ * mass"; mc_period <= 0 maps x to itself), and a mass ratio q in [q_lo, q_hi] that may
+ * extend below 1 (q and 1/q name the same binary); aligned spins fixed at chi1, chi2.  The
+ * prior of the space is uniform in (x, q). */
+typedef struct {
+  double x_lo, x_hi;
+  double mc_period, mc_base;
+  double q_lo, q_hi;
+  double chi1, chi2;
+} mbis_tiling_space;
+
+/* Sec. II, App. A: the paper tiles the space of waveforms with a template bank and maps
+ * every prior sample to the tile of its best-matching template; the match is the overlap
+ * of Eq. 1's inner product between unit-norm waveforms, maximised over phase at a common
+ * coalescence time (the TaylorF2 waveform of the likelihood, zero at and above the ISCO),
+ * weighted by one PSD.  grid: the frequency grid; psd (host, n_bins doubles > 0 on the
+ * bins the space reaches).  Every point of the space must have a live bin (an ISCO above
+ * f_lo).  Copies what it needs to the device; the caller keeps ownership of its arrays.
+ * Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_tiling_create(const mbis_freq_grid* grid, const double* psd, const mbis_tiling_space* space,
+                               mbis_tiling** out);
+
+/* Stochastic template placement (App. A, "Template bank generation"): the candidates
+ * (host, [2][n_cand]: x row then q row, inside the space) are visited in order, and one
+ * joins the bank when its match with every template already in the bank is below
+ * min_match (0 < min_match < 1).  Placement stops after stop_after consecutive
+ * rejections, at max_templates (1..16384) or at the end of the candidates.  Matches are
+ * FP64 on the device; the accept decisions are taken on the host in candidate order.
+ * Replaces any earlier bank (and drops the pool and mixture).  n_templates, n_used (host,
+ * nullable): the bank size and the candidates visited.
+ * Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_tiling_bank(mbis_tiling* t, int64_t n_cand, const double* cand, double min_match,
+                             int64_t stop_after, int32_t max_templates, int32_t* n_templates, int64_t* n_used);
+
+/* The bank: *n_templates (host); coords (host, nullable, [2][T]) the templates' (x, q);
+ * physical (host, nullable, [2][T]) their chirp mass and mass ratio >= 1; cand_index
+ * (host, nullable, [T]) their positions in the candidate list.  MBIS_E_STATE without a
+ * bank. */
+mbis_status mbis_tiling_templates(const mbis_tiling* t, int32_t* n_templates, double* coords, double* physical,
+                                  int32_t* cand_index);
+
+/* FP64 match of n point pairs (device, [2][n] each: x row then q row); out (device, n).
+ * The matches that drive template placement.  Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_tiling_match(mbis_tiling* t, int64_t n, const double* a, const double* b, double* out,
+                              void* cuda_stream);
+
+/* Tile of each point (App. A, "Tiling the prior volume"): the template of highest match,
+ * the lowest index among equal ones.  pts (device, [2][n]); tile (device, n int32; -1 for
+ * a point outside the space); match (device, n float, nullable) the best match.  The
+ * sample-by-template overlaps are one TF32 tensor-core contraction (tcgen05, FP32
+ * accumulation) over the live bins, the sample waveforms computed in registers and never
+ * stored; matches carry ~1e-5 absolute error, so points whose two best templates match
+ * within that may land in either tile.  Asynchronous: a device-side wait that timed out
+ * is reported by the next mbis_tiling_set_pool.  Needs a bank.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_tiling_assign(mbis_tiling* t, int64_t n, const double* pts, int32_t* tile, float* match,
+                               void* cuda_stream);
+
+/* The prior sample that defines the tiles' prior volumes: pts (device, [2][n], points drawn
+ * from the prior, 1 <= n < 2^31) is copied, assigned, and sorted into per-tile lists (in
+ * increasing sample order).  Drops an earlier mixture.  Synchronises the stream.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID (a point outside the space), MBIS_E_OOM,
+ * MBIS_E_CUDA, MBIS_E_TIMEOUT. */
+mbis_status mbis_tiling_set_pool(mbis_tiling* t, int64_t n, const double* pts, void* cuda_stream);
+
+/* Pool members of every tile: counts (host, [T] int64); tile_of (device, nullable, [n]
+ * int32) the pool's tile indices; members (device, nullable, [n] int32) the pool indices
+ * grouped by tile, each tile in increasing order, tiles in order. */
+mbis_status mbis_tiling_pool(const mbis_tiling* t, int64_t* counts, int32_t* tile_of, int32_t* members,
+                             void* cuda_stream);
+
+/* The mixture (Sec. II; App. A, "Generation of the posterior distribution"): tile j is
+ * drawn with probability p_j proportional to n_j L_j, n_j its pool members (its share of
+ * the prior volume) and ln L_j = loglike_tpl[j] (device, [T]) the log-likelihood ratio at
+ * its template, e.g. from mbis_loglike on the templates' physical coordinates.
+ * Synchronises the stream.  Errors: MBIS_E_STATE (no pool), MBIS_E_INVALID (no tile with
+ * members has a finite log-likelihood), MBIS_E_CUDA. */
+mbis_status mbis_tiling_set_loglike(mbis_tiling* t, const double* loglike_tpl, void* cuda_stream);
+
+/* n draws of the mixture: draw i uses the Philox4x32-10 block of counter
+ * (lo32(ctr0 + i), hi32(ctr0 + i), 3, 0) and key (lo32(seed), hi32(seed)); words 0-1 pick
+ * the tile by its cumulative weight, words 2-3 one of its members by multiply-shift.
+ * coords (device, nullable, [2][n]): the drawn (x, q); theta (device, [2][n]): their chirp
+ * mass and mass ratio >= 1, the rows of a likelihood context sampling (Mc, q); log_q
+ * (device, n): ln g = ln pi + ln p_j - ln(n_j / N); log_prior (device, n): ln pi, uniform
+ * in (x, q); pool_index (device, nullable, n int32).  Errors: MBIS_E_STATE (no mixture),
+ * MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_tiling_draw(mbis_tiling* t, uint64_t seed, uint64_t ctr0, int64_t n, double* coords, double* theta,
+                             double* log_q, double* log_prior, int32_t* pool_index, void* cuda_stream);
+
+void mbis_tiling_destroy(mbis_tiling* t);
+const char* mbis_tiling_last_error(const mbis_tiling* t);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

@@ -130,7 +130,20 @@ def _load():
         "mbis_server_poll": [p, p, i32, p],
         "mbis_server_stats_get": [p, p],
         "mbis_debug_wait_timeout": [u64, p, p],
+        "mbis_tiling_create": [p, p, p, p],
+        "mbis_tiling_bank": [p, i64, p, d, i64, i32, p, p],
+        "mbis_tiling_templates": [p, p, p, p, p],
+        "mbis_tiling_match": [p, i64, p, p, p, p],
+        "mbis_tiling_assign": [p, i64, p, p, p, p],
+        "mbis_tiling_set_pool": [p, i64, p, p],
+        "mbis_tiling_pool": [p, p, p, p, p],
+        "mbis_tiling_set_loglike": [p, p, p],
+        "mbis_tiling_draw": [p, u64, u64, i64, p, p, p, p, p, p],
     }
+    lib.mbis_tiling_destroy.restype = None
+    lib.mbis_tiling_destroy.argtypes = [p]
+    lib.mbis_tiling_last_error.restype = C.c_char_p
+    lib.mbis_tiling_last_error.argtypes = [p]
     lib.mbis_server_destroy.restype = None
     lib.mbis_server_destroy.argtypes = [p]
     lib.mbis_batch_destroy.restype = None
@@ -450,3 +463,76 @@ def mbis_fisher(ctx, theta, ids, steps):
     g = np.zeros((P, P))
     _check(_lib.mbis_fisher(ctx, pth, P, pid, pst, g.ctypes.data), ctx)
     return g
+
+
+# ------------------------------------------------------------------------------- tiled proposal
+class TilingSpace(C.Structure):
+    _fields_ = [("x_lo", C.c_double), ("x_hi", C.c_double), ("mc_period", C.c_double), ("mc_base", C.c_double),
+                ("q_lo", C.c_double), ("q_hi", C.c_double), ("chi1", C.c_double), ("chi2", C.c_double)]
+
+
+def _tcheck(status, t):
+    if status != MBIS_OK:
+        msg = _lib.mbis_tiling_last_error(t)
+        raise MbisError(status, msg.decode() if msg else "")
+
+
+def mbis_tiling_create(f_lo, df, n_bins, psd, x_lo, x_hi, mc_period, mc_base, q_lo, q_hi, chi1=0.0, chi2=0.0):
+    grid = FreqGrid(f_lo, df, n_bins)
+    psd_a, psd_p = _host(psd, np.float64)
+    sp = TilingSpace(x_lo, x_hi, mc_period, mc_base, q_lo, q_hi, chi1, chi2)
+    out = C.c_void_p()
+    _tcheck(_lib.mbis_tiling_create(C.byref(grid), psd_p, C.byref(sp), C.byref(out)), None)
+    return out.value
+
+
+def mbis_tiling_destroy(t):
+    _lib.mbis_tiling_destroy(t)
+
+
+def mbis_tiling_bank(t, cand, min_match, stop_after, max_templates):
+    """Stochastic placement over host candidates [2][n]; returns (n_templates, n_used)."""
+    cand = np.ascontiguousarray(np.asarray(cand, dtype=np.float64).reshape(2, -1))
+    nt, nu = C.c_int32(), C.c_int64()
+    _tcheck(_lib.mbis_tiling_bank(t, cand.shape[1], cand.ctypes.data, min_match, stop_after, max_templates,
+                                  C.byref(nt), C.byref(nu)), t)
+    return nt.value, nu.value
+
+
+def mbis_tiling_templates(t):
+    """(coords [2][T], physical [2][T], candidate index [T]) of the bank."""
+    nt = C.c_int32()
+    _tcheck(_lib.mbis_tiling_templates(t, C.byref(nt), None, None, None), t)
+    T = nt.value
+    coords, phys, idx = np.zeros((2, T)), np.zeros((2, T)), np.zeros(T, dtype=np.int32)
+    _tcheck(_lib.mbis_tiling_templates(t, C.byref(nt), coords.ctypes.data, phys.ctypes.data, idx.ctypes.data), t)
+    return coords, phys, idx
+
+
+def mbis_tiling_match(t, n, a, b, out, stream=None):
+    _tcheck(_lib.mbis_tiling_match(t, n, _dev(a), _dev(b), _dev(out), _stream(stream)), t)
+
+
+def mbis_tiling_assign(t, n, pts, tile, match=None, stream=None):
+    _tcheck(_lib.mbis_tiling_assign(t, n, _dev(pts), _dev(tile), _dev(match), _stream(stream)), t)
+
+
+def mbis_tiling_set_pool(t, n, pts, stream=None):
+    _tcheck(_lib.mbis_tiling_set_pool(t, n, _dev(pts), _stream(stream)), t)
+
+
+def mbis_tiling_pool(t, T, tile_of=None, members=None, stream=None):
+    """Pool counts per tile (host int64 [T]); optionally copies the tile indices and member
+    lists into device buffers."""
+    counts = np.zeros(T, dtype=np.int64)
+    _tcheck(_lib.mbis_tiling_pool(t, counts.ctypes.data, _dev(tile_of), _dev(members), _stream(stream)), t)
+    return counts
+
+
+def mbis_tiling_set_loglike(t, loglike_tpl, stream=None):
+    _tcheck(_lib.mbis_tiling_set_loglike(t, _dev(loglike_tpl), _stream(stream)), t)
+
+
+def mbis_tiling_draw(t, seed, ctr0, n, theta, log_q, log_prior, coords=None, pool_index=None, stream=None):
+    _tcheck(_lib.mbis_tiling_draw(t, seed, ctr0, n, _dev(coords), _dev(theta), _dev(log_q), _dev(log_prior),
+                                  _dev(pool_index), _stream(stream)), t)

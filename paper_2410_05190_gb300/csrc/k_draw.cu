@@ -1,34 +1,14 @@
 // k_draw.cu -- proposal draws (g of Eq. 5) and prior densities (pi of Eq. 5).
 //
-// One thread per sample.  Normals come from Philox4x32-10 (Salmon et al., SC'11): the
-// generator is written here from its published round function (two 32x32 multiplies per
-// round, Weyl key schedule, ten rounds).  Sample i of a call uses counter
-// (lo32(ctr0 + i), hi32(ctr0 + i), 2, block) and key (lo32(seed), hi32(seed)); each block
-// yields two Box-Muller pairs.  Because the counter names the sample, a sample's value
-// does not depend on batch boundaries, launch shape or scheduling.
+// One thread per sample.  Normals come from Philox4x32-10 (philox.cuh).  Sample i of a
+// call uses counter (lo32(ctr0 + i), hi32(ctr0 + i), 2, block) and key (lo32(seed),
+// hi32(seed)); each block yields two Box-Muller pairs.  Because the counter names the
+// sample, a sample's value does not depend on batch boundaries, launch shape or scheduling.
 #include "internal.h"
+#include "philox.cuh"
 
 namespace mbis {
 namespace {
-
-struct Philox4 {
-  uint32_t v[4];
-};
-
-__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                                 uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  Philox4 o = {{c0, c1, c2, c3}};
-  return o;
-}
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1) {
   const double u1 = ((double)a + 0.5) * 2.3283064365386963e-10;  // 2^-32

@@ -233,8 +233,8 @@ class TiledDemo:
 
 def tiled_demo(n_pool=1 << 22, snr=15.0, seed=POPULATION_SEED + 5):
     """Source at Mc = 25, q = 3.5 (m1 = 55.75, m2 = 15.93 Msun), zero spins, fixed sky and
-    orientation, H1+L1, 20-512 Hz at 1/4 Hz (1969 bins), coloured Gaussian noise at network
-    SNR 15, phase marginalised; x in [20, 28) with Mc = 24 + mod(x, 4), q in [1/6, 6]; bank
+    orientation, H1+L1, 20-128 Hz at 1/4 Hz (433 bins; every waveform of the space ends
+    below 80 Hz), coloured Gaussian noise at network SNR 15, phase marginalised; x in [20, 28) with Mc = 24 + mod(x, 4), q in [1/6, 6]; bank
     at minimal match 0.996, stopping after 2000 consecutive rejections; a prior pool of
     2^22 points."""
     mc, q = 25.0, 3.5
@@ -242,7 +242,7 @@ def tiled_demo(n_pool=1 << 22, snr=15.0, seed=POPULATION_SEED + 5):
     m2 = m1 / q
     spec = EventSpec(m1, m2, dict(chi1=0.0, chi2=0.0, ra=1.0, dec=0.5, psi=0.3, iota=0.4, tc=0.0, phic=0.0),
                      gmst=0.0, snr=snr, noise_seed=(seed << 8) + 1, draw_seed=(seed << 8) + 2)
-    w = Workload("tiled_demo", ["H1", "L1"], 20.0, 512.0, 0.25, [MC, Q], MARG_PHASE, 1 << 16, "mixed", "c64",
+    w = Workload("tiled_demo", ["H1", "L1"], 20.0, 128.0, 0.25, [MC, Q], MARG_PHASE, 1 << 16, "mixed", "c64",
                  1.0, 0, 0.0, [spec])
     return TiledDemo(w, 20.0, 28.0, 4.0, 24.0, 1.0 / 6.0, 6.0, 0.996, 2000, 4096, 1 << 17, (seed << 8) + 3,
                      n_pool, (seed << 8) + 4, (seed << 8) + 5)
