@@ -440,6 +440,108 @@ def batch_measurement(m, torch, steps=3, warmup=2):
     return out
 
 
+
+
+def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
+    """The tiled proposal of the two-parameter demonstration: template placement, the
+    tensor-core tile assignment of the 2^22-point prior pool (CUDA events; roofline in
+    useful FP16 tensor flops), the pool's member lists, and the seconds from the template
+    likelihoods to 1e4 effective samples."""
+    d = workloads.tiled_demo()
+    w = d.workload
+    spec = w.events[0]
+    ev = event_setup(m, w, spec, workloads.network(w.detectors))
+    q_max = max(d.q_hi, 1.0 / d.q_lo)
+    ev["prop"] = dict(ids=np.array([MC, Q], dtype=np.int32), mean=np.array([25.0, 3.5]), chol=np.diag([0.1, 0.1]),
+                      scale=1.0, lo=np.array([d.mc_base, 1.0]), hi=np.array([d.mc_base + d.mc_period, q_max]), flags=0)
+    t = m.mbis_tiling_create(w.f_lo, w.df, w.n_bins, ev["psd"][0], d.x_lo, d.x_hi, d.mc_period, d.mc_base, d.q_lo,
+                             d.q_hi)
+    ctx = make_ctx(m, w, ev, m.MIXED)
+    try:
+        cand = workloads.uniform_points(d.n_candidates, d.x_lo, d.x_hi, d.q_lo, d.q_hi, d.candidate_seed)
+        t0 = time.perf_counter()
+        T, used = m.mbis_tiling_bank(t, cand, d.min_match, d.stop_after, d.max_templates)
+        bank_s = time.perf_counter() - t0
+        _, phys, _ = m.mbis_tiling_templates(t)
+        N = d.n_pool
+        pool_h = workloads.uniform_points(N, d.x_lo, d.x_hi, d.q_lo, d.q_hi, d.pool_seed)
+        pool = torch.tensor(pool_h, dtype=torch.float64, device="cuda")
+        tile = torch.empty(N, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        m.mbis_tiling_assign(t, N, pool, tile, None, stream)       # warm-up
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.mbis_tiling_assign(t, N, pool, tile, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        t_assign = statistics.mean(times)
+        # useful work: one complex multiply-add (8 flops) per (sample, live bin, template);
+        # executed: samples sorted by live-bin count in CTAs of 128, templates sorted the
+        # same way in passes of 256 (two MMA blocks of N = 256), each (CTA, pass) running
+        # the 32-bin K-blocks that both reach
+        mc_p = d.mc_base + np.mod(pool_h[0], d.mc_period)
+        qp = np.maximum(pool_h[1], 1.0 / pool_h[1])
+        live = live_bins(mc_p, qp, w.f_lo, w.df, w.n_bins)
+        useful = 8.0 * float(live.sum()) * T
+        srt = np.zeros(((N + 127) // 128) * 128)
+        srt[:N] = np.sort(live)
+        kb_cta = np.ceil(srt.reshape(-1, 128).max(axis=1) / 32)
+        kc_t = np.sort(live_bins(phys[0], phys[1], w.f_lo, w.df, w.n_bins))[::-1]
+        kb_pass = np.array([np.ceil(kc_t[i:i + 256].max() / 32) for i in range(0, T, 256)])
+        kblocks = float(np.minimum(kb_cta[:, None], kb_pass[None, :]).sum())
+        executed = kblocks * 128 * 64 * 512 * 2
+        peak = peaks().get("bf16_tflops", 1900.0)   # dense FP16 runs at the BF16 rate
+        achieved = useful / t_assign / 1e12
+        t0 = time.perf_counter()
+        m.mbis_tiling_set_pool(t, N, pool)
+        pool_s = time.perf_counter() - t0
+        # per event: template likelihoods -> mixture -> batches of draws, likelihoods, weights
+        theta = torch.empty((2, batch), dtype=torch.float64, device="cuda")
+        lq, lp, ll = (torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(3))
+        th_t = torch.tensor(phys, dtype=torch.float64, device="cuda")
+        ll_t = torch.empty(T, dtype=torch.float64, device="cuda")
+        runs = []
+        for r in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.mbis_loglike(ctx, T, th_t, ll_t)
+            m.mbis_tiling_set_loglike(t, ll_t)
+            m.mbis_reset_running(ctx)
+            drawn = 0
+            while True:
+                m.mbis_tiling_draw(t, spec.draw_seed + r, drawn, batch, theta, lq, lp)
+                m.mbis_loglike(ctx, batch, theta, ll)
+                s = m.mbis_reduce(ctx, batch, ll, lp, lq, None, True)
+                drawn += batch
+                if s["ess"] >= target or drawn >= 1 << 22:
+                    break
+            runs.append(dict(seconds=time.perf_counter() - t0, ess=s["ess"], drawn=drawn, log_z=s["log_z"]))
+    finally:
+        m.mbis_destroy(ctx)
+        m.mbis_tiling_destroy(t)
+    return {"workload": "tiled proposal, two-parameter demonstration (App. A): cyclic chirp mass 24 + mod(x, 4) over "
+                        "x in [20, 28), q in [1/6, 6], Mc = 25, q = 3.5 source at SNR 15, H1+L1, 20-128 Hz at 1/4 Hz; "
+                        "bank at minimal match 0.996, prior pool of 2^22 points",
+            "templates": T, "candidates_visited": used, "bank_seconds": bank_s,
+            "assign": {"launch_ms": t_assign * 1e3, "samples_per_s": N / t_assign,
+                       "sample_template_matches_per_s": N * T / t_assign,
+                       "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": achieved / peak,
+                                    "note": "useful FP16 tensor flops (8 per sample x live bin x template) per "
+                                            "launch / launch time, against the measured dense BF16 burst peak (FP16 "
+                                            "runs at the BF16 rate)"},
+                       "executed_tflops": executed / t_assign / 1e12, "useful_over_executed": useful / executed},
+            "set_pool_seconds": pool_s,
+            "seconds_to_1e4_ess": {"median": statistics.median(x["seconds"] for x in runs),
+                                   "measured": "template likelihoods + mixture + batches of 2^14 draws, likelihoods "
+                                               "and merged weights until ESS >= 1e4 (wall clock)",
+                                   "runs": runs},
+            "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
+
+
 SERVE_SEED = 0x5E12E
 
 
@@ -545,8 +647,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--extras", default="ess,bbh,batch,serve",
-                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve) or 'none'")
+    ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled",
+                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-compare", type=int, default=0,
                     help="also process the stream's first K requests serially in FP64 (slow)")
@@ -587,6 +689,8 @@ def main():
             out["bbh"] = bbh_measurement(m, torch)
         if "batch" in extras:
             out["uneven_batch"] = batch_measurement(m, torch)
+        if "tiled" in extras:
+            out["tiled_proposal"] = tiled_measurement(m, torch)
         if "serve" in extras:
             served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
             if args.serve_compare > 0:

@@ -380,12 +380,14 @@ mbis_status mbis_tiling_match(mbis_tiling* t, int64_t n, const double* a, const 
 /* Tile of each point (App. A, "Tiling the prior volume"): the template of highest match,
  * the lowest index among equal ones.  pts (device, [2][n]); tile (device, n int32; -1 for
  * a point outside the space); match (device, n float, nullable) the best match.  The
- * sample-by-template overlaps are one TF32 tensor-core contraction (tcgen05, FP32
+ * sample-by-template overlaps are one FP16 tensor-core contraction (tcgen05, FP32
  * accumulation) over the live bins, the sample waveforms computed in registers and never
- * stored; matches carry ~1e-5 absolute error, so points whose two best templates match
- * within that may land in either tile.  Asynchronous: a device-side wait that timed out
- * is reported by the next mbis_tiling_set_pool.  Needs a bank.
- * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_CUDA. */
+ * stored; matches carry ~1e-4 absolute error at most, so points whose two best templates
+ * match within that may land in either tile.  Points are processed in order of their
+ * live-bin count (a device-side sort into scratch that the tiling object keeps and grows
+ * to the largest n seen), so calls on one tiling object must not overlap.  Asynchronous: a
+ * device-side wait that timed out is reported by the next mbis_tiling_set_pool.  Needs a
+ * bank; 0 <= n < 2^31.  Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
 mbis_status mbis_tiling_assign(mbis_tiling* t, int64_t n, const double* pts, int32_t* tile, float* match,
                                void* cuda_stream);
 

@@ -7,6 +7,8 @@
 //   u_k = w_k e^(-i Psi(f_k)) / sqrt(sum_{k' < kcut} w_k'^2),  w_k = f_k^(-7/6) / sqrt(S_k),
 // zero at and above the ISCO.  The match of two points is |sum_k conj(u_a,k) u_b,k|, the
 // normalised overlap maximised over a constant phase.
+#include <cuda_fp16.h>
+
 #include "physics.cuh"
 #include "philox.cuh"
 #include "tc.cuh"
@@ -164,7 +166,7 @@ __global__ void append_kernel(int32_t n, const int32_t* __restrict__ idx, const 
 // then the two whitening weights scaled by wscale = 1 / max(w), then padding.
 __global__ void bin_records_kernel(TilingGrid g, double wscale, float* out) {
   const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.n_kb * 8) return;
+  if (p >= g.n_kb * (kTileBins / 2)) return;
   float* r = out + (int64_t)p * kBinRecord;
   for (int e = 0; e < 2; ++e) {
     const int32_t k = 2 * p + e;
@@ -176,91 +178,199 @@ __global__ void bin_records_kernel(TilingGrid g, double wscale, float* out) {
   r[19] = 0.f;
 }
 
-// Template operand: chunk c holds templates 128c .. 128c + 127 as 256 rows (template t:
-// row 2t gives Re conj(a) b, row 2t + 1 Im conj(a) b against a sample row laid out as
-// (Re a_k, Im a_k) pairs), one 16-bin K-block of 32 TF32 values per 128-byte row, 16-byte
+// Template operand: pass p holds templates perm[256 p .. 256 p + 255] (ordered by live-bin
+// count; -1 pads), as two halves of 128 templates, each 256 rows (template slot i: row 2i
+// gives Re conj(a) b, row 2i + 1 Im conj(a) b against a sample row laid out as
+// (Re a_k, Im a_k) pairs), one 32-bin K-block of 64 FP16 values per 128-byte row, 16-byte
 // chunk c of row n at byte n * 128 + ((c ^ (n & 7)) << 4) (the 128-byte swizzle).
-__global__ void template_tiles_kernel(int32_t T, const double2* __restrict__ rows, TilingGrid g, float* out) {
-  const int32_t kb = blockIdx.x, chunk = blockIdx.y, n = threadIdx.x;
-  const int32_t t = chunk * kTileTemplates + (n >> 1);
+// Layout [pass][K-block][half][256 rows][64].
+__global__ void template_tiles_kernel(const int32_t* __restrict__ perm, const double2* __restrict__ rows, TilingGrid g,
+                                      __half* out) {
+  const int32_t kb = blockIdx.x, ph = blockIdx.y, n = threadIdx.x;
+  const int32_t p = ph >> 1, h = ph & 1;
+  const int32_t t = perm[p * 2 * kTileTemplates + h * kTileTemplates + (n >> 1)];
   const bool im = n & 1;
-  float* tile = out + ((int64_t)chunk * g.n_kb + kb) * 8192;
-  for (int kk = 0; kk < 16; ++kk) {
-    const int32_t k = kb * 16 + kk;
+  __half* tile = out + (((int64_t)p * g.n_kb + kb) * 2 + h) * (kTileBytes / 2);
+  for (int kk = 0; kk < kTileBins; ++kk) {
+    const int32_t k = kb * kTileBins + kk;
     double2 v = make_double2(0.0, 0.0);
-    if (t < T && k < g.K) v = rows[(int64_t)t * g.K + k];
+    if (t >= 0 && k < g.K) v = rows[(int64_t)t * g.K + k];
     const float e[2] = {(float)(im ? v.y : v.x), (float)(im ? -v.x : v.y)};
-    for (int h = 0; h < 2; ++h) {
-      const int kidx = 2 * kk + h, c16 = kidx >> 2, pos = kidx & 3;
-      tile[n * 32 + (((c16 ^ (n & 7)) << 2) | pos)] = tc::tf32_round(e[h]);
+    for (int c = 0; c < 2; ++c) {
+      const int kidx = 2 * kk + c, c16 = kidx >> 3, pos = kidx & 7;
+      tile[n * 64 + (((c16 ^ (n & 7)) << 3) | pos)] = __float2half_rn(e[c]);
     }
   }
 }
 
 // ---- tile assignment on the tensor cores ------------------------------------------------
 // The sample-by-template overlaps are a real contraction [samples x 2K] . [2K x 2T].  A CTA
-// of 256 threads owns two tiles of 128 samples and visits the templates in passes of 128
-// (one MMA column block of 256 per tile, TMEM columns [256 t, 256 t + 256)).  Per 16-bin
-// K-block every thread writes its sample's 16 (Re, Im) pairs, rounded to TF32, into its
-// row of a swizzled shared-memory tile; the block's template tile arrives by bulk copy;
-// the last thread done issues 2 x 4 tcgen05.mma.kind::tf32 and commits to an mbarrier.
-// After a pass's last K-block each thread reads its row's 128 complex overlaps back from
-// TMEM (one block late, before the next pass's first MMA overwrites them) and keeps the
-// running best.
-constexpr int kAThreads = 256;
-constexpr uint32_t kATile = 16384;                      // 128 rows x 128 bytes
-constexpr uint32_t kBTile = 32768;                      // 256 rows x 128 bytes
-constexpr uint32_t kAOffA = 0;                          // [2 buf][2 tile][kATile]
-constexpr uint32_t kAOffB = kAOffA + 2 * 2 * kATile;    // [2 buf][kBTile]
-constexpr uint32_t kASmem = kAOffB + 2 * kBTile + 1024;
-constexpr uint32_t kAIdesc = tc::idesc_tf32(128, 2 * kTileTemplates);
+// owns 128 samples (the MMA's M) and visits the templates in passes of 256: two MMA column
+// blocks of N = 256 (128 templates each as Re / Im rows), accumulated in TMEM columns
+// [0, 256) and [256, 512).  Templates are ordered by live-bin count and each pass runs only
+// over the K-blocks that both its templates and the CTA's samples reach.  Operands are FP16
+// (the 11-bit significand of TF32 at twice its rate and half its bytes; the normalised
+// waveform values, ~0.1, sit far inside the FP16 range).  Sixteen compute warps write the
+// sample operand: per 32-bin K-block, four threads per sample (one per 8-bin quarter)
+// compute e^(-i Psi) of their bins from FP32 phase coefficients and write them, rounded to
+// FP16, into the sample's row of a 128-byte-swizzled shared-memory tile.  A seventeenth warp
+// issues the 2 x 4 tcgen05.mma.kind::f16 of each block once its operands are in place,
+// commits to an mbarrier, and bulk-copies the next block's template tile.  After a pass's
+// last block each compute thread reads back 64 of its sample's 256 complex overlaps (one
+// block late, before the next pass's first MMA overwrites them) and keeps the running best;
+// the four parts' bests are merged at the end.
+constexpr int kParts = 4;                        // threads per sample
+constexpr int kACompute = 128 * kParts;          // compute threads
+constexpr int kAThreads = kACompute + 32;        // + the MMA-issuer warp
+constexpr uint32_t kATile = 16384;               // 128 rows x 128 bytes
+constexpr uint32_t kBHalf = kTileBytes;          // 256 rows (128 templates) x 128 bytes
+constexpr uint32_t kBBlock = 2 * kBHalf;         // one K-block of a pass
+constexpr uint32_t kAOffA = 0;                   // [2 buf][kATile]
+constexpr uint32_t kAOffB = kAOffA + 2 * kATile; // [2 buf][kBBlock]
+constexpr uint32_t kASmem = kAOffB + 2 * kBBlock + 1024;
+constexpr uint32_t kAIdesc = tc::idesc_f16(128, 2 * kTileTemplates);
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// The TaylorF2 phase coefficients of physics.cuh (phase_coeffs_a, the same series) in
+// single precision, for the FP16 sample operand: q >= 1, a = pi M, la = ln a, a13 = a^(1/3);
+// C[j] in turns for basis j = 0..7 (the constant and the coalescence-time term drop out of
+// the match).  The constants are folded in double at compile time.
+__device__ __forceinline__ void phase_coeffs_f32(float q, float chi1, float chi2, float a, float la, float a13,
+                                                 float* C) {
+  constexpr float pi = (float)kPi;
+  const float eta = q / ((1.f + q) * (1.f + q));
+  const float dm = (q - 1.f) / (q + 1.f);
+  const float xs = 0.5f * (chi1 + chi2), xa = 0.5f * (chi1 - chi2);
+  const float e2 = eta * eta, e3 = e2 * eta;
+  const float phi2 = (float)(3715.0 / 756.0) + (float)(55.0 / 9.0) * eta;
+  const float phi3 = -16.f * pi + (float)(113.0 / 3.0) * dm * xa + ((float)(113.0 / 3.0) - (float)(76.0 / 3.0) * eta) * xs;
+  const float phi4 = (float)(15293365.0 / 508032.0) + (float)(27145.0 / 504.0) * eta + (float)(3085.0 / 72.0) * e2 +
+                     (-50.625f + 200.f * eta) * xa * xa - 101.25f * dm * xa * xs + (-50.625f + 2.5f * eta) * xs * xs;
+  const float c5 = pi * ((float)(38645.0 / 756.0) - (float)(65.0 / 9.0) * eta) +
+                   dm * ((float)(-732985.0 / 2268.0) + (float)(140.0 / 9.0) * eta) * xa +
+                   ((float)(-732985.0 / 2268.0) + (float)(24260.0 / 81.0) * eta + (float)(340.0 / 9.0) * e2) * xs;
+  const float a6 = (float)(11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * kPi * kPi -
+                           6848.0 / 21.0 * (kEulerGamma + 1.3862943611198906)) +
+                   (float)(-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * kPi * kPi) * eta +
+                   (float)(76055.0 / 1728.0) * e2 - (float)(127825.0 / 1296.0) * e3 +
+                   pi * ((float)(2270.0 / 3.0) * dm * xa + ((float)(2270.0 / 3.0) - 520.f * eta) * xs) +
+                   ((float)(75515.0 / 144.0) - (float)(8225.0 / 18.0) * eta) * dm * xa * xs +
+                   ((float)(75515.0 / 288.0) - (float)(263245.0 / 252.0) * eta - 480.f * e2) * xa * xa +
+                   ((float)(75515.0 / 288.0) - (float)(232415.0 / 504.0) * eta + (float)(1255.0 / 9.0) * e2) * xs * xs;
+  const float phi7 =
+      pi * ((float)(77096675.0 / 254016.0) + (float)(378515.0 / 1512.0) * eta - (float)(74045.0 / 756.0) * e2) +
+      ((float)(-25150083775.0 / 3048192.0) + (float)(10566655595.0 / 762048.0) * eta -
+       (float)(1042165.0 / 3024.0) * e2 + (float)(5345.0 / 36.0) * e3) * xs +
+      dm * ((float)(-25150083775.0 / 3048192.0) + (float)(26804935.0 / 6048.0) * eta - (float)(1985.0 / 48.0) * e2) *
+          xa;
+  const float a23 = a13 * a13;
+  const float pre = (float)(3.0 / 128.0 / kTwoPi) / eta;
+  C[0] = pre / (a23 * a23 * a13);
+  C[1] = pre * phi2 / a;
+  C[2] = pre * phi3 / a23;
+  C[3] = pre * phi4 / a13;
+  C[4] = pre * c5;
+  C[5] = pre * a13 * (a6 - (float)(6848.0 / 63.0) * la);
+  C[6] = -pre * a13 * (float)(6848.0 / 63.0);
+  C[7] = pre * phi7 * a23;
+}
+
+// Per-sample set-up of the FP16 operand: the live-bin count from the total mass in FP64
+// (FP32 seed, one Newton step: the ISCO cut agrees with FP64 to the bin), the phase
+// coefficients in FP32, the inverse norm from the FP64 prefix table.
+struct FastSetup {
+  float cf[kNumBasis - 1];
+  int32_t kcut;
+  float inv_s;
+};
+
+__device__ __forceinline__ FastSetup fast_setup(const TilingSpace& sp, const TilingGrid& g, double x, double q) {
+  FastSetup o;
+  double mc, qp;
+  map_point(sp, x, q, mc, qp);
+  const double u = (1.0 + qp) * (1.0 + qp) / qp, u3 = u * u * u;
+  double y = (double)powf((float)u, 0.6f);
+  const double y4 = (y * y) * (y * y);
+  y = 0.8 * y + u3 / (5.0 * y4);                   // y^5 = u^3
+  const double m_sec = mc * kTsun * y;
+  o.kcut = live_bins_m(m_sec, g.f_lo, g.df, g.K);
+  const float am = (float)(kPi * m_sec);
+  phase_coeffs_f32((float)qp, (float)sp.chi1, (float)sp.chi2, am, logf(am), cbrtf(am), o.cf);
+  o.inv_s = o.kcut > 0 ? rsqrtf((float)(g.w2sum[o.kcut] * g.inv_wref2)) : 0.f;
+  return o;
+}
+
+__global__ void kcut_kernel(TilingSpace sp, TilingGrid g, int64_t n, const double* __restrict__ pts,
+                            int32_t* __restrict__ kc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = pts[i], q = pts[n + i];
+  int32_t k = 0;
+  if (in_space(sp, x, q)) {
+    double mc, qp;
+    map_point(sp, x, q, mc, qp);
+    const float qf = (float)qp;
+    const float m_sec = (float)(mc * kTsun) * powf((1.f + qf) * (1.f + qf) / qf, 0.6f);
+    const float fi = 1.f / (14.696938f * (float)kPi * m_sec);
+    k = (int32_t)fminf(fmaxf(ceilf((fi - (float)g.f_lo) / (float)g.df), 0.f), (float)g.K);
+  }
+  kc[i] = k;
+}
+
 __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // bbar[b]: template tile of buffer b landed; full[b]: the 256 threads wrote A[b];
-  // mbar[b]: the MMAs reading buffer b completed.
+  // bbar[b]: template tile of buffer b landed; full[b]: the 256 compute threads wrote A[b];
+  // mbar[b]: the MMAs reading buffers b completed.
   __shared__ __align__(8) uint64_t bbar[2], full[2], mbar[2];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_kmax, s_done[2];
+  __shared__ int s_kmax, s_nblk;
   __shared__ int s_issued_b[2], s_issued_m[2];
   __shared__ volatile int s_bad;
-  const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
-  const int64_t s = (int64_t)blockIdx.x * kAThreads + tid;
-  const bool active = s < a.n;
+  __shared__ float s_cf[kNumBasis - 1][128];
+  __shared__ float s_inv[128];
+  __shared__ int32_t s_kcut[128];
+  __shared__ float s_b2[kParts][128];
+  __shared__ int32_t s_bt[kParts][128];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool compute = tid < kACompute;
+  const int row = tid & 127, part = compute ? tid >> 7 : 0;
+  const int64_t slot = (int64_t)blockIdx.x * 128 + row;
+  const bool active = compute && slot < a.n;
+  const int64_t s = active ? (a.order ? (int64_t)a.order[slot] : slot) : 0;
 
-  // ---- per-sample set-up (FP64), coefficients handed to FP32 in turns
+  // ---- per-sample set-up by the first thread of each sample
   double x = 0.0, q = 1.0;
   if (active) {
     x = a.pts[s];
     q = a.pts[a.n + s];
   }
   const bool valid = active && in_space(a.sp, x, q);
-  float cf[kNumBasis - 1];
-  int32_t kcut = 0;
-  float inv_s = 0.f;  // 1 / norm, with the table's weights scaled by 1 / wref
-  if (valid) {
-    const PointSetup ps = point_setup(a.sp, a.g, x, q);
+  if (compute && part == 0) {
+    int32_t kc = 0;
+    float inv = 0.f;
+    if (valid) {
+      const FastSetup fs = fast_setup(a.sp, a.g, x, q);
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = (float)ps.pc.C[j];
-    kcut = ps.kcut;
-    inv_s = (float)(ps.inv_norm * a.g.wref);
-  } else {
+      for (int j = 0; j < kNumBasis - 1; ++j) s_cf[j][row] = fs.cf[j];
+      kc = fs.kcut;
+      inv = fs.inv_s;
+    } else {
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = 0.f;
+      for (int j = 0; j < kNumBasis - 1; ++j) s_cf[j][row] = 0.f;
+    }
+    s_kcut[row] = kc;
+    s_inv[row] = inv;
   }
-
   if (tid == 0) {
     s_kmax = 0;
     s_bad = 0;
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&bbar[b], 1);
-      tc::mbar_init(&full[b], kAThreads);
+      tc::mbar_init(&full[b], kACompute);
       tc::mbar_init(&mbar[b], 1);
-      s_done[b] = 0;
       s_issued_b[b] = 0;
       s_issued_m[b] = 0;
     }
@@ -270,152 +380,224 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  atomicMax(&s_kmax, kcut);
+  float cf[kNumBasis - 1];
+#pragma unroll
+  for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = s_cf[j][row];
+  const int32_t kcut = compute ? s_kcut[row] : 0;
+  const float inv_s = compute ? s_inv[row] : 0.f;
+  if (compute && part == 0) atomicMax(&s_kmax, kcut);
   __syncthreads();
   const uint32_t tmem = s_tmem;
-  const int32_t nkb = (s_kmax + 15) / 16;  // K-blocks this CTA needs
-  const int32_t nblk = nkb * a.n_chunk;    // blocks over all passes
+  const int32_t nkb_cta = (s_kmax + kTileBins - 1) / kTileBins;
+  // blocks of pass p: the K-blocks that both the pass's templates and this CTA's samples reach
+  auto pass_blocks = [&](int p) { return nkb_cta < a.nkb_pass[p] ? nkb_cta : a.nkb_pass[p]; };
+  if (tid == 0) {
+    int nb = 0;
+    for (int p = 0; p < a.n_pass; ++p) nb += pass_blocks(p);
+    s_nblk = nb;
+  }
+  __syncthreads();
+  const int32_t nblk = s_nblk;
 
   unsigned char* sA = sm + kAOffA;
   unsigned char* sB = sm + kAOffB;
-  auto load_b = [&](int g) {
-    const int b = g & 1;
-    const int32_t pass = g / nkb, kb = g % nkb;
-    const float* src = a.tiles + ((int64_t)pass * a.g.n_kb + kb) * 8192;
-    tc::mbar_expect_tx(&bbar[b], kBTile);
-    tc::bulk_g2s(sB + b * kBTile, src, kBTile / 2, &bbar[b]);
-    tc::bulk_g2s(sB + b * kBTile + kBTile / 2, src + 4096, kBTile / 2, &bbar[b]);
-    ++s_issued_b[b];
-  };
-  if (tid == 0 && nblk > 0) load_b(0);
-
   bool bad = false;
-  float best2 = -1.f;
+  float best2 = -1.f;   // this thread's best |overlap|^2 and template (compute threads)
   int32_t best_t = -1;
-  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(tile * 2 * kTileTemplates);
-  // this thread's 128 overlaps of pass `pass` against the running best (strictly greater:
-  // the lowest template index wins a tie)
-  auto drain = [&](int pass) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < 2 * kTileTemplates; c0 += 32) {
-      uint32_t r[32];
-      tc::tmem_ld32(tbase + c0, r);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
-        const float m2 = fmaf(re, re, im * im);
-        const int32_t t = pass * kTileTemplates + (c0 >> 1) + i;
-        if (t < a.T && m2 > best2) {
-          best2 = m2;
-          best_t = t;
-        }
-      }
-    }
-  };
 
-  const float4* recs = reinterpret_cast<const float4*>(a.bins);
-  for (int32_t g = 0; g < nblk; ++g) {
-    const int b = g & 1;
-    const int32_t pass = g / nkb, kb = g % nkb;
-    if (g >= 2) {
-      // A[b] is free once the MMAs of block g - 2 completed
-      const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)(((g - 2) >> 1) & 1));
-      if (__any_sync(0xffffffffu, !ok || s_bad)) {
-        bad = true;
-        break;
-      }
-    }
-    unsigned char* rowA = sA + (b * 2 + tile) * kATile + row * 128;
-#pragma unroll 2
-    for (int kk = 0; kk < 16; kk += 2) {
-      const int32_t k = kb * 16 + kk;
-      float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k < kcut) {
-        const float4* rc = recs + (int64_t)(k >> 1) * (kBinRecord / 4);
-        const float4 r0 = __ldg(rc), r1 = __ldg(rc + 1), r2 = __ldg(rc + 2), r3 = __ldg(rc + 3), r4 = __ldg(rc + 4);
-        float2 t = __fmul2_rn(f2(cf[0]), make_float2(r0.x, r0.y));
-        t = __ffma2_rn(f2(cf[1]), make_float2(r0.z, r0.w), t);
-        t = __ffma2_rn(f2(cf[2]), make_float2(r1.x, r1.y), t);
-        t = __ffma2_rn(f2(cf[3]), make_float2(r1.z, r1.w), t);
-        t = __ffma2_rn(f2(cf[4]), make_float2(r2.x, r2.y), t);
-        t = __ffma2_rn(f2(cf[5]), make_float2(r2.z, r2.w), t);
-        t = __ffma2_rn(f2(cf[6]), make_float2(r3.x, r3.y), t);
-        t = __ffma2_rn(f2(cf[7]), make_float2(r3.z, r3.w), t);
-        t.x -= rintf(t.x);  // turns in [-1/2, 1/2]: the MUFU argument stays in [-pi, pi]
-        t.y -= rintf(t.y);
-        const float2 ang = __fmul2_rn(t, f2(kTwoPiF));
-        float2 sn, cs;
-        __sincosf(ang.x, &sn.x, &cs.x);
-        __sincosf(ang.y, &sn.y, &cs.y);
-        const float2 amp = __fmul2_rn(make_float2(r4.x, r4.y), f2(inv_s));
-        const float2 re = __fmul2_rn(amp, cs), im = __fmul2_rn(amp, sn);  // u = amp e^(-i 2 pi t)
-        hi = make_float4(tc::tf32_round(re.x), tc::tf32_round(-im.x), tc::tf32_round(re.y), tc::tf32_round(-im.y));
-        if (k + 1 >= kcut) {
-          hi.z = 0.f;
-          hi.w = 0.f;
-        }
-      }
-      const int chunk = (kk >> 1) ^ (row & 7);
-      *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
-    }
-    if (kb == 0 && pass > 0) {
-      // the pass that ended with block g - 1: read its overlaps before the MMAs of block g
-      // start the accumulator afresh
-      const bool ok = tc::mbar_wait(&mbar[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1));
-      if (__any_sync(0xffffffffu, !ok || s_bad)) {
-        bad = true;
-        break;
-      }
-      tc::fence_after_sync();
-      drain(pass - 1);
-      tc::fence_before_sync();
-    }
-    tc::fence_proxy_async();
-    tc::mbar_arrive(&full[b]);
-    if (atomicAdd(&s_done[b], 1) == kAThreads - 1) {
-      atomicExch(&s_done[b], 0);
-      __threadfence_block();
-      const uint32_t par = (uint32_t)((g >> 1) & 1);
-      bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar[b], par);
-      if (ok) {
-        tc::fence_after_sync();
-        const uint32_t a_base = tc::smem_addr(sA + b * 2 * kATile);
-        const uint32_t b_base = tc::smem_addr(sB + b * kBTile);
+  if (!compute) {
+    // ---- the MMA-issuer warp (one elected thread)
+    if (lane == 0 && nblk > 0) {
+      auto load_b = [&](int g, int p, int kb) {
+        const int b = g & 1;
+        const unsigned char* src = a.tiles + ((int64_t)p * a.g.n_kb + kb) * kBBlock;
+        tc::mbar_expect_tx(&bbar[b], kBBlock);
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int c = 0; c < 4; ++c)
+          tc::bulk_g2s(sB + b * kBBlock + c * (kBBlock / 4), src + c * (kBBlock / 4), kBBlock / 4, &bbar[b]);
+        ++s_issued_b[b];
+      };
+      int p = 0, kb = 0;
+      while (p < a.n_pass && pass_blocks(p) == 0) ++p;
+      load_b(0, p, 0);
+      for (int g = 0; g < nblk; ++g) {
+        const int b = g & 1;
+        const uint32_t par = (uint32_t)((g >> 1) & 1);
+        bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar[b], par);
+        if (ok && s_bad) ok = false;
+        if (!ok) {
+          bad = true;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t a_base = tc::smem_addr(sA + b * kATile);
+        const uint32_t b_base = tc::smem_addr(sB + b * kBBlock);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            tc::mma_tf32(tmem + t * 2 * kTileTemplates, tc::desc_k_sw128(a_base + t * kATile + ks * 32),
-                         tc::desc_k_sw128(b_base + ks * 32), kAIdesc, (kb > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_f16(tmem + h * 2 * kTileTemplates, tc::desc_k_sw128(a_base + ks * 32),
+                        tc::desc_k_sw128(b_base + h * kBHalf + ks * 32), kAIdesc, (kb > 0 || ks > 0) ? 1u : 0u);
         tc::commit(&mbar[b]);
         ++s_issued_m[b];
+        // the next block: same pass or the next pass with blocks
+        if (++kb >= pass_blocks(p)) {
+          kb = 0;
+          do {
+            ++p;
+          } while (p < a.n_pass && pass_blocks(p) == 0);
+        }
         if (g + 1 < nblk) {
           // buffer b ^ 1 is free once the MMAs of block g - 1 completed
           ok = g < 1 || tc::mbar_wait(&mbar[b ^ 1], (uint32_t)(((g - 1) >> 1) & 1));
-          if (ok) load_b(g + 1);
+          if (!ok) {
+            bad = true;
+            break;
+          }
+          load_b(g + 1, p, kb);
         }
       }
-      if (!ok) {
+      if (bad) {
         s_bad = 1;
         atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
       }
     }
-  }
-  if (!bad && nblk > 0) {
-    const bool ok = tc::mbar_wait(&mbar[(nblk - 1) & 1], (uint32_t)(((nblk - 1) >> 1) & 1));
-    if (__any_sync(0xffffffffu, !ok || s_bad)) {
-      bad = true;
-    } else {
-      tc::fence_after_sync();
-      drain(a.n_chunk - 1);
-      tc::fence_before_sync();
+    __syncwarp();
+  } else {
+    // ---- compute warps
+    // TMEM columns [128 part, 128 part + 128): pass slots 64 part .. 64 part + 63
+    const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(part * 128);
+    // this thread's 64 overlaps of pass p against the running best; a tie goes to the lowest
+    // template index
+    auto drain = [&](int p) {
+      const int32_t* perm = a.perm + (int64_t)p * 2 * kTileTemplates + part * 64;
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tbase + c0, r);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
+          const float m2 = fmaf(re, re, im * im);
+          const int32_t t = __ldg(perm + (c0 >> 1) + i);
+          if (t >= 0 && (m2 > best2 || (m2 == best2 && t < best_t))) {
+            best2 = m2;
+            best_t = t;
+          }
+        }
+      }
+    };
+    const float4* recs = reinterpret_cast<const float4*>(a.bins);
+    unsigned char* rowA0 = sA + row * 128;
+    int g = 0, last_p = -1;
+    for (int p = 0; p < a.n_pass && !bad; ++p) {
+      const int nb = pass_blocks(p);
+      for (int kb = 0; kb < nb; ++kb, ++g) {
+        const int b = g & 1;
+        if (g >= 2) {
+          // A[b] is free once the MMAs of block g - 2 completed
+          const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)(((g - 2) >> 1) & 1));
+          if (__any_sync(0xffffffffu, !ok || s_bad)) {
+            bad = true;
+            break;
+          }
+        }
+        unsigned char* rowA = rowA0 + b * kATile;
+        // this thread's 8 bins of the block: 2 chunks of 16 bytes, 4 bins (8 FP16) each
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = 2 * part + j;
+          uint32_t wv[4];
+#pragma unroll
+          for (int pr = 0; pr < 2; ++pr) {
+            const int32_t k = kb * kTileBins + 4 * c + 2 * pr;
+            float2 re = f2(0.f), im = f2(0.f);
+            if (k < kcut) {
+              const float4* rc = recs + (int64_t)(k >> 1) * (kBinRecord / 4);
+              const float4 r0 = __ldg(rc), r1 = __ldg(rc + 1), r2 = __ldg(rc + 2), r3 = __ldg(rc + 3),
+                           r4 = __ldg(rc + 4);
+              float2 t = __fmul2_rn(f2(cf[0]), make_float2(r0.x, r0.y));
+              t = __ffma2_rn(f2(cf[1]), make_float2(r0.z, r0.w), t);
+              t = __ffma2_rn(f2(cf[2]), make_float2(r1.x, r1.y), t);
+              t = __ffma2_rn(f2(cf[3]), make_float2(r1.z, r1.w), t);
+              t = __ffma2_rn(f2(cf[4]), make_float2(r2.x, r2.y), t);
+              t = __ffma2_rn(f2(cf[5]), make_float2(r2.z, r2.w), t);
+              t = __ffma2_rn(f2(cf[6]), make_float2(r3.x, r3.y), t);
+              t = __ffma2_rn(f2(cf[7]), make_float2(r3.z, r3.w), t);
+              t.x -= rintf(t.x);  // turns in [-1/2, 1/2]: the MUFU argument stays in [-pi, pi]
+              t.y -= rintf(t.y);
+              const float2 ang = __fmul2_rn(t, f2(kTwoPiF));
+              float2 sn, cs;
+              __sincosf(ang.x, &sn.x, &cs.x);
+              __sincosf(ang.y, &sn.y, &cs.y);
+              const float2 amp = __fmul2_rn(make_float2(r4.x, r4.y), f2(inv_s));
+              re = __fmul2_rn(amp, cs);   // u = amp e^(-i 2 pi t)
+              im = __fmul2_rn(amp, sn);
+              if (k + 1 >= kcut) {
+                re.y = 0.f;
+                im.y = 0.f;
+              }
+            }
+            const __half2 h0 = __floats2half2_rn(re.x, -im.x), h1 = __floats2half2_rn(re.y, -im.y);
+            wv[2 * pr] = *reinterpret_cast<const uint32_t*>(&h0);
+            wv[2 * pr + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+          }
+          *reinterpret_cast<uint4*>(rowA + ((c ^ (row & 7)) << 4)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        if (kb == 0 && last_p >= 0) {
+          // the pass that ended with block g - 1: read its overlaps before the MMAs of block g
+          // start the accumulators afresh
+          const bool ok = tc::mbar_wait(&mbar[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1));
+          if (__any_sync(0xffffffffu, !ok || s_bad)) {
+            bad = true;
+            break;
+          }
+          tc::fence_after_sync();
+          drain(last_p);
+          tc::fence_before_sync();
+        }
+        tc::fence_proxy_async();
+        tc::mbar_arrive(&full[b]);
+      }
+      if (nb > 0) last_p = p;
+    }
+    if (!bad && nblk > 0) {
+      const bool ok = tc::mbar_wait(&mbar[(nblk - 1) & 1], (uint32_t)(((nblk - 1) >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok || s_bad)) {
+        bad = true;
+      } else {
+        tc::fence_after_sync();
+        drain(last_p);
+        tc::fence_before_sync();
+      }
+    }
+    if (bad) {
+      s_bad = 1;
+      atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
     }
   }
-  if (bad) {
-    s_bad = 1;
-    atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
+  // merge the four parts' bests of each sample (a tie goes to the lower template index)
+  if (compute) {
+    s_b2[part][row] = best2;
+    s_bt[part][row] = best_t;
   }
   __syncthreads();
+  if (compute && part == 0) {
+#pragma unroll
+    for (int o = 1; o < kParts; ++o) {
+      const float o2 = s_b2[o][row];
+      const int32_t ot = s_bt[o][row];
+      if (ot >= 0 && (best_t < 0 || o2 > best2 || (o2 == best2 && ot < best_t))) {
+        best2 = o2;
+        best_t = ot;
+      }
+    }
+    if (active) {
+      const bool ok = valid && kcut > 0 && !s_bad && best_t >= 0;
+      a.tile[s] = ok ? best_t : -1;
+      if (a.match) a.match[s] = ok ? sqrtf(fmaxf(best2, 0.f)) : 0.f;
+    }
+  }
   if (tid == 0 && s_bad) {
     // let every copy and MMA issued land (bounded) before the CTA releases its memory
     for (int b = 0; b < 2; ++b) {
@@ -426,11 +608,6 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc<512>(tmem);
-  if (active) {
-    const bool ok = valid && kcut > 0 && !bad && !s_bad && best_t >= 0;
-    a.tile[s] = ok ? best_t : -1;
-    if (a.match) a.match[s] = ok ? sqrtf(fmaxf(best2, 0.f)) : 0.f;
-  }
 }
 
 // ---- stable counting sort of tile indices ---------------------------------------------
@@ -601,15 +778,22 @@ cudaError_t launch_tiling_append(int32_t n, const int32_t* idx, const double2* s
 }
 
 cudaError_t launch_tiling_bin_records(const TilingGrid& g, double wscale, float* out, cudaStream_t s) {
-  const int32_t n = g.n_kb * 8;
+  const int32_t n = g.n_kb * (kTileBins / 2);
   bin_records_kernel<<<(n + 127) / 128, 128, 0, s>>>(g, wscale, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tiling_template_tiles(int32_t T, const double2* rows, const TilingGrid& g, int32_t n_chunk,
-                                         float* out, cudaStream_t s) {
-  dim3 grid(g.n_kb, n_chunk);
-  template_tiles_kernel<<<grid, 256, 0, s>>>(T, rows, g, out);
+cudaError_t launch_tiling_template_tiles(const int32_t* perm, int32_t n_pass, const double2* rows, const TilingGrid& g,
+                                         void* out, cudaStream_t s) {
+  dim3 grid(g.n_kb, 2 * n_pass);
+  template_tiles_kernel<<<grid, 256, 0, s>>>(perm, rows, g, static_cast<__half*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tiling_kcut(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, int32_t* kc,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  kcut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, g, n, pts, kc);
   return cudaGetLastError();
 }
 
@@ -621,7 +805,7 @@ cudaError_t launch_tiling_assign(const AssignArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int64_t blocks = (a.n + kAThreads - 1) / kAThreads;
+  const int64_t blocks = (a.n + 127) / 128;
   assign_kernel<<<(unsigned)blocks, kAThreads, kASmem, s>>>(a);
   return cudaGetLastError();
 }

@@ -31,8 +31,14 @@ struct mbis_tiling {
   std::vector<int32_t> cand_idx;
   double2* d_rows = nullptr;  // [cap][K]
   double2* d_kmaj = nullptr;  // [K][cap]
-  float* d_tiles = nullptr;   // [n_chunk][n_kb][8192]
-  int32_t n_chunk = 0;
+  void* d_tiles = nullptr;    // FP16 [n_pass][n_kb][2][256 x 64]
+  int32_t n_pass = 0;
+  int32_t* d_perm = nullptr;  // [n_pass * 256] templates by pass slot (ordered by live-bin count), -1 pads
+  std::vector<int32_t> nkb_pass;
+  // scratch of the assignment's sample ordering (grown on demand)
+  int64_t scr_n = 0;
+  int32_t *d_kc = nullptr, *d_order = nullptr, *d_shist = nullptr, *d_scount = nullptr, *d_soffset = nullptr,
+          *d_snbad = nullptr;
   // pool
   int64_t N = 0;
   double* d_pool = nullptr;   // [2][N]
@@ -54,6 +60,7 @@ struct mbis_tiling {
     g.w = d_w;
     g.w2sum = d_w2sum;
     g.wref = wref;
+    g.inv_wref2 = 1.0 / (wref * wref);
     return g;
   }
 };
@@ -110,10 +117,22 @@ void drop_bank(mbis_tiling* t) {
   tfree(t->d_rows);
   tfree(t->d_kmaj);
   tfree(t->d_tiles);
-  t->T = t->cap = t->n_chunk = 0;
+  tfree(t->d_perm);
+  t->nkb_pass.clear();
+  t->T = t->cap = t->n_pass = 0;
   t->tx.clear();
   t->tq.clear();
   t->cand_idx.clear();
+}
+
+void drop_scratch(mbis_tiling* t) {
+  tfree(t->d_kc);
+  tfree(t->d_order);
+  tfree(t->d_shist);
+  tfree(t->d_scount);
+  tfree(t->d_soffset);
+  tfree(t->d_snbad);
+  t->scr_n = 0;
 }
 
 bool in_space(const TilingSpace& s, double x, double q) {
@@ -213,7 +232,7 @@ mbis_status mbis_tiling_create(const mbis_freq_grid* grid, const double* psd, co
   t->df = grid->df;
   t->n_bins = grid->n_bins;
   t->K = K;
-  t->n_kb = (K + 15) / 16;
+  t->n_kb = (K + mbis::kTileBins - 1) / mbis::kTileBins;
   t->wref = wref;
   double* d_w2 = nullptr;
   auto fail_free = [&](mbis_status st, const std::string& msg) {
@@ -224,7 +243,7 @@ mbis_status mbis_tiling_create(const mbis_freq_grid* grid, const double* psd, co
   if (cudaMalloc(&t->d_w, sizeof(double) * K) != cudaSuccess ||
       cudaMalloc(&t->d_w2sum, sizeof(double) * (K + 1)) != cudaSuccess ||
       cudaMalloc(&d_w2, sizeof(double) * K) != cudaSuccess ||
-      cudaMalloc(&t->d_bins, sizeof(float) * (size_t)t->n_kb * 8 * mbis::kBinRecord) != cudaSuccess ||
+      cudaMalloc(&t->d_bins, sizeof(float) * (size_t)t->n_kb * (mbis::kTileBins / 2) * mbis::kBinRecord) != cudaSuccess ||
       cudaMalloc(&t->d_err, sizeof(int32_t)) != cudaSuccess)
     return fail_free(MBIS_E_OOM, "mbis_tiling_create: out of device memory");
   cudaError_t e = cudaMemcpy(t->d_w, w.data(), sizeof(double) * K, cudaMemcpyHostToDevice);
@@ -242,6 +261,7 @@ mbis_status mbis_tiling_create(const mbis_freq_grid* grid, const double* psd, co
 void mbis_tiling_destroy(mbis_tiling* t) {
   if (!t) return;
   drop_bank(t);
+  drop_scratch(t);
   tfree(t->d_w);
   tfree(t->d_w2sum);
   tfree(t->d_bins);
@@ -354,11 +374,32 @@ mbis_status mbis_tiling_bank(mbis_tiling* t, int64_t n_cand, const double* cand,
     drop_bank(t);
     return st;
   }
-  // TF32 template tiles of the tensor-core assignment
-  t->n_chunk = (t->T + mbis::kTileTemplates - 1) / mbis::kTileTemplates;
-  T_TRY(t, cudaMalloc(&t->d_tiles, sizeof(float) * (size_t)t->n_chunk * t->n_kb * 8192));
-  T_TRY(t, mbis::launch_tiling_template_tiles(t->T, t->d_rows, g, t->n_chunk, t->d_tiles, nullptr));
-  T_TRY(t, cudaDeviceSynchronize());
+  // TF32 template tiles of the tensor-core assignment: templates ordered by live-bin count
+  // (most first) into passes of 256, each pass running over the K-blocks its templates reach
+  {
+    const int32_t T = t->T;
+    std::vector<int32_t> kc(T), order(T);
+    for (int32_t j = 0; j < T; ++j) {
+      double mc, qp;
+      physical(t->sp, t->tx[j], t->tq[j], &mc, &qp);
+      kc[j] = mbis::live_bins_m(mbis::total_mass_seconds(mc, qp), t->f_lo, t->df, K);
+      order[j] = j;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return kc[a] > kc[b]; });
+    t->n_pass = (T + mbis::kPassTemplates - 1) / mbis::kPassTemplates;
+    std::vector<int32_t> perm((size_t)t->n_pass * mbis::kPassTemplates, -1);
+    t->nkb_pass.assign(t->n_pass, 0);
+    for (int32_t i = 0; i < T; ++i) {
+      perm[i] = order[i];
+      const int32_t p = i / mbis::kPassTemplates;
+      t->nkb_pass[p] = std::max(t->nkb_pass[p], (kc[order[i]] + mbis::kTileBins - 1) / mbis::kTileBins);
+    }
+    T_TRY(t, cudaMalloc(&t->d_perm, sizeof(int32_t) * perm.size()));
+    T_TRY(t, cudaMemcpy(t->d_perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
+    T_TRY(t, cudaMalloc(&t->d_tiles, (size_t)t->n_pass * t->n_kb * 2 * mbis::kTileBytes));
+    T_TRY(t, mbis::launch_tiling_template_tiles(t->d_perm, t->n_pass, t->d_rows, g, t->d_tiles, nullptr));
+    T_TRY(t, cudaDeviceSynchronize());
+  }
   if (n_templates) *n_templates = t->T;
   if (n_used) *n_used = i;
   return MBIS_OK;
@@ -391,20 +432,45 @@ mbis_status mbis_tiling_match(mbis_tiling* t, int64_t n, const double* a, const 
 mbis_status mbis_tiling_assign(mbis_tiling* t, int64_t n, const double* pts, int32_t* tile, float* match, void* stream) {
   if (!t) return tfail(nullptr, MBIS_E_INVALID, "mbis_tiling_assign: null tiling");
   if (t->T == 0) return tfail(t, MBIS_E_STATE, "mbis_tiling_assign: no bank");
-  if (n < 0 || (n > 0 && (!pts || !tile))) return tfail(t, MBIS_E_INVALID, "mbis_tiling_assign: bad n or buffer");
+  if (n < 0 || n > 2147483647LL || (n > 0 && (!pts || !tile)))
+    return tfail(t, MBIS_E_INVALID, "mbis_tiling_assign: need 0 <= n < 2^31 and buffers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0) return MBIS_OK;
+  // process the points in order of their live-bin count, so that the 128 samples of a CTA
+  // reach similar K (a stable counting sort on the count)
+  if (n > t->scr_n) {
+    drop_scratch(t);
+    const int64_t n_seg = (n + mbis::kSortSegment - 1) / mbis::kSortSegment;
+    if (cudaMalloc(&t->d_kc, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&t->d_order, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&t->d_shist, sizeof(int32_t) * (size_t)n_seg * (t->K + 1)) != cudaSuccess ||
+        cudaMalloc(&t->d_scount, sizeof(int32_t) * (t->K + 1)) != cudaSuccess ||
+        cudaMalloc(&t->d_soffset, sizeof(int32_t) * (t->K + 1)) != cudaSuccess ||
+        cudaMalloc(&t->d_snbad, sizeof(int32_t)) != cudaSuccess) {
+      drop_scratch(t);
+      return tfail(t, MBIS_E_OOM, "mbis_tiling_assign: out of device memory");
+    }
+    t->scr_n = n;
+  }
+  T_TRY(t, mbis::launch_tiling_kcut(t->sp, t->grid(), n, pts, t->d_kc, s));
+  T_TRY(t, mbis::launch_tiling_lists(n, t->d_kc, t->K + 1, t->d_shist, t->d_scount, t->d_soffset, t->d_snbad,
+                                     t->d_order, s));
   mbis::AssignArgs a;
   a.sp = t->sp;
   a.g = t->grid();
   a.n = n;
   a.pts = pts;
+  a.order = t->d_order;
   a.tile = tile;
   a.match = match;
   a.T = t->T;
-  a.n_chunk = t->n_chunk;
-  a.tiles = t->d_tiles;
+  a.n_pass = t->n_pass;
+  a.perm = t->d_perm;
+  a.tiles = static_cast<const unsigned char*>(t->d_tiles);
   a.bins = t->d_bins;
   a.err = t->d_err;
-  T_TRY(t, mbis::launch_tiling_assign(a, static_cast<cudaStream_t>(stream)));
+  for (int p = 0; p < mbis::kMaxPasses; ++p) a.nkb_pass[p] = p < t->n_pass ? t->nkb_pass[p] : 0;
+  T_TRY(t, mbis::launch_tiling_assign(a, s));
   return MBIS_OK;
 }
 

@@ -9,9 +9,13 @@
 
 namespace mbis {
 
-constexpr int kTileTemplates = 128;       // templates per tensor-core pass (MMA N = 256 real columns)
+constexpr int kTileTemplates = 128;       // templates per MMA column block (N = 256 real columns)
+constexpr int kPassTemplates = 2 * kTileTemplates;  // templates per pass of the assignment
 constexpr int kTilingMaxTemplates = 16384;
+constexpr int kMaxPasses = kTilingMaxTemplates / kPassTemplates;
 constexpr int kBinRecord = 20;            // floats per bin pair of the FP32 table: 8 basis pairs, w pair, pad
+constexpr int kTileBins = 32;             // bins per K-block of the assignment: 64 FP16 values, one 128-byte row
+constexpr uint32_t kTileBytes = 32768;    // one half of a pass's K-block: 256 rows x 128 bytes
 
 // The sampled space on the device.
 struct TilingSpace {
@@ -22,10 +26,11 @@ struct TilingSpace {
 struct TilingGrid {
   double f_lo, df;
   int32_t K;           // bins any point of the space reaches (largest live-bin count)
-  int32_t n_kb;        // 16-bin K-blocks covering K
+  int32_t n_kb;        // kTileBins-bin K-blocks covering K
   const double* w;     // [K] f^(-7/6) / sqrt(S)
   const double* w2sum; // [K + 1] prefix sums of w^2
   double wref;         // max w: the FP32 table holds w / wref
+  double inv_wref2;    // 1 / wref^2
 };
 
 // FP64 unit-norm waveforms of n points (pts [2][n]): rows [n][K] (nullable) and k-major
@@ -41,23 +46,31 @@ cudaError_t launch_tiling_pair_match(const TilingSpace& sp, const TilingGrid& g,
 // copy rows src[idx[i]] (n rows of K) into dst rows row0 + i and k-major columns row0 + i
 cudaError_t launch_tiling_append(int32_t n, const int32_t* idx, const double2* src, int32_t K, double2* dst_rows,
                                  int32_t row0, double2* dst_kmaj, int32_t ldk, cudaStream_t s);
-// FP32 basis / weight records for the tensor-core pass: [n_kb * 8 bin pairs][kBinRecord]
+// FP32 basis / weight records for the tensor-core pass: [n_kb * kTileBins / 2 bin pairs][kBinRecord]
 cudaError_t launch_tiling_bin_records(const TilingGrid& g, double wscale, float* out, cudaStream_t s);
-// TF32 template tiles: [n_chunk][n_kb][256 rows x 32] swizzled K-major
-cudaError_t launch_tiling_template_tiles(int32_t T, const double2* rows, const TilingGrid& g, int32_t n_chunk,
-                                         float* out, cudaStream_t s);
+// FP16 template tiles: [n_pass][n_kb][2 halves][256 rows x 64] swizzled K-major, templates
+// in the order perm ([n_pass * 256], -1 pads)
+cudaError_t launch_tiling_template_tiles(const int32_t* perm, int32_t n_pass, const double2* rows, const TilingGrid& g,
+                                         void* out, cudaStream_t s);
+// approximate live-bin count of each point (0 outside the space): the sort key of the
+// assignment's sample order
+cudaError_t launch_tiling_kcut(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, int32_t* kc,
+                               cudaStream_t s);
 
 struct AssignArgs {
   TilingSpace sp;
   TilingGrid g;
   int64_t n;
   const double* pts;     // [2][n]
+  const int32_t* order;  // [n] processing order of the points (null: as given)
   int32_t* tile;         // [n]
   float* match;          // [n] or null
-  int32_t T, n_chunk;
-  const float* tiles;    // template tiles
+  int32_t T, n_pass;
+  const int32_t* perm;   // [n_pass * 256] template of each pass slot, -1 pads
+  const unsigned char* tiles;  // FP16 template tiles
   const float* bins;     // bin records
   int32_t* err;          // device error word
+  int32_t nkb_pass[kMaxPasses];  // K-blocks each pass's templates reach
 };
 cudaError_t launch_tiling_assign(const AssignArgs& a, cudaStream_t s);
 

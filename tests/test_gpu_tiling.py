@@ -3,7 +3,7 @@ oracle on the two-parameter demonstration space.
 
 * FP64 matches and template placement: identical banks (every accept decision of the
   oracle lies far from the minimal match compared with FP64 rounding).
-* Tile assignment (TF32 tensor-core contraction): the chosen template's match is within
+* Tile assignment (FP16 tensor-core contraction): the chosen template's match is within
   MATCH_TOL of the best one, and equals the oracle's choice wherever the two best
   templates differ by more than 2 MATCH_TOL; the reported match is within MATCH_TOL.
 * Member lists, mixture and draws: bitwise the oracle's on a pool without near ties.
@@ -21,7 +21,7 @@ from gpu_common import LOGL_TOL, m, torch, gpu_context, set_metric  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
-# TF32 operands round to 2^-11 relative: with unit-norm waveforms the match error is at most
+# FP16 operands round to 2^-11 relative: with unit-norm waveforms the match error is at most
 # ~1e-3 (all roundings aligned) and ~3e-5 for independent roundings over 100-240 live bins;
 # the largest seen over a few thousand points is 7.6e-5.
 MATCH_TOL = 2e-4
