@@ -378,7 +378,8 @@ mbis_status mbis_tiling_match(mbis_tiling* t, int64_t n, const double* a, const 
                               void* cuda_stream);
 
 /* Tile of each point (App. A, "Tiling the prior volume"): the template of highest match,
- * the lowest index among equal ones.  pts (device, [2][n]); tile (device, n int32; -1 for
+ * equal FP32 matches going to the template the contraction visits first (templates are
+ * visited in order of live-bin count).  pts (device, [2][n]); tile (device, n int32; -1 for
  * a point outside the space); match (device, n float, nullable) the best match.  The
  * sample-by-template overlaps are one FP16 tensor-core contraction (tcgen05, FP32
  * accumulation) over the live bins, the sample waveforms computed in registers and never

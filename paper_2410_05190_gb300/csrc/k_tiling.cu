@@ -302,20 +302,26 @@ __device__ __forceinline__ FastSetup fast_setup(const TilingSpace& sp, const Til
   return o;
 }
 
-__global__ void kcut_kernel(TilingSpace sp, TilingGrid g, int64_t n, const double* __restrict__ pts,
-                            int32_t* __restrict__ kc) {
+// Set-up of every point at full occupancy: its record (FP32 phase coefficients, inverse
+// norm, live-bin count; zero outside the space) and its live-bin count, the key that
+// orders samples so that a CTA's samples reach similar K.
+__global__ void setup_kernel(TilingSpace sp, TilingGrid g, int64_t n, const double* __restrict__ pts,
+                             float4* __restrict__ rec, int32_t* __restrict__ kc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double x = pts[i], q = pts[n + i];
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
   int32_t k = 0;
   if (in_space(sp, x, q)) {
-    double mc, qp;
-    map_point(sp, x, q, mc, qp);
-    const float qf = (float)qp;
-    const float m_sec = (float)(mc * kTsun) * powf((1.f + qf) * (1.f + qf) / qf, 0.6f);
-    const float fi = 1.f / (14.696938f * (float)kPi * m_sec);
-    k = (int32_t)fminf(fmaxf(ceilf((fi - (float)g.f_lo) / (float)g.df), 0.f), (float)g.K);
+    const FastSetup fs = fast_setup(sp, g, x, q);
+    k = fs.kcut;
+    r0 = make_float4(fs.cf[0], fs.cf[1], fs.cf[2], fs.cf[3]);
+    r1 = make_float4(fs.cf[4], fs.cf[5], fs.cf[6], fs.cf[7]);
+    r2 = make_float4(fs.inv_s, __int_as_float(k), 0.f, 0.f);
   }
+  rec[3 * i] = r0;
+  rec[3 * i + 1] = r1;
+  rec[3 * i + 2] = r2;
   kc[i] = k;
 }
 
@@ -341,28 +347,24 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   const bool active = compute && slot < a.n;
   const int64_t s = active ? (a.order ? (int64_t)a.order[slot] : slot) : 0;
 
-  // ---- per-sample set-up by the first thread of each sample
-  double x = 0.0, q = 1.0;
-  if (active) {
-    x = a.pts[s];
-    q = a.pts[a.n + s];
-  }
-  const bool valid = active && in_space(a.sp, x, q);
+  // ---- the sample's set-up record (written by setup_kernel), read by part 0
   if (compute && part == 0) {
-    int32_t kc = 0;
-    float inv = 0.f;
-    if (valid) {
-      const FastSetup fs = fast_setup(a.sp, a.g, x, q);
-#pragma unroll
-      for (int j = 0; j < kNumBasis - 1; ++j) s_cf[j][row] = fs.cf[j];
-      kc = fs.kcut;
-      inv = fs.inv_s;
-    } else {
-#pragma unroll
-      for (int j = 0; j < kNumBasis - 1; ++j) s_cf[j][row] = 0.f;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    if (active) {
+      r0 = a.rec[3 * s];
+      r1 = a.rec[3 * s + 1];
+      r2 = a.rec[3 * s + 2];
     }
-    s_kcut[row] = kc;
-    s_inv[row] = inv;
+    s_cf[0][row] = r0.x;
+    s_cf[1][row] = r0.y;
+    s_cf[2][row] = r0.z;
+    s_cf[3][row] = r0.w;
+    s_cf[4][row] = r1.x;
+    s_cf[5][row] = r1.y;
+    s_cf[6][row] = r1.z;
+    s_cf[7][row] = r1.w;
+    s_inv[row] = r2.x;
+    s_kcut[row] = __float_as_int(r2.y);
   }
   if (tid == 0) {
     s_kmax = 0;
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = s_cf[j][row];
   const int32_t kcut = compute ? s_kcut[row] : 0;
   const float inv_s = compute ? s_inv[row] : 0.f;
+  const bool valid = active && kcut > 0;
   if (compute && part == 0) atomicMax(&s_kmax, kcut);
   __syncthreads();
   const uint32_t tmem = s_tmem;
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
   unsigned char* sA = sm + kAOffA;
   unsigned char* sB = sm + kAOffB;
   bool bad = false;
-  float best2 = -1.f;   // this thread's best |overlap|^2 and template (compute threads)
+  float best2 = -1.f;   // this thread's best |overlap|^2 and its slot p * 256 + i (compute threads)
   int32_t best_t = -1;
 
   if (!compute) {
@@ -467,23 +470,30 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
     // ---- compute warps
     // TMEM columns [128 part, 128 part + 128): pass slots 64 part .. 64 part + 63
     const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(part * 128);
-    // this thread's 64 overlaps of pass p against the running best; a tie goes to the lowest
-    // template index
+    // this thread's 64 overlaps of pass p against the running best, 16 at a time: the
+    // chunk's maximum first, the slot only when it beats the best (the first slot visited
+    // wins a tie)
     auto drain = [&](int p) {
-      const int32_t* perm = a.perm + (int64_t)p * 2 * kTileTemplates + part * 64;
 #pragma unroll 1
       for (int c0 = 0; c0 < 128; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld32(tbase + c0, r);
+        float m2[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
-          const float m2 = fmaf(re, re, im * im);
-          const int32_t t = __ldg(perm + (c0 >> 1) + i);
-          if (t >= 0 && (m2 > best2 || (m2 == best2 && t < best_t))) {
-            best2 = m2;
-            best_t = t;
-          }
+          m2[i] = fmaf(re, re, im * im);
+        }
+        float cmax = m2[0];
+#pragma unroll
+        for (int i = 1; i < 16; ++i) cmax = fmaxf(cmax, m2[i]);
+        if (cmax > best2) {
+          int bi = 15;
+#pragma unroll
+          for (int i = 15; i >= 0; --i)
+            if (m2[i] == cmax) bi = i;
+          best2 = cmax;
+          best_t = p * 2 * kTileTemplates + part * 64 + (c0 >> 1) + bi;
         }
       }
     };
@@ -503,42 +513,39 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
           }
         }
         unsigned char* rowA = rowA0 + b * kATile;
-        // this thread's 8 bins of the block: 2 chunks of 16 bytes, 4 bins (8 FP16) each
+        // this thread's 8 bins of the block: 2 chunks of 16 bytes, 4 bins (8 FP16) each, the
+        // values (Re a_k, Im a_k) of a_k = amp e^(-i 2 pi t_k)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int c = 2 * part + j;
+          const int32_t k0 = kb * kTileBins + 4 * c;
           uint32_t wv[4];
 #pragma unroll
           for (int pr = 0; pr < 2; ++pr) {
-            const int32_t k = kb * kTileBins + 4 * c + 2 * pr;
-            float2 re = f2(0.f), im = f2(0.f);
-            if (k < kcut) {
-              const float4* rc = recs + (int64_t)(k >> 1) * (kBinRecord / 4);
-              const float4 r0 = __ldg(rc), r1 = __ldg(rc + 1), r2 = __ldg(rc + 2), r3 = __ldg(rc + 3),
-                           r4 = __ldg(rc + 4);
-              float2 t = __fmul2_rn(f2(cf[0]), make_float2(r0.x, r0.y));
-              t = __ffma2_rn(f2(cf[1]), make_float2(r0.z, r0.w), t);
-              t = __ffma2_rn(f2(cf[2]), make_float2(r1.x, r1.y), t);
-              t = __ffma2_rn(f2(cf[3]), make_float2(r1.z, r1.w), t);
-              t = __ffma2_rn(f2(cf[4]), make_float2(r2.x, r2.y), t);
-              t = __ffma2_rn(f2(cf[5]), make_float2(r2.z, r2.w), t);
-              t = __ffma2_rn(f2(cf[6]), make_float2(r3.x, r3.y), t);
-              t = __ffma2_rn(f2(cf[7]), make_float2(r3.z, r3.w), t);
-              t.x -= rintf(t.x);  // turns in [-1/2, 1/2]: the MUFU argument stays in [-pi, pi]
-              t.y -= rintf(t.y);
-              const float2 ang = __fmul2_rn(t, f2(kTwoPiF));
-              float2 sn, cs;
-              __sincosf(ang.x, &sn.x, &cs.x);
-              __sincosf(ang.y, &sn.y, &cs.y);
-              const float2 amp = __fmul2_rn(make_float2(r4.x, r4.y), f2(inv_s));
-              re = __fmul2_rn(amp, cs);   // u = amp e^(-i 2 pi t)
-              im = __fmul2_rn(amp, sn);
-              if (k + 1 >= kcut) {
-                re.y = 0.f;
-                im.y = 0.f;
-              }
+            const int32_t k = k0 + 2 * pr;
+            const float4* rc = recs + (int64_t)(k >> 1) * (kBinRecord / 4);
+            const float4 r0 = __ldg(rc), r1 = __ldg(rc + 1), r2 = __ldg(rc + 2), r3 = __ldg(rc + 3), r4 = __ldg(rc + 4);
+            float2 t = __fmul2_rn(f2(cf[0]), make_float2(r0.x, r0.y));
+            t = __ffma2_rn(f2(cf[1]), make_float2(r0.z, r0.w), t);
+            t = __ffma2_rn(f2(cf[2]), make_float2(r1.x, r1.y), t);
+            t = __ffma2_rn(f2(cf[3]), make_float2(r1.z, r1.w), t);
+            t = __ffma2_rn(f2(cf[4]), make_float2(r2.x, r2.y), t);
+            t = __ffma2_rn(f2(cf[5]), make_float2(r2.z, r2.w), t);
+            t = __ffma2_rn(f2(cf[6]), make_float2(r3.x, r3.y), t);
+            t = __ffma2_rn(f2(cf[7]), make_float2(r3.z, r3.w), t);
+            t.x -= rintf(t.x);  // turns in [-1/2, 1/2]: the MUFU argument stays in [-pi, pi]
+            t.y -= rintf(t.y);
+            const float2 ang = __fmul2_rn(t, f2(-kTwoPiF));
+            float2 sn, cs;
+            __sincosf(ang.x, &sn.x, &cs.x);
+            __sincosf(ang.y, &sn.y, &cs.y);
+            float2 amp = __fmul2_rn(make_float2(r4.x, r4.y), f2(inv_s));
+            if (k0 + 3 >= kcut) {  // the sample's ISCO cut falls in this chunk
+              amp.x = k < kcut ? amp.x : 0.f;
+              amp.y = k + 1 < kcut ? amp.y : 0.f;
             }
-            const __half2 h0 = __floats2half2_rn(re.x, -im.x), h1 = __floats2half2_rn(re.y, -im.y);
+            const float2 re = __fmul2_rn(amp, cs), im = __fmul2_rn(amp, sn);
+            const __half2 h0 = __floats2half2_rn(re.x, im.x), h1 = __floats2half2_rn(re.y, im.y);
             wv[2 * pr] = *reinterpret_cast<const uint32_t*>(&h0);
             wv[2 * pr + 1] = *reinterpret_cast<const uint32_t*>(&h1);
           }
@@ -593,8 +600,9 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
       }
     }
     if (active) {
-      const bool ok = valid && kcut > 0 && !s_bad && best_t >= 0;
-      a.tile[s] = ok ? best_t : -1;
+      const int32_t t = best_t >= 0 ? a.perm[best_t] : -1;
+      const bool ok = valid && !s_bad && t >= 0;
+      a.tile[s] = ok ? t : -1;
       if (a.match) a.match[s] = ok ? sqrtf(fmaxf(best2, 0.f)) : 0.f;
     }
   }
@@ -790,10 +798,10 @@ cudaError_t launch_tiling_template_tiles(const int32_t* perm, int32_t n_pass, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_tiling_kcut(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, int32_t* kc,
-                               cudaStream_t s) {
+cudaError_t launch_tiling_setup(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, float4* rec,
+                                int32_t* kc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  kcut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, g, n, pts, kc);
+  setup_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, g, n, pts, rec, kc);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ struct mbis_tiling {
   std::vector<int32_t> nkb_pass;
   // scratch of the assignment's sample ordering (grown on demand)
   int64_t scr_n = 0;
+  float4* d_rec = nullptr;
   int32_t *d_kc = nullptr, *d_order = nullptr, *d_shist = nullptr, *d_scount = nullptr, *d_soffset = nullptr,
           *d_snbad = nullptr;
   // pool
@@ -127,6 +128,7 @@ void drop_bank(mbis_tiling* t) {
 
 void drop_scratch(mbis_tiling* t) {
   tfree(t->d_kc);
+  tfree(t->d_rec);
   tfree(t->d_order);
   tfree(t->d_shist);
   tfree(t->d_scount);
@@ -442,6 +444,7 @@ mbis_status mbis_tiling_assign(mbis_tiling* t, int64_t n, const double* pts, int
     drop_scratch(t);
     const int64_t n_seg = (n + mbis::kSortSegment - 1) / mbis::kSortSegment;
     if (cudaMalloc(&t->d_kc, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&t->d_rec, sizeof(float4) * 3 * n) != cudaSuccess ||
         cudaMalloc(&t->d_order, sizeof(int32_t) * n) != cudaSuccess ||
         cudaMalloc(&t->d_shist, sizeof(int32_t) * (size_t)n_seg * (t->K + 1)) != cudaSuccess ||
         cudaMalloc(&t->d_scount, sizeof(int32_t) * (t->K + 1)) != cudaSuccess ||
@@ -452,14 +455,14 @@ mbis_status mbis_tiling_assign(mbis_tiling* t, int64_t n, const double* pts, int
     }
     t->scr_n = n;
   }
-  T_TRY(t, mbis::launch_tiling_kcut(t->sp, t->grid(), n, pts, t->d_kc, s));
+  T_TRY(t, mbis::launch_tiling_setup(t->sp, t->grid(), n, pts, t->d_rec, t->d_kc, s));
   T_TRY(t, mbis::launch_tiling_lists(n, t->d_kc, t->K + 1, t->d_shist, t->d_scount, t->d_soffset, t->d_snbad,
                                      t->d_order, s));
   mbis::AssignArgs a;
   a.sp = t->sp;
   a.g = t->grid();
   a.n = n;
-  a.pts = pts;
+  a.rec = t->d_rec;
   a.order = t->d_order;
   a.tile = tile;
   a.match = match;

@@ -52,16 +52,16 @@ cudaError_t launch_tiling_bin_records(const TilingGrid& g, double wscale, float*
 // in the order perm ([n_pass * 256], -1 pads)
 cudaError_t launch_tiling_template_tiles(const int32_t* perm, int32_t n_pass, const double2* rows, const TilingGrid& g,
                                          void* out, cudaStream_t s);
-// approximate live-bin count of each point (0 outside the space): the sort key of the
-// assignment's sample order
-cudaError_t launch_tiling_kcut(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, int32_t* kc,
-                               cudaStream_t s);
+// set-up record of each point ([n][3] float4: FP32 phase coefficients, inverse norm,
+// live-bin count; zero outside the space) and its live-bin count (the sort key)
+cudaError_t launch_tiling_setup(const TilingSpace& sp, const TilingGrid& g, int64_t n, const double* pts, float4* rec,
+                                int32_t* kc, cudaStream_t s);
 
 struct AssignArgs {
   TilingSpace sp;
   TilingGrid g;
   int64_t n;
-  const double* pts;     // [2][n]
+  const float4* rec;     // [n][3] set-up records
   const int32_t* order;  // [n] processing order of the points (null: as given)
   int32_t* tile;         // [n]
   float* match;          // [n] or null
