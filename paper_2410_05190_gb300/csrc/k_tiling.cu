@@ -227,7 +227,9 @@ constexpr uint32_t kBHalf = kTileBytes;          // 256 rows (128 templates) x 1
 constexpr uint32_t kBBlock = 2 * kBHalf;         // one K-block of a pass
 constexpr uint32_t kAOffA = 0;                   // [2 buf][kATile]
 constexpr uint32_t kAOffB = kAOffA + 2 * kATile; // [2 buf][kBBlock]
-constexpr uint32_t kASmem = kAOffB + 2 * kBBlock + 1024;
+constexpr uint32_t kAOffR = kAOffB + 2 * kBBlock;  // basis records of the CTA's bins
+constexpr uint32_t kRecSmem = 24576;             // up to 19 K-blocks (608 bins) of records
+constexpr uint32_t kASmem = kAOffR + kRecSmem + 1024;
 constexpr uint32_t kAIdesc = tc::idesc_f16(128, 2 * kTileTemplates);
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
@@ -399,6 +401,15 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
     for (int p = 0; p < a.n_pass; ++p) nb += pass_blocks(p);
     s_nblk = nb;
   }
+  // the basis records of the bins this CTA reaches, read by every compute thread in every
+  // pass: staged once in shared memory when they fit (else read through L1)
+  const int32_t n_rec4 = nkb_cta * (kTileBins / 2) * (kBinRecord / 4);
+  const bool rec_smem = n_rec4 * 16 <= (int32_t)kRecSmem;
+  float4* s_rec = reinterpret_cast<float4*>(sm + kAOffR);
+  if (rec_smem) {
+    const float4* src = reinterpret_cast<const float4*>(a.bins);
+    for (int i = tid; i < n_rec4; i += kAThreads) s_rec[i] = __ldg(src + i);
+  }
   __syncthreads();
   const int32_t nblk = s_nblk;
 
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
         }
       }
     };
-    const float4* recs = reinterpret_cast<const float4*>(a.bins);
+    const float4* recs = rec_smem ? s_rec : reinterpret_cast<const float4*>(a.bins);
     unsigned char* rowA0 = sA + row * 128;
     int g = 0, last_p = -1;
     for (int p = 0; p < a.n_pass && !bad; ++p) {
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(kAThreads, 1) assign_kernel(AssignArgs a) {
           for (int pr = 0; pr < 2; ++pr) {
             const int32_t k = k0 + 2 * pr;
             const float4* rc = recs + (int64_t)(k >> 1) * (kBinRecord / 4);
-            const float4 r0 = __ldg(rc), r1 = __ldg(rc + 1), r2 = __ldg(rc + 2), r3 = __ldg(rc + 3), r4 = __ldg(rc + 4);
+            const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3], r4 = rc[4];
             float2 t = __fmul2_rn(f2(cf[0]), make_float2(r0.x, r0.y));
             t = __ffma2_rn(f2(cf[1]), make_float2(r0.z, r0.w), t);
             t = __ffma2_rn(f2(cf[2]), make_float2(r1.x, r1.y), t);

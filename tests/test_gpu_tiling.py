@@ -127,6 +127,31 @@ def test_tensor_core_assignment_against_the_oracle(m, torch, demo, otl, gtl, ban
     print(f"assignment: max |match error| {err:.2e}, {100 * amb:.1f}% of points within 2e-4 of a tie")
 
 
+def test_assignment_over_long_bands_rewrites_the_sample_tiles(m, torch):
+    """A finer grid (df = 1/16 Hz, up to 960 live bins: 30 K-blocks per sample, records read
+    through L1 instead of shared memory) against the oracle."""
+    f_lo, df = 20.0, 1.0 / 16
+    nb = workloads.n_bins_for(f_lo, 128.0, df)
+    psd = oracle.psd_aligo(f_lo + df * np.arange(nb))
+    otl = oracle.Tiling(f_lo, df, nb, psd, 24.0, 26.0, 0.0, 0.0, 1.0, 3.0)
+    t = m.mbis_tiling_create(f_lo, df, nb, psd, 24.0, 26.0, 0.0, 0.0, 1.0, 3.0)
+    try:
+        cand = workloads.uniform_points(6000, 24.0, 26.0, 1.0, 3.0, seed=31)
+        idx_o, used_o, margin = otl.bank(cand, 0.995, 400, 4096)
+        T, used = m.mbis_tiling_bank(t, cand, 0.995, 400, 4096)
+        assert margin > 1e-10 and T == len(idx_o) and used == used_o
+        pts = workloads.uniform_points(1500 + 11, 24.0, 26.0, 1.0, 3.0, seed=32)
+        n = pts.shape[1]
+        tile = torch.empty(n, dtype=torch.int32, device="cuda")
+        match = torch.empty(n, dtype=torch.float32, device="cuda")
+        m.mbis_tiling_assign(t, n, dev(torch, pts), tile, match)
+        torch.cuda.synchronize()
+        err, amb = check_assignment(otl, cand[:, idx_o], pts, tile.cpu().numpy(), match.cpu().numpy())
+        print(f"long band ({nb} bins, {T} templates): max |match error| {err:.2e}")
+    finally:
+        m.mbis_tiling_destroy(t)
+
+
 def test_assignment_edge_cases(m, torch, demo, gtl, banks):
     # points outside the space get no tile; an empty call is a no-op
     pts = np.array([[demo.x_hi + 1.0, demo.x_lo, 21.0], [1.0, demo.q_hi * 2, 3.5]])
