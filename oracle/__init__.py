@@ -109,6 +109,7 @@ def lib():
             "or_tiling_lists": (None, [i64, p, i32, p, p, p]),
             "or_tiling_mixture": (d, [i32, p, p, p]),
             "or_tiling_draw": (None, [u64, u64, i64, i32, p, d, p, p, p, p, i64, p, p, p]),
+            "or_credible_levels": (None, [i64, i32, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -439,3 +440,13 @@ def tiling_draw(seed, ctr0, n, c, m, loglike_tpl, count, offset, members, n_pool
     lib().or_tiling_draw(seed, ctr0, n, len(c), _ptr(c), m, _ptr(ll), _ptr(count), _ptr(offset), _ptr(members),
                          n_pool, _ptr(idx), _ptr(tile), _ptr(lr))
     return idx, tile, lr
+
+
+def credible_levels(theta, weights, ref):
+    """Weighted fraction of the samples [P][n] below ref [P] per slot (ties count half)."""
+    th, w, r = _f64(theta), _f64(weights), _f64(ref)
+    P = len(r)
+    n = th.reshape(P, -1).shape[1]
+    out = np.zeros(P)
+    lib().or_credible_levels(n, P, _ptr(th), _ptr(w), _ptr(r), _ptr(out))
+    return out

@@ -38,6 +38,8 @@
  *                                images of one binary share a tile
  *   mixture / draws ............ E_g[w] = mean prior likelihood exactly; equal weights
  *                                (ESS = n) when L is constant per tile; frequencies
+ *   credible levels ............ order statistics of equal weights; mirror symmetry; the
+ *                                Gaussian posterior of a linear model (normal CDF)
  * Parity unpinned: the physical values of the 2.5PN, 3PN and 3.5PN aligned-spin
  * coefficients (only their test-mass limit and label symmetry are pinned).
  */
@@ -927,5 +929,30 @@ void or_tiling_draw(uint64_t seed, uint64_t ctr0, int64_t n, int32_t T, const do
     pool_idx[i] = members[offset[j] + (int64_t)k];
     tile_out[i] = j;
     log_ratio[i] = loglike_tpl[j] - m - log(total) + log((double)n_pool);
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Credible level of a reference point (the P-P self-consistency test of Sec. III A): for
+ * every sampled slot p, the weighted fraction of the posterior below the reference,
+ *   level_p = [sum_i w_i 1(theta_pi < ref_p) + 1/2 sum_i w_i 1(theta_pi = ref_p)] / sum_i w_i,
+ * with the importance weights w_i (Eq. 5; any positive scale).  Over sources drawn from the
+ * prior and analysed with the same prior, the level of the true value is uniform on [0, 1].
+ * theta is SoA [P][n]; sums in long double. */
+void or_credible_levels(int64_t n, int32_t P, const double* theta, const double* w, const double* ref, double* out) {
+  long double tot = 0.0L;
+  for (int64_t i = 0; i < n; ++i)
+    if (w[i] > 0.0) tot += w[i];
+  for (int32_t p = 0; p < P; ++p) {
+    long double below = 0.0L;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!(w[i] > 0.0)) continue;
+      const double x = theta[(int64_t)p * n + i];
+      if (x < ref[p])
+        below += w[i];
+      else if (x == ref[p])
+        below += 0.5L * w[i];
+    }
+    out[p] = tot > 0.0L ? (double)(below / tot) : NAN;
   }
 }
