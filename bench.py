@@ -542,6 +542,95 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
             "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
 
 
+def pp_measurement(m, torch, n_tiled=256, n_bns=64):
+    """P-P self-consistency (Sec. III A): credible levels of the true parameters over
+    simulated populations, KS p-value per parameter and Fisher's combination.
+    (1) the tiled demonstration: sources drawn from the (x, q) prior, tiled proposal;
+    (2) the BNS population: the Fisher Gaussian refitted by the ESS loop, then one batch."""
+    from paper_2410_05190_gb300 import pp
+    out = {}
+    # (1) tiled
+    d = workloads.tiled_demo()
+    w = d.workload
+    spec = w.events[0]
+    dn = workloads.network(w.detectors)
+    dets = m.make_detectors(*dn)
+    psd1 = m.mbis_psd_aligo(w.f_lo, w.df, w.n_bins)
+    psd = np.tile(psd1, (w.n_det, 1))
+    t = m.mbis_tiling_create(w.f_lo, w.df, w.n_bins, psd1, d.x_lo, d.x_hi, d.mc_period, d.mc_base, d.q_lo, d.q_hi)
+    try:
+        cand = workloads.uniform_points(d.n_candidates, d.x_lo, d.x_hi, d.q_lo, d.q_hi, d.candidate_seed)
+        T, _ = m.mbis_tiling_bank(t, cand, d.min_match, d.stop_after, d.max_templates)
+        _, phys, _ = m.mbis_tiling_templates(t)
+        pool = workloads.uniform_points(d.n_pool, d.x_lo, d.x_hi, d.q_lo, d.q_hi, d.pool_seed)
+        m.mbis_tiling_set_pool(t, d.n_pool, torch.tensor(pool, device="cuda"))
+        an = pp.TiledAnalysis(m, torch, t, phys, (d.mc_base, d.mc_base + d.mc_period),
+                              (1.0, max(d.q_hi, 1.0 / d.q_lo)), 1 << 16)
+        th0 = np.zeros(11)
+        mc0 = (spec.m1 * spec.m2) ** 0.6 / (spec.m1 + spec.m2) ** 0.2
+        th0[MC], th0[Q] = mc0, spec.m1 / spec.m2
+        for k, v in spec.params.items():
+            th0[workloads.PARAM_NAMES.index(k)] = v
+        th0[DL] = 1.0
+        _, snr2 = m.mbis_inject(w.f_lo, w.df, w.n_bins, dets, psd, spec.gmst, th0)
+        dl = math.sqrt(snr2) / spec.snr
+        pop = workloads.tiled_population(d, n_tiled)
+        lv, eff = [], []
+        t0 = time.perf_counter()
+        for src in pop:
+            th = th0.copy()
+            th[MC] = d.mc_base + math.fmod(src["x"], d.mc_period)
+            th[Q] = max(src["q"], 1.0 / src["q"])
+            th[PHIC] = src["phic"]
+            th[DL] = dl
+            strain, _ = m.mbis_inject(w.f_lo, w.df, w.n_bins, dets, psd, spec.gmst, th, src["noise_seed"], True)
+            levels, summ = an.run(strain.astype(np.complex64), psd, dets, w.f_lo, w.df, th, spec.gmst,
+                                  [src["x"], src["q"]], src["draw_seed"])
+            lv.append(levels)
+            eff.append(summ["ess"] / an.n)
+        secs = time.perf_counter() - t0
+        lv = np.array(lv)
+        pv = {"x": pp.ks_pvalue(lv[:, 0]), "q": pp.ks_pvalue(lv[:, 1])}
+        out["tiled_demo"] = {"sources": n_tiled, "samples_per_source": an.n, "ks_pvalue": pv,
+                             "combined_pvalue": pp.combined_pvalue(list(pv.values())),
+                             "median_efficiency": float(np.median(eff)), "seconds": secs,
+                             "sources_per_s": n_tiled / secs}
+    finally:
+        m.mbis_tiling_destroy(t)
+    # (2) BNS with the refitted Gaussian
+    wb = workloads.bns_population(n_events=n_bns)
+    dn = workloads.network(wb.detectors)
+    lv, effs = [], []
+    names = [workloads.PARAM_NAMES[i] for i in wb.sampled]
+    n_final = 1 << 18
+    t0 = time.perf_counter()
+    for spec in wb.events:
+        ev = event_setup(m, wb, spec, dn)
+        ctx = make_ctx(m, wb, ev, m.MIXED)
+        try:
+            P = len(ev["prop"]["ids"])
+            bufs = ess_buffers(torch, P, 1 << 16)
+            m.mbis_run_to_ess(ctx, *bufs, ess_target=2000.0, batch=1 << 16, max_samples=1 << 20,
+                              seed=spec.draw_seed, refine=4, refine_scale=1.2)
+            th_s = torch.empty((P, n_final), dtype=torch.float64, device="cuda")
+            lq, lp, ll, wt = (torch.empty(n_final, dtype=torch.float64, device="cuda") for _ in range(4))
+            m.mbis_draw(ctx, spec.draw_seed ^ 0x5EED, 0, n_final, th_s, lq, lp)
+            m.mbis_loglike(ctx, n_final, th_s, ll)
+            summ = m.mbis_reduce(ctx, n_final, ll, lp, lq, wt)
+            lv.append(pp.levels(m, torch, n_final, th_s, wt, [ev["th"][i] for i in wb.sampled]))
+            effs.append(summ["ess"] / n_final)
+        finally:
+            m.mbis_destroy(ctx)
+    secs = time.perf_counter() - t0
+    lv = np.array(lv)
+    pv = {nm: pp.ks_pvalue(lv[:, k]) for k, nm in enumerate(names)}
+    out["bns_population"] = {"events": n_bns, "samples_per_event": n_final, "ks_pvalue": pv,
+                             "combined_pvalue": pp.combined_pvalue(list(pv.values())),
+                             "median_efficiency": float(np.median(effs)), "seconds": secs,
+                             "proposal": "Fisher Gaussian refitted 4 times by the ESS loop"}
+    return out
+
+
 SERVE_SEED = 0x5E12E
 
 
@@ -647,8 +736,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled",
-                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled) or 'none'")
+    ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled,pp",
+                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled, pp) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-compare", type=int, default=0,
                     help="also process the stream's first K requests serially in FP64 (slow)")
@@ -691,6 +780,8 @@ def main():
             out["uneven_batch"] = batch_measurement(m, torch)
         if "tiled" in extras:
             out["tiled_proposal"] = tiled_measurement(m, torch)
+        if "pp" in extras:
+            out["pp_self_consistency"] = pp_measurement(m, torch)
         if "serve" in extras:
             served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
             if args.serve_compare > 0:

@@ -427,6 +427,18 @@ mbis_status mbis_tiling_draw(mbis_tiling* t, uint64_t seed, uint64_t ctr0, int64
 void mbis_tiling_destroy(mbis_tiling* t);
 const char* mbis_tiling_last_error(const mbis_tiling* t);
 
+/* ---- P-P self-consistency (Sec. III A) --------------------------------------------- */
+
+/* Credible level of a reference point under weighted samples: for each slot p < P,
+ *   level[p] = (sum_i w_i [theta[p][i] < ref[p]] + 1/2 sum_i w_i [theta[p][i] == ref[p]]) / sum_i w_i
+ * over the positive weights.  The paper validates its posteriors by the distribution of
+ * this level of the true parameters over a simulated population (uniform when the method
+ * is self-consistent).  theta (device, [P][n]), weights (device, n; any positive scale,
+ * e.g. the normalised weights of mbis_reduce), ref (host, P), levels (device, P; NaN when
+ * no weight is positive).  n >= 1, 1 <= P <= 16.  Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_credible_levels(int64_t n, int32_t P, const double* theta, const double* weights, const double* ref,
+                                 double* levels, void* cuda_stream);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

@@ -130,6 +130,7 @@ def _load():
         "mbis_server_poll": [p, p, i32, p],
         "mbis_server_stats_get": [p, p],
         "mbis_debug_wait_timeout": [u64, p, p],
+        "mbis_credible_levels": [i64, i32, p, p, p, p, p],
         "mbis_tiling_create": [p, p, p, p],
         "mbis_tiling_bank": [p, i64, p, d, i64, i32, p, p],
         "mbis_tiling_templates": [p, p, p, p, p],
@@ -536,3 +537,11 @@ def mbis_tiling_set_loglike(t, loglike_tpl, stream=None):
 def mbis_tiling_draw(t, seed, ctr0, n, theta, log_q, log_prior, coords=None, pool_index=None, stream=None):
     _tcheck(_lib.mbis_tiling_draw(t, seed, ctr0, n, _dev(coords), _dev(theta), _dev(log_q), _dev(log_prior),
                                   _dev(pool_index), _stream(stream)), t)
+
+
+# ------------------------------------------------------------------------------- P-P test
+def mbis_credible_levels(n, theta, weights, ref, levels, stream=None):
+    """Weighted fraction below ref [P] (host) of the samples theta [P][n] (device), into
+    levels [P] (device)."""
+    r, pr = _host(ref, np.float64)
+    _check(_lib.mbis_credible_levels(n, len(r), _dev(theta), _dev(weights), pr, _dev(levels), _stream(stream)))

@@ -258,6 +258,18 @@ def uniform_points(n, x_lo, x_hi, q_lo, q_hi, seed):
     return out
 
 
+def tiled_population(demo: "TiledDemo", n_events, seed=POPULATION_SEED + 6):
+    """Sources of the tiled demonstration space drawn from its prior (uniform in x and q),
+    phase uniform in [0, 2 pi), a common luminosity distance (the one giving network SNR
+    15 to the demonstration source), noise and draw seeds: the P-P population."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.uniform(demo.x_lo, demo.x_hi, n_events)
+    q = rng.uniform(demo.q_lo, demo.q_hi, n_events)
+    phic = rng.uniform(0.0, 2 * math.pi, n_events)
+    return [dict(x=float(x[e]), q=float(q[e]), phic=float(phic[e]), noise_seed=(seed << 8) + 2 * e + 1,
+                 draw_seed=(seed << 8) + 2 * e + 2) for e in range(n_events)]
+
+
 def scaled(w: Workload, n_events=None, n_samples=None, f_hi=None):
     """A copy of a workload with fewer events, fewer samples or a shorter band (for the
     oracle-sized parity cases)."""
