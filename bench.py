@@ -542,11 +542,12 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
             "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
 
 
-def pp_measurement(m, torch, n_tiled=256, n_bns=64):
+def pp_measurement(m, torch, n_tiled=256, n_bns=128):
     """P-P self-consistency (Sec. III A): credible levels of the true parameters over
     simulated populations, KS p-value per parameter and Fisher's combination.
     (1) the tiled demonstration: sources drawn from the (x, q) prior, tiled proposal;
-    (2) the BNS population: the Fisher Gaussian refitted by the ESS loop, then one batch."""
+    (2) BNS sources drawn from the analysis prior (workloads.bns_pp_population): the Fisher
+    Gaussian refitted by the ESS loop, then one batch."""
     from paper_2410_05190_gb300 import pp
     out = {}
     # (1) tiled
@@ -597,8 +598,8 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=64):
                              "sources_per_s": n_tiled / secs}
     finally:
         m.mbis_tiling_destroy(t)
-    # (2) BNS with the refitted Gaussian
-    wb = workloads.bns_population(n_events=n_bns)
+    # (2) BNS drawn from the analysis prior, the refitted Gaussian proposal
+    wb = workloads.bns_pp_population(n_events=n_bns)
     dn = workloads.network(wb.detectors)
     lv, effs = [], []
     names = [workloads.PARAM_NAMES[i] for i in wb.sampled]
@@ -606,6 +607,9 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=64):
     t0 = time.perf_counter()
     for spec in wb.events:
         ev = event_setup(m, wb, spec, dn)
+        for k, slot in enumerate(wb.sampled):   # the population's prior, not a box about the truth
+            if slot in workloads.PP_BOX:
+                ev["prop"]["lo"][k], ev["prop"]["hi"][k] = workloads.PP_BOX[slot]
         ctx = make_ctx(m, wb, ev, m.MIXED)
         try:
             P = len(ev["prop"]["ids"])

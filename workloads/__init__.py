@@ -270,6 +270,37 @@ def tiled_population(demo: "TiledDemo", n_events, seed=POPULATION_SEED + 6):
                  draw_seed=(seed << 8) + 2 * e + 2) for e in range(n_events)]
 
 
+PP_BOX = {MC: (1.1, 1.5), Q: (1.0, 1.6), TC: (-5e-4, 5e-4)}
+
+
+def bns_pp_population(n_events=64, seed=POPULATION_SEED + 7):
+    """BNS sources drawn from the fixed prior that their analysis uses, for the P-P test:
+    flat in (m1, m2) inside Mc in [1.1, 1.5], q = m1/m2 in [1, 1.6] (by rejection from
+    m ~ U[1.0, 2.0] sorted), chi ~ U[-0.05, 0.05], t_c ~ U[-0.5, 0.5] ms, isotropic sky and
+    orientation, SNR ~ U[10, 30], coloured noise; H1+L1, 20-1024 Hz at 1/128 Hz; sampled
+    (Mc, q, chi1, chi2, t_c); phase and distance marginalised.  The analysis box is PP_BOX."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    events = []
+    for e in range(n_events):
+        while True:
+            m = np.sort(rng.uniform(1.0, 2.0, size=2))[::-1]
+            mc = (m[0] * m[1]) ** 0.6 / (m[0] + m[1]) ** 0.2
+            if PP_BOX[MC][0] <= mc <= PP_BOX[MC][1] and m[0] / m[1] <= PP_BOX[Q][1]:
+                break
+        chi = rng.uniform(-0.05, 0.05, size=2)
+        ra, dec, psi, iota = _isotropic(rng)
+        gmst = rng.uniform(0.0, 2 * math.pi)
+        phic = rng.uniform(0.0, 2 * math.pi)
+        tc = rng.uniform(*PP_BOX[TC])
+        snr = rng.uniform(10.0, 30.0)
+        events.append(EventSpec(float(m[0]), float(m[1]),
+                                dict(chi1=float(chi[0]), chi2=float(chi[1]), ra=ra, dec=dec, psi=psi, iota=iota,
+                                     tc=tc, phic=phic),
+                                gmst, snr, noise_seed=(seed << 8) + 2 * e + 1, draw_seed=(seed << 8) + 2 * e + 2))
+    return Workload("bns_pp_population", ["H1", "L1"], 20.0, 1024.0, 1.0 / 128, [MC, Q, CHI1, CHI2, TC],
+                    MARG_PHASE | MARG_DISTANCE, 1 << 18, "mixed", "c64", 1.5, PRIOR_M1M2, 0.05, events)
+
+
 def scaled(w: Workload, n_events=None, n_samples=None, f_hi=None):
     """A copy of a workload with fewer events, fewer samples or a shorter band (for the
     oracle-sized parity cases)."""
