@@ -110,6 +110,8 @@ def lib():
             "or_tiling_mixture": (d, [i32, p, p, p]),
             "or_tiling_draw": (None, [u64, u64, i64, i32, p, d, p, p, p, p, i64, p, p, p]),
             "or_credible_levels": (None, [i64, i32, p, p, p, p]),
+            "or_rb_loglike": (d, [p, p, i32, p, p]),
+            "or_rb_loglike_batch": (None, [p, p, i32, p, i64, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -449,4 +451,15 @@ def credible_levels(theta, weights, ref):
     n = th.reshape(P, -1).shape[1]
     out = np.zeros(P)
     lib().or_credible_levels(n, P, _ptr(th), _ptr(w), _ptr(r), _ptr(out))
+    return out
+
+
+def rb_loglike_batch(ev: OracleEvent, par0, edges, pars):
+    """Relative-binning log-likelihood ratios of n x 11 parameter rows about the fiducial
+    par0 with bin edges (bin indices, edges[0] = 0, edges[-1] = n_bins)."""
+    pars = _f64(pars).reshape(-1, NPAR)
+    p0 = _f64(par0)
+    e = np.ascontiguousarray(edges, dtype=np.int32)
+    out = np.zeros(len(pars))
+    lib().or_rb_loglike_batch(C.byref(ev.s), _ptr(p0), len(e) - 1, _ptr(e), len(pars), _ptr(pars), _ptr(out))
     return out
