@@ -542,7 +542,7 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
             "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
 
 
-def pp_measurement(m, torch, n_tiled=256, n_bns=128):
+def pp_measurement(m, torch, n_tiled=256, n_bns=256):
     """P-P self-consistency (Sec. III A): credible levels of the true parameters over
     simulated populations, KS p-value per parameter and Fisher's combination.
     (1) the tiled demonstration: sources drawn from the (x, q) prior, tiled proposal;
@@ -633,6 +633,54 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=128):
                              "median_efficiency": float(np.median(effs)), "seconds": secs,
                              "proposal": "Fisher Gaussian refitted 4 times by the ESS loop"}
     return out
+
+
+def rb_measurement(m, torch, evs, n=1 << 20, n_sigma=5.0, eps=0.3, reps=3):
+    """Relative binning on the BNS benchmark event: bins from mbis_rb_edges, likelihood rate
+    (CUDA events) against the exact fused kernel on the same draws, and its error: per
+    sample against the exact log L, and in ESS and log Z."""
+    ev = evs[0]
+    w = ev["w"]
+    ctx = make_ctx(m, w, ev, m.MIXED)
+    try:
+        edges = m.mbis_rb_edges(ctx, ev["th"], n_sigma, eps)
+        m.mbis_rb_setup(ctx, ev["th"], edges)
+        P = len(ev["prop"]["ids"])
+        theta = torch.empty((P, n), dtype=torch.float64, device="cuda")
+        lq, lp, ll, lr = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4))
+        stream = torch.cuda.current_stream()
+        m.mbis_draw(ctx, ev["spec"].draw_seed, 0, n, theta, lq, lp, stream)
+        m.mbis_loglike(ctx, n, theta, ll, stream)
+        m.mbis_rb_loglike(ctx, n, theta, lr, stream)
+        times = {"exact": [], "rb": []}
+        for _ in range(reps):
+            for key, fn in (("exact", lambda: m.mbis_loglike(ctx, n, theta, ll, stream)),
+                            ("rb", lambda: m.mbis_rb_loglike(ctx, n, theta, lr, stream))):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times[key].append(e0.elapsed_time(e1) / 1e3)
+        se = m.mbis_reduce(ctx, n, ll, lp, lq)
+        sr = m.mbis_reduce(ctx, n, lr, lp, lq)
+        a, b, p = ll.cpu().numpy(), lr.cpu().numpy(), lp.cpu().numpy()
+        ok = np.isfinite(p)
+        lw = a[ok] + p[ok] - lq.cpu().numpy()[ok]
+        heavy = lw > lw.max() - 10.0
+        err = np.abs(b[ok] - a[ok])
+        t_ex, t_rb = statistics.mean(times["exact"]), statistics.mean(times["rb"])
+    finally:
+        m.mbis_destroy(ctx)
+    return {"workload": "bns_population event 0, 2^20 proposal samples, 128,513 bins, phase + distance marginalised",
+            "coarse_bins": int(len(edges) - 1), "bins_rule": f"mbis_rb_edges: {n_sigma} proposal sigmas, {eps} rad per bin",
+            "rb": {"value": n / t_rb, "unit": UNIT, "launch_ms": t_rb * 1e3},
+            "exact": {"value": n / t_ex, "unit": UNIT, "launch_ms": t_ex * 1e3},
+            "speedup": t_ex / t_rb,
+            "abs_dlogl_posterior_samples": {"median": float(np.median(err[heavy])), "max": float(err[heavy].max()),
+                                            "n": int(heavy.sum())},
+            "abs_dlogl_all_in_prior": {"median": float(np.median(err)), "p99": float(np.quantile(err, 0.99))},
+            "ess_exact": se["ess"], "ess_rb": sr["ess"], "dlogz": sr["log_z"] - se["log_z"]}
 
 
 SERVE_SEED = 0x5E12E
@@ -740,8 +788,9 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled,pp",
-                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled, pp) or 'none'")
+    ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled,pp,rb",
+                    help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled, pp, rb) or "
+                         "'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-compare", type=int, default=0,
                     help="also process the stream's first K requests serially in FP64 (slow)")
@@ -786,6 +835,8 @@ def main():
             out["tiled_proposal"] = tiled_measurement(m, torch)
         if "pp" in extras:
             out["pp_self_consistency"] = pp_measurement(m, torch)
+        if "rb" in extras:
+            out["relative_binning"] = rb_measurement(m, torch, evs)
         if "serve" in extras:
             served, reqs, res = serve_measurement(m, torch, n_req=args.serve_requests)
             if args.serve_compare > 0:

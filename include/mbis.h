@@ -439,6 +439,33 @@ const char* mbis_tiling_last_error(const mbis_tiling* t);
 mbis_status mbis_credible_levels(int64_t n, int32_t P, const double* theta, const double* weights, const double* ref,
                                  double* levels, void* cuda_stream);
 
+/* ---- relative binning (a faster approximate likelihood) ---------------------------- */
+
+/* The paper notes (Sec. IV) that faster likelihood evaluations plug into its method
+ * directly; relative binning (Zackay, Dai & Venumadhav 2018) is one.  About a fiducial
+ * theta0 (host, 11 slots) the template's ratio to the fiducial is taken as linear inside each
+ * of n_rb coarse bins with edges (host, n_rb + 1 increasing bin indices, edges[0] = 0,
+ * edges[n_rb] = n_bins; the last edge is the frequency one past the grid), so a likelihood
+ * costs n_rb + 1 phase evaluations instead of n_bins; <h|h> stays exact.  Needs a context
+ * with a metric, fixed sky and orientation (the folded table) and no time marginalisation;
+ * mbis_set_metric drops the set-up.  Allocates its summary data with cudaMalloc.
+ * Errors: MBIS_E_STATE, MBIS_E_UNSUPPORTED, MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
+mbis_status mbis_rb_setup(mbis_ctx* ctx, const double* theta0, int32_t n_rb, const int32_t* edges);
+
+/* Relative-binning log-likelihood ratios of n samples (device theta [P][n] -> loglike [n]),
+ * with the marginalisations of the context.  The error against mbis_loglike grows with the
+ * square of each bin's phase excursion (see mbis_rb_edges).  Errors: MBIS_E_STATE (no
+ * set-up), MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_rb_loglike(mbis_ctx* ctx, int64_t n, const double* theta, double* loglike, void* cuda_stream);
+
+/* Coarse bins for relative binning: each bin's largest change of the template's phase
+ * relative to the fiducial, over the box theta0 +- n_sigma proposal standard deviations
+ * (clipped to the prior), stays below eps_rad, which bounds the chord's error by about
+ * eps_rad^2 / 8 of the bin's overlap.  edges (host, max_bins + 1), *n_rb (host).
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID (more than max_bins bins). */
+mbis_status mbis_rb_edges(const mbis_ctx* ctx, const double* theta0, double n_sigma, double eps_rad, int32_t max_bins,
+                          int32_t* edges, int32_t* n_rb);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);

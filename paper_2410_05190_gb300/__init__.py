@@ -131,6 +131,9 @@ def _load():
         "mbis_server_stats_get": [p, p],
         "mbis_debug_wait_timeout": [u64, p, p],
         "mbis_credible_levels": [i64, i32, p, p, p, p, p],
+        "mbis_rb_setup": [p, p, i32, p],
+        "mbis_rb_loglike": [p, i64, p, p, p],
+        "mbis_rb_edges": [p, p, d, d, i32, p, p],
         "mbis_tiling_create": [p, p, p, p],
         "mbis_tiling_bank": [p, i64, p, d, i64, i32, p, p],
         "mbis_tiling_templates": [p, p, p, p, p],
@@ -545,3 +548,23 @@ def mbis_credible_levels(n, theta, weights, ref, levels, stream=None):
     levels [P] (device)."""
     r, pr = _host(ref, np.float64)
     _check(_lib.mbis_credible_levels(n, len(r), _dev(theta), _dev(weights), pr, _dev(levels), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------- relative binning
+def mbis_rb_setup(ctx, theta0, edges):
+    t0, pt = _host(theta0, np.float64)
+    e, pe = _host(edges, np.int32)
+    _check(_lib.mbis_rb_setup(ctx, pt, len(e) - 1, pe), ctx)
+
+
+def mbis_rb_loglike(ctx, n, theta, loglike, stream=None):
+    _check(_lib.mbis_rb_loglike(ctx, n, _dev(theta), _dev(loglike), _stream(stream)), ctx)
+
+
+def mbis_rb_edges(ctx, theta0, n_sigma, eps_rad, max_bins=65536):
+    """Bin edges (int32 array of n_rb + 1) for relative binning about theta0."""
+    t0, pt = _host(theta0, np.float64)
+    edges = np.zeros(max_bins + 1, dtype=np.int32)
+    nrb = C.c_int32()
+    _check(_lib.mbis_rb_edges(ctx, pt, n_sigma, eps_rad, max_bins, edges.ctypes.data, C.byref(nrb)), ctx)
+    return edges[:nrb.value + 1].copy()

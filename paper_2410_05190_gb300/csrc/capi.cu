@@ -594,6 +594,7 @@ mbis_status mbis_create(const mbis_event* ev, const double* psd, const mbis_dete
 
 void mbis_destroy(mbis_ctx* c) {
   if (!c) return;
+  rb_free(c);
   free_tables(c);
   dfree(c, c->d_strain);
   dfree(c, c->d_psd64);

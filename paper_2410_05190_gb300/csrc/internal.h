@@ -207,6 +207,7 @@ void ess_result(const EssState& st, mbis_summary* out, int64_t* n_drawn, int64_t
 DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
                         double* log_prior);
 LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, double* loglike);
+void rb_free(mbis_ctx* c);
 }  // namespace mbis
 
 // the context behind the opaque handle
@@ -254,6 +255,14 @@ struct mbis_ctx {
   int32_t n_blocks = 0;
   int32_t* d_err = nullptr;
   double* d_gl = nullptr;
+  // relative binning about a fiducial (mbis_rb_setup)
+  int32_t rb_n = 0;                 // coarse bins (0: not set up)
+  uint64_t rb_gen = 0;              // tables generation the summary data belong to
+  int32_t* d_rb_edges = nullptr;    // [rb_n + 1] bin indices of the edges
+  void* d_rb_rec = nullptr;         // [rb_n + 1] 64-byte coarse-bin records (k_rb.cu)
+  double* d_rb_prefix = nullptr;    // [4][n_bins + 1] prefix sums of W, (f - f_lo) W (re, im)
+  double rb_scale = 1.0;
+  double rb_C0[mbis::kNumBasis] = {}, rb_cst0 = 0.0;
   // reduction scratch
   mbis::ReduceScratch red = {};
   double* h_result = nullptr;  // pinned host scratch, kHostScratch doubles: [0..3] reduction, [4] error word,
