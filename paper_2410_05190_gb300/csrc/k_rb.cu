@@ -28,7 +28,7 @@
 namespace mbis {
 namespace {
 
-constexpr int kRbThreads = 128;
+constexpr int kRbThreads = 256;
 constexpr int kRbChunk = 16;
 constexpr size_t kRbSmemMax = 112 * 1024;  // records staged in shared memory up to 1791 bins
 constexpr float kTwoPiF = 6.28318530717958647692f;
