@@ -318,6 +318,8 @@ LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, doubl
   a.ff_phase = c->ff_phase;
   a.err = c->d_err;
   a.gl = c->d_gl;
+  a.glf = reinterpret_cast<const float*>(c->d_gl + kGLSize);
+  a.dist = dist_const(c->opts.dmin_mpc, c->opts.dmax_mpc);
   return a;
 }
 }  // namespace mbis
@@ -383,11 +385,15 @@ mbis_status mbis::create_ctx(const mbis_event* ev, const double* psd, const mbis
   CREATE_TRY(dalloc(c, &c->d_basis, sizeof(double) * kNumBasis * (size_t)c->n_bins));
   CREATE_TRY(launch_basis_table(c->f_lo, c->df, c->n_bins, c->d_basis, s));
   {
+    // FP64 nodes / weights followed by their FP32 copy
     double gl[kGLSize];
+    float glf[kGLSize];
     fill_gauss_legendre(gl);
-    CREATE_TRY(dalloc(c, &c->d_gl, sizeof(gl)));
+    fill_gauss_legendre_f32(glf);
+    CREATE_TRY(dalloc(c, &c->d_gl, sizeof(gl) + sizeof(glf)));
     CREATE_TRY(cudaMemcpyAsync(c->d_gl, gl, sizeof(gl), cudaMemcpyHostToDevice, s));
-    CREATE_TRY(cudaStreamSynchronize(s));  // gl is on this stack frame
+    CREATE_TRY(cudaMemcpyAsync(c->d_gl + kGLSize, glf, sizeof(glf), cudaMemcpyHostToDevice, s));
+    CREATE_TRY(cudaStreamSynchronize(s));  // gl, glf are on this stack frame
   }
   CREATE_TRY(dalloc(c, &c->d_err, sizeof(int32_t)));
   CREATE_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));

@@ -1,5 +1,6 @@
 // ffloat.cuh -- float-float ("double-single") helpers for the anchor-block entry of the
-// mixed-precision kernels, for events whose phase terms stay below kFloatFloatMaxTurns.
+// mixed-precision kernels, for events whose phase terms stay below kFloatFloatMaxTurns, and
+// for their running sums of FP32 partial sums.
 #pragma once
 #include <cstdint>
 
@@ -13,6 +14,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
+
+// A running sum of floats as an unevaluated pair: each addition into h is error-free
+// (two-sum) and its rounding error is gathered in l, so the pair carries ~2^-48 relative
+// accuracy without FP64 arithmetic (which the GB300 runs at a small fraction of FP32).
+struct FFSum {
+  float h = 0.0f, l = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(h, x, s, e);
+    h = s;
+    l = __fadd_rn(l, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
 
 // (sh, sl) += (ch, cl) * (bh, bl)
 __device__ __forceinline__ void ff_mac(float ch, float cl, float bh, float bl, float& sh, float& sl) {

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/mbis.h"
+#include "marg.cuh"
 #include "physics.cuh"
 
 namespace mbis {
@@ -78,6 +79,8 @@ struct LikeArgs {
   int32_t ff_phase;           // block entry in float-float (phase terms below kFloatFloatMaxTurns)
   int32_t* err;               // device error word (timeouts)
   const double* gl;           // Gauss-Legendre nodes / weights (marg.cuh layout)
+  const float* glf;           // the same nodes / weights in FP32 (mixed-precision marginal)
+  DistConst dist;             // distance-marginal constants of [dmin, dmax]
 };
 
 struct DrawArgs {

@@ -209,7 +209,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   }
 
   // ---- sweep over frequency
-  double Zr = 0.0, Zi = 0.0;
+  FFSum Zr, Zi;  // the chunks' FP32 sums, added without FP64 arithmetic
   BlockState st;
   int32_t blk_end = 0;
   int blk = -1;
@@ -287,8 +287,12 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
       }
       k = seg_end;
     }
-    Zr += (double)zr.x + (double)zr.y;
-    Zi += ((double)zi.x + (double)zi.y) - ((double)zn.x + (double)zn.y);
+    Zr.add(zr.x);
+    Zr.add(zr.y);
+    Zi.add(zi.x);
+    Zi.add(zi.y);
+    Zi.add(-zn.x);
+    Zi.add(-zn.y);
     __syncthreads();  // every thread is done with buffer b
     if (tid == 0 && ch + kNbuf < nch) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -314,7 +318,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
     return;
   }
   // ---- marginalisation (Sec. III)
-  const double zr = A * a.cscale * Zr, zi = A * a.cscale * Zi;
+  const double zr = A * a.cscale * Zr.value(), zi = A * a.cscale * Zi.value();
   const double H = A * A * a.tfold[kcut];
   double ll;
   if (a.marg == 0) {
@@ -322,7 +326,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   } else if (a.marg == MBIS_MARG_PHASE) {
     ll = log_i0(hypot(zr, zi)) - 0.5 * H;
   } else {
-    ll = log_distance_marginal_mixed(hypot(zr, zi), H, a.dmin, a.dmax, a.gl);
+    ll = log_distance_marginal_mixed(hypot(zr, zi), H, a.dist, a.glf);
   }
   a.out[s] = ll;
 }

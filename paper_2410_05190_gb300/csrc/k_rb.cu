@@ -13,7 +13,7 @@
 // exact (the amplitude prefix table).  Per sample the phase is evaluated at the n_rb + 1
 // edges only: its difference from the fiducial's, in FP32 from FP64 coefficient
 // differences, then MUFU sine / cosine; the chord sums run in FP32 over chunks of 16 bins
-// added into FP64.
+// whose sums are gathered as float pairs (no FP64 arithmetic in the loop over bins).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,13 +22,14 @@
 #include <string>
 #include <vector>
 
+#include "ffloat.cuh"
 #include "internal.h"
 #include "marg.cuh"
 
 namespace mbis {
 namespace {
 
-constexpr int kRbThreads = 256;
+constexpr int kRbThreads = 512;
 constexpr int kRbChunk = 16;
 constexpr size_t kRbSmemMax = 112 * 1024;  // records staged in shared memory up to 1791 bins
 constexpr float kTwoPiF = 6.28318530717958647692f;
@@ -111,7 +112,7 @@ __device__ __forceinline__ void cmac(float2 a, float2 b, float& zr, float& zi) {
   zi = fmaf(a.x, b.y, fmaf(a.y, b.x, zi));
 }
 
-__global__ void __launch_bounds__(kRbThreads) rb_loglike_kernel(RbArgs r) {
+__global__ void __launch_bounds__(kRbThreads, 2) rb_loglike_kernel(RbArgs r) {
   extern __shared__ RbRec s_rec[];
   const LikeArgs& a = r.la;
   const RbRec* recs = r.rec;
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(kRbThreads) rb_loglike_kernel(RbArgs r) {
   for (int j = 0; j < kNumBasis; ++j) dC[j] = (float)(pc.C[j] - r.C0[j]);
   const float dcst = (float)(pc.cst - r.cst0);
 
-  double zr64 = 0.0, zi64 = 0.0;
+  FFSum zr_all, zi_all;        // the chunk sums (scaled), added without FP64 arithmetic
+  double zr64 = 0.0, zi64 = 0.0;  // the partial bin at the ISCO cut (FP64 prefix sums)
   float zr = 0.f, zi = 0.f;
   RbRec cur = recs[0];
   float2 rho = rho_at(cur, dC, dcst);
@@ -156,8 +158,8 @@ __global__ void __launch_bounds__(kRbThreads) rb_loglike_kernel(RbArgs r) {
       cmac(rho, make_float2(cur.sum.x, cur.sum.y), zr, zi);
       cmac(slope, make_float2(cur.sum.z, cur.sum.w), zr, zi);
       if ((b + 1) % kRbChunk == 0) {
-        zr64 += (double)zr * r.scale;
-        zi64 += (double)zi * r.scale;
+        zr_all.add(zr);
+        zi_all.add(zi);
         zr = zi = 0.f;
       }
     } else {
@@ -175,15 +177,17 @@ __global__ void __launch_bounds__(kRbThreads) rb_loglike_kernel(RbArgs r) {
     rho = rho1;
     cur = nxt;
   }
-  zr64 += (double)zr * r.scale;
-  zi64 += (double)zi * r.scale;
+  zr_all.add(zr);
+  zi_all.add(zi);
+  zr64 += zr_all.value() * r.scale;
+  zi64 += zi_all.value() * r.scale;
   const double z = ms.amp * hypot(zr64, zi64);
   const double H = ms.amp * ms.amp * a.tfold[kcut];
   double ll;
   if (a.marg == MBIS_MARG_PHASE)
     ll = log_i0(z) - 0.5 * H;
   else if (a.marg == (MBIS_MARG_PHASE | MBIS_MARG_DISTANCE))
-    ll = log_distance_marginal_mixed(z, H, a.dmin, a.dmax, a.gl);  // as the fused kernel
+    ll = log_distance_marginal_mixed(z, H, a.dist, a.glf);  // as the fused kernel
   else
     ll = ms.amp * zr64 - 0.5 * H;  // no marginalisation: Re (d|h) - <h|h> / 2
   a.out[s] = ll;

@@ -106,61 +106,84 @@ struct LogSumExpF {
   }
 };
 
-// The same quadrature as log_distance_marginal, with the nodes evaluated in FP32 as
-// differences G(s) - G(s_ref) from one FP64 evaluation at s_ref (the peak, or the
-// large-distance end when there is none).  The differences are formed from small
-// quantities (u - u_ref = u_ref expm1(s - s_ref)), so FP32 keeps ~1e-6 relative accuracy
-// on each weight and the result carries the FP64 accuracy of G(s_ref).
-__device__ __forceinline__ void dist_rule_f(LogSumExpF& L, double a, double b, int panels, int n, const double* x,
-                                            const double* w, float Z, float H, double s_ref, float u_ref,
-                                            float phi_ref) {
-  const double h = (b - a) / panels;
+// One composite rule over [lo, hi] (offsets from the reference point s_ref) with the nodes
+// evaluated in FP32 as differences G(s) - G(s_ref): u - u_ref = u_ref expm1(s - s_ref)
+// keeps the differences small, so FP32 carries ~1e-6 relative accuracy on each weight.
+__device__ __forceinline__ void dist_rule_f(LogSumExpF& L, float lo, float hi, int panels, int n, const float* x,
+                                            const float* w, float Z, float H, float u_ref, float phi_ref) {
+  const float h = (hi - lo) * (1.0f / (float)panels), half = 0.5f * h;
   for (int p = 0; p < panels; ++p) {
-    const double mid = a + (p + 0.5) * h;
-    const float half = (float)(0.5 * h);
-    const float dmid = (float)(mid - s_ref);
+    const float mid = fmaf((float)p + 0.5f, h, lo);
     for (int i = 0; i < n; ++i) {
-      const float d = fmaf(half, (float)x[i], dmid);  // s - s_ref
+      const float d = fmaf(half, __ldg(x + i), mid);  // s - s_ref
       const float du = u_ref * expm1f(d);
       const float u = u_ref + du;
       const float g = Z * du - 0.5f * H * du * (2.0f * u_ref + du) - 3.0f * d + (log_i0_minus_x_f(Z * u) - phi_ref);
-      L.add(g, half * (float)w[i]);
+      L.add(g, half * __ldg(w + i));
     }
   }
 }
+#endif
 
-__device__ __forceinline__ double log_distance_marginal_mixed(double Z, double H, double dmin, double dmax,
-                                                              const double* gl) {
-  const double* x48 = gl;
-  const double* w48 = gl + kGL48;
-  const double* x8 = gl + 2 * kGL48;
-  const double* w8 = gl + 2 * kGL48 + kGL8;
-  const double c0 = log(3.0 / (dmax * dmax * dmax - dmin * dmin * dmin));
-  const double s_lo = -log(dmax), s_hi = -log(dmin);
+// Per-context constants of the distance marginal: c0 = ln(3 / (dmax^3 - dmin^3)), the
+// large-distance end u_lo = 1 / dmax rounded to FP32 with s_lo = ln(u_lo) taken from that
+// rounded value (so that the FP32 reference points below stay consistent with their
+// logarithms), and the width of the range in s.
+struct DistConst {
+  double c0, s_lo;
+  float u_lo, span;
+};
+
+inline DistConst dist_const(double dmin, double dmax) {
+  DistConst d;
+  d.c0 = std::log(3.0 / (dmax * dmax * dmax - dmin * dmin * dmin));
+  d.u_lo = (float)(1.0 / dmax);
+  d.s_lo = std::log((double)d.u_lo);
+  d.span = (float)(-std::log(dmin) - d.s_lo);
+  return d;
+}
+
+#ifdef __CUDACC__
+// The distance marginal of log_distance_marginal with the same rules (48-point window of
+// +-12 widths about the peak, 4-panel 8-point composite rules outside it; 24 panels of 8
+// points without a peak), taken in FP32 about a reference point s_ref (the peak, or the
+// large-distance end): every node contributes G(s) - G(s_ref) from dist_rule_f, and G(s_ref)
+// itself is assembled in FP64 from exact products,
+//   G(s_ref) = c0 - 3 s_ref + Z u_ref + [ln I0(Z u_ref) - Z u_ref] - H u_ref^2 / 2,
+// so that the few terms that grow with the signal (Z u_ref, H u_ref^2 reach 10^4) keep FP64
+// accuracy while the bracket, the window and the nodes run in FP32.  The reference u_ref is
+// an FP32 number and s_ref = s_lo + (its offset), consistent with ln u_ref to FP32 rounding.
+__device__ __forceinline__ double log_distance_marginal_mixed(double Z, double H, const DistConst& dc,
+                                                              const float* gl) {
+  const float* x48 = gl;
+  const float* w48 = gl + kGL48;
+  const float* x8 = gl + 2 * kGL48;
+  const float* w8 = gl + 2 * kGL48 + kGL8;
+  const float Zf = (float)Z, Hf = (float)H, span = dc.span;
   bool window = false;
-  double wlo = s_lo, whi = s_hi, s_ref = s_lo;
-  if (H > 0.0 && Z * Z > 14.0 * H) {
-    const double u = (Z + sqrt(Z * Z - 14.0 * H)) / (2.0 * H);
-    const double sig = 1.0 / sqrt(fmax(Z * u - 7.0, 1e-300));
-    const double sc = log(u);
-    wlo = fmax(s_lo, sc - 12.0 * sig);
-    whi = fmin(s_hi, sc + 12.0 * sig);
+  float wlo = 0.0f, whi = span, r_ref = 0.0f;  // offsets from s_lo
+  if (Hf > 0.0f && Zf * Zf > 14.0f * Hf) {
+    const float u = (Zf + sqrtf(Zf * Zf - 14.0f * Hf)) / (2.0f * Hf);
+    const float sig = rsqrtf(fmaxf(Zf * u - 7.0f, 1e-30f));
+    const float rc = logf(u / dc.u_lo);
+    wlo = fmaxf(0.0f, rc - 12.0f * sig);
+    whi = fminf(span, rc + 12.0f * sig);
     window = wlo < whi;
-    s_ref = fmin(fmax(sc, s_lo), s_hi);
+    r_ref = fminf(fmaxf(rc, 0.0f), span);
   }
-  const double u_ref = exp(s_ref);
-  const double g_ref = c0 - 3.0 * s_ref + log_i0(Z * u_ref) - 0.5 * H * u_ref * u_ref;
-  const float Zf = (float)Z, Hf = (float)H, uf = (float)u_ref;
+  const float uf = dc.u_lo * __expf(r_ref);
   const float phi_ref = log_i0_minus_x_f(Zf * uf);
   LogSumExpF L;
   if (window) {
-    dist_rule_f(L, wlo, whi, 1, kGL48, x48, w48, Zf, Hf, s_ref, uf, phi_ref);
-    if (wlo > s_lo) dist_rule_f(L, s_lo, wlo, 4, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
-    if (whi < s_hi) dist_rule_f(L, whi, s_hi, 4, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
+    dist_rule_f(L, wlo - r_ref, whi - r_ref, 1, kGL48, x48, w48, Zf, Hf, uf, phi_ref);
+    if (wlo > 0.0f) dist_rule_f(L, -r_ref, wlo - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
+    if (whi < span) dist_rule_f(L, whi - r_ref, span - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
   } else {
-    dist_rule_f(L, s_lo, s_hi, 24, kGL8, x8, w8, Zf, Hf, s_ref, uf, phi_ref);
+    dist_rule_f(L, -r_ref, span - r_ref, 24, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
   }
-  return g_ref + (double)L.m + log((double)L.acc);
+  const double u_ref = (double)uf;
+  const double g_ref = dc.c0 - 3.0 * (dc.s_lo + (double)r_ref) + Z * u_ref - 0.5 * H * u_ref * u_ref + (double)phi_ref;
+  return g_ref + (double)L.m + (double)logf(L.acc);
 }
 #endif
 
@@ -188,6 +211,13 @@ inline void gauss_legendre(int n, double* x, double* w) {
 inline void fill_gauss_legendre(double* gl) {
   gauss_legendre(kGL48, gl, gl + kGL48);
   gauss_legendre(kGL8, gl + 2 * kGL48, gl + 2 * kGL48 + kGL8);
+}
+
+// the same table rounded to FP32 (the mixed-precision marginal's copy)
+inline void fill_gauss_legendre_f32(float* glf) {
+  double gl[kGLSize];
+  fill_gauss_legendre(gl);
+  for (int i = 0; i < kGLSize; ++i) glf[i] = (float)gl[i];
 }
 
 }  // namespace mbis
