@@ -262,7 +262,8 @@ struct mbis_ctx {
   int32_t rb_n = 0;                 // coarse bins (0: not set up)
   uint64_t rb_gen = 0;              // tables generation the summary data belong to
   int32_t* d_rb_edges = nullptr;    // [rb_n + 1] bin indices of the edges
-  void* d_rb_rec = nullptr;         // [rb_n + 1] 64-byte coarse-bin records (k_rb.cu)
+  void* d_rb_rec = nullptr;         // [rb_n + 1] 48-byte edge records (k_rb.cu)
+  void* d_rb_q = nullptr;           // [rb_n] float2 q_b / scale (k_rb.cu)
   double* d_rb_prefix = nullptr;    // [4][n_bins + 1] prefix sums of W, (f - f_lo) W (re, im)
   double rb_scale = 1.0;
   double rb_C0[mbis::kNumBasis] = {}, rb_cst0 = 0.0;

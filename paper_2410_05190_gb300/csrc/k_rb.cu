@@ -7,13 +7,17 @@
 // replaced by its chord through the bin's edges.  With the fiducial-heterodyned data weights
 // W_k = c_k e^(-i 2 pi Psi0(f_k)) (c the folded data table, which carries the detector
 // responses, delays, f^(-7/6), 1/S and 4 df), the overlap becomes
-//   Z = A sum_b [rho(f_b) A0_b + (rho(f_b+1) - rho(f_b)) / (f_b+1 - f_b) A1_b],
-//   A0_b = sum_{k in b} W_k,  A1_b = sum_{k in b} W_k (f_k - f_b),  rho = e^(-i 2 pi dPsi),
-// the bin holding the sample's ISCO cut summed only below it (from prefix sums); <h|h> stays
-// exact (the amplitude prefix table).  Per sample the phase is evaluated at the n_rb + 1
-// edges only: its difference from the fiducial's, in FP32 from FP64 coefficient
-// differences, then MUFU sine / cosine; the chord sums run in FP32 over chunks of 16 bins
-// whose sums are gathered as float pairs (no FP64 arithmetic in the loop over bins).
+//   Z = A sum_b [rho_b A0_b + (rho_b+1 - rho_b) / (f_b+1 - f_b) A1_b],
+//   A0_b = sum_{k in b} W_k,  A1_b = sum_{k in b} W_k (f_k - f_b),  rho_e = e^(-i 2 pi dPsi(f_e)).
+// Regrouped by edge, with p_b = A0_b - A1_b / w_b and q_b = A1_b / w_b (w_b the bin's width),
+//   Z = A [sum_{e < n} rho_e (p_e + q_e-1) + rho_n q_n-1],
+// n the number of bins that lie wholly below the sample's ISCO cut: one complex weight per
+// edge, so that the sweep costs one phase evaluation and one complex multiply-add per edge.
+// The bin holding the cut is summed only below it (from FP64 prefix sums); <h|h> stays exact
+// (the amplitude prefix table).  The phase difference from the fiducial's runs in FP32 from
+// FP64 coefficient differences, then MUFU sine / cosine; the edge sums run in FP32 over
+// chunks of 16 edges whose sums are gathered as float pairs (no FP64 arithmetic in the
+// sweep).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,9 +33,9 @@
 namespace mbis {
 namespace {
 
-constexpr int kRbThreads = 512;
+constexpr int kRbThreads = 256;
 constexpr int kRbChunk = 16;
-constexpr size_t kRbSmemMax = 112 * 1024;  // records staged in shared memory up to 1791 bins
+constexpr size_t kRbSmemMax = 112 * 1024;  // records staged in shared memory up to 2388 bins
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 // W_k and (f_k - f_lo) W_k as four real rows [re W, im W, re fW, im fW][n]
@@ -53,73 +57,88 @@ __global__ void rb_weights_kernel(int32_t n, const double2* __restrict__ c, cons
   out[3 * (int64_t)n + k] = fk * wi;
 }
 
-// One coarse-bin record (64 bytes): basis_j at the bin's left edge, 1 / width, the edge's bin
-// index, and the bin's sums (A0, A1) / scale; record n_rb carries the last edge only.
-struct RbRec {
-  float be[kNumBasis];
-  float invw;
-  int32_t k0;
-  float pad;
-  float4 sum;
-};
-static_assert(sizeof(RbRec) == 64, "coarse-bin record is 64 bytes");
+// One edge record: three float4 = (c_e re, c_e im, B_0, B_1), (B_2 .. B_5), (B_6, B_7, B_8, 0),
+// c_e = (p_e + q_e-1) / scale (zero at the last edge) and B_j the basis at the edge.
+constexpr int kEdgeVec = 3;
+
+// bin b's sums from the prefix tables: A0 and A1 / w as (re, im) pairs
+__device__ __forceinline__ void bin_sums(const double* T, int64_t m, int32_t k0, int32_t k1, double df, double& a0r,
+                                         double& a0i, double& qr, double& qi) {
+  a0r = T[k1] - T[k0];
+  a0i = T[m + k1] - T[m + k0];
+  const double ofs = (double)k0 * df;  // f_b - f_lo
+  const double inv_w = 1.0 / ((double)(k1 - k0) * df);
+  qr = ((T[2 * m + k1] - T[2 * m + k0]) - ofs * a0r) * inv_w;
+  qi = ((T[3 * m + k1] - T[3 * m + k0]) - ofs * a0i) * inv_w;
+}
 
 __global__ void rb_summary_kernel(int32_t n_rb, int32_t n, const int32_t* __restrict__ edges,
                                   const double* __restrict__ T, double f_lo, double df, double inv_scale,
-                                  RbRec* rec) {
-  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b > n_rb) return;
-  RbRec r = {};
-  const double fe = f_lo + (double)edges[b] * df;
-  for (int j = 0; j < kNumBasis; ++j) r.be[j] = (float)basis(j, fe);
-  r.k0 = edges[b];
-  if (b < n_rb) {
-    const int32_t k0 = edges[b], k1 = edges[b + 1];
-    const int64_t m = (int64_t)n + 1;
-    const double a0r = T[k1] - T[k0], a0i = T[m + k1] - T[m + k0];
-    const double ofs = (double)k0 * df;  // f_b - f_lo
-    const double a1r = (T[2 * m + k1] - T[2 * m + k0]) - ofs * a0r;
-    const double a1i = (T[3 * m + k1] - T[3 * m + k0]) - ofs * a0i;
-    r.sum = make_float4((float)(a0r * inv_scale), (float)(a0i * inv_scale), (float)(a1r * inv_scale),
-                        (float)(a1i * inv_scale));
-    r.invw = (float)(1.0 / ((double)(k1 - k0) * df));
+                                  float4* rec, float2* q_out) {
+  const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > n_rb) return;
+  const int64_t m = (int64_t)n + 1;
+  double cr = 0.0, ci = 0.0;
+  if (e < n_rb) {
+    double a0r, a0i, qr, qi;
+    bin_sums(T, m, edges[e], edges[e + 1], df, a0r, a0i, qr, qi);
+    cr += a0r - qr;
+    ci += a0i - qi;
+    q_out[e] = make_float2((float)(qr * inv_scale), (float)(qi * inv_scale));
   }
-  rec[b] = r;
+  if (e > 0 && e < n_rb) {
+    double a0r, a0i, qr, qi;
+    bin_sums(T, m, edges[e - 1], edges[e], df, a0r, a0i, qr, qi);
+    cr += qr;
+    ci += qi;
+  }
+  float b[kNumBasis];
+  const double fe = f_lo + (double)edges[e] * df;
+  for (int j = 0; j < kNumBasis; ++j) b[j] = (float)basis(j, fe);
+  float4* r = rec + (int64_t)kEdgeVec * e;
+  r[0] = make_float4((float)(cr * inv_scale), (float)(ci * inv_scale), b[0], b[1]);
+  r[1] = make_float4(b[2], b[3], b[4], b[5]);
+  r[2] = make_float4(b[6], b[7], b[8], 0.0f);
 }
 
 struct RbArgs {
   LikeArgs la;
   int32_t n_rb;
-  const RbRec* rec;      // [n_rb + 1]
+  const float4* rec;     // [n_rb + 1][kEdgeVec]
+  const float2* q;       // [n_rb] q_b / scale
+  const int32_t* edges;  // [n_rb + 1]
   int32_t rec_smem;      // stage the records in shared memory
   const double* prefix;  // [4][n_bins + 1]
   double scale;
   double C0[kNumBasis], cst0;
 };
 
-__device__ __forceinline__ float2 rho_at(const RbRec& r, const float* dC, float dcst) {
-  float t = dcst;
-#pragma unroll
-  for (int j = 0; j < kNumBasis; ++j) t = fmaf(dC[j], r.be[j], t);
-  t -= rintf(t);  // turns in [-1/2, 1/2]
-  float s, c;
-  __sincosf(-kTwoPiF * t, &s, &c);
-  return make_float2(c, s);  // e^(-i 2 pi t)
+// e^(-i 2 pi dPsi) at one edge, and the edge's weight c_e
+__device__ __forceinline__ float2 edge_rho(const float4* __restrict__ e, const float* dC, float dcst, float2& c) {
+  const float4 r0 = e[0], r1 = e[1], r2 = e[2];
+  c = make_float2(r0.x, r0.y);
+  float t = fmaf(dC[0], r0.z, dcst);
+  t = fmaf(dC[1], r0.w, t);
+  t = fmaf(dC[2], r1.x, t);
+  t = fmaf(dC[3], r1.y, t);
+  t = fmaf(dC[4], r1.z, t);
+  t = fmaf(dC[5], r1.w, t);
+  t = fmaf(dC[6], r2.x, t);
+  t = fmaf(dC[7], r2.y, t);
+  t = fmaf(dC[8], r2.z, t);
+  // the nearest integer removed (1.5 * 2^23 rounds |t| < 2^22 to an integer): turns in [-1/2, 1/2]
+  t = __fsub_rn(t, __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f));
+  float s, co;
+  __sincosf(-kTwoPiF * t, &s, &co);
+  return make_float2(co, s);
 }
 
-__device__ __forceinline__ void cmac(float2 a, float2 b, float& zr, float& zi) {
-  zr = fmaf(a.x, b.x, fmaf(-a.y, b.y, zr));
-  zi = fmaf(a.x, b.y, fmaf(a.y, b.x, zi));
-}
-
-__global__ void __launch_bounds__(kRbThreads, 2) rb_loglike_kernel(RbArgs r) {
-  extern __shared__ RbRec s_rec[];
+__global__ void __launch_bounds__(kRbThreads, 3) rb_loglike_kernel(RbArgs r) {
+  extern __shared__ float4 s_rec[];
   const LikeArgs& a = r.la;
-  const RbRec* recs = r.rec;
+  const float4* recs = r.rec;
   if (r.rec_smem) {
-    const float4* src = reinterpret_cast<const float4*>(r.rec);
-    float4* dst = reinterpret_cast<float4*>(s_rec);
-    for (int i = threadIdx.x; i < 4 * (r.n_rb + 1); i += blockDim.x) dst[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < kEdgeVec * (r.n_rb + 1); i += blockDim.x) s_rec[i] = __ldg(r.rec + i);
     __syncthreads();
     recs = s_rec;
   }
@@ -143,44 +162,66 @@ __global__ void __launch_bounds__(kRbThreads, 2) rb_loglike_kernel(RbArgs r) {
   for (int j = 0; j < kNumBasis; ++j) dC[j] = (float)(pc.C[j] - r.C0[j]);
   const float dcst = (float)(pc.cst - r.cst0);
 
-  FFSum zr_all, zi_all;        // the chunk sums (scaled), added without FP64 arithmetic
-  double zr64 = 0.0, zi64 = 0.0;  // the partial bin at the ISCO cut (FP64 prefix sums)
-  float zr = 0.f, zi = 0.f;
-  RbRec cur = recs[0];
-  float2 rho = rho_at(cur, dC, dcst);
-  for (int32_t b = 0; b < r.n_rb; ++b) {
-    const RbRec nxt = recs[b + 1];
-    const int32_t k0 = cur.k0, k1 = nxt.k0;
-    if (k0 >= kcut) break;
-    const float2 rho1 = rho_at(nxt, dC, dcst);
-    const float2 slope = make_float2((rho1.x - rho.x) * cur.invw, (rho1.y - rho.y) * cur.invw);
-    if (k1 <= kcut) {
-      cmac(rho, make_float2(cur.sum.x, cur.sum.y), zr, zi);
-      cmac(slope, make_float2(cur.sum.z, cur.sum.w), zr, zi);
-      if ((b + 1) % kRbChunk == 0) {
-        zr_all.add(zr);
-        zi_all.add(zi);
-        zr = zi = 0.f;
-      }
-    } else {
-      // the bin holding the ISCO cut: its sums below the cut, from the prefix tables
-      const int64_t m = (int64_t)a.n_bins + 1;
-      const double* T = r.prefix;
-      const double a0r = T[kcut] - T[k0], a0i = T[m + kcut] - T[m + k0];
-      const double ofs = (double)k0 * a.df;
-      const double a1r = (T[2 * m + kcut] - T[2 * m + k0]) - ofs * a0r;
-      const double a1i = (T[3 * m + kcut] - T[3 * m + k0]) - ofs * a0i;
-      zr64 += (double)rho.x * a0r - (double)rho.y * a0i + (double)slope.x * a1r - (double)slope.y * a1i;
-      zi64 += (double)rho.x * a0i + (double)rho.y * a0r + (double)slope.x * a1i + (double)slope.y * a1r;
-      break;
+  // nfull = the last edge at or below the cut: bins 0 .. nfull-1 lie wholly below it
+  int32_t lo = 0, hi = r.n_rb;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(r.edges + mid) <= kcut)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int32_t nfull = lo;
+
+  FFSum zr_all, zi_all;  // chunk sums, scaled by 1 / scale
+  int32_t e = 0;
+  for (; e + kRbChunk <= nfull; e += kRbChunk) {
+    float zr = 0.f, zi = 0.f;
+#pragma unroll
+    for (int j = 0; j < kRbChunk; ++j) {
+      float2 c;
+      const float2 rho = edge_rho(recs + kEdgeVec * (e + j), dC, dcst, c);
+      zr = fmaf(rho.x, c.x, fmaf(-rho.y, c.y, zr));
+      zi = fmaf(rho.x, c.y, fmaf(rho.y, c.x, zi));
     }
-    rho = rho1;
-    cur = nxt;
+    zr_all.add(zr);
+    zi_all.add(zi);
+  }
+  float zr = 0.f, zi = 0.f;
+  for (; e < nfull; ++e) {
+    float2 c;
+    const float2 rho = edge_rho(recs + kEdgeVec * e, dC, dcst, c);
+    zr = fmaf(rho.x, c.x, fmaf(-rho.y, c.y, zr));
+    zi = fmaf(rho.x, c.y, fmaf(rho.y, c.x, zi));
+  }
+  // edge nfull: the far end of the last whole bin, and the near end of the bin holding the cut
+  float2 c_unused;
+  const float2 rho_n = edge_rho(recs + kEdgeVec * nfull, dC, dcst, c_unused);
+  if (nfull > 0) {
+    const float2 q = r.q[nfull - 1];
+    zr = fmaf(rho_n.x, q.x, fmaf(-rho_n.y, q.y, zr));
+    zi = fmaf(rho_n.x, q.y, fmaf(rho_n.y, q.x, zi));
   }
   zr_all.add(zr);
   zi_all.add(zi);
-  zr64 += zr_all.value() * r.scale;
-  zi64 += zi_all.value() * r.scale;
+  double zr64 = zr_all.value() * r.scale, zi64 = zi_all.value() * r.scale;
+  const int32_t k0 = __ldg(r.edges + nfull);
+  if (k0 < kcut) {
+    // the bin holding the ISCO cut (nfull < n_rb here): its sums below the cut, from the
+    // prefix tables, against the chord through the bin's two edges
+    const int32_t k1 = __ldg(r.edges + nfull + 1);
+    const float2 rho1 = edge_rho(recs + kEdgeVec * (nfull + 1), dC, dcst, c_unused);
+    const double inv_w = 1.0 / ((double)(k1 - k0) * a.df);
+    const double sr = (double)(rho1.x - rho_n.x) * inv_w, si = (double)(rho1.y - rho_n.y) * inv_w;
+    const int64_t m = (int64_t)a.n_bins + 1;
+    const double* T = r.prefix;
+    const double a0r = T[kcut] - T[k0], a0i = T[m + kcut] - T[m + k0];
+    const double ofs = (double)k0 * a.df;
+    const double a1r = (T[2 * m + kcut] - T[2 * m + k0]) - ofs * a0r;
+    const double a1i = (T[3 * m + kcut] - T[3 * m + k0]) - ofs * a0i;
+    zr64 += (double)rho_n.x * a0r - (double)rho_n.y * a0i + sr * a1r - si * a1i;
+    zi64 += (double)rho_n.x * a0i + (double)rho_n.y * a0r + sr * a1i + si * a1r;
+  }
   const double z = ms.amp * hypot(zr64, zi64);
   const double H = ms.amp * ms.amp * a.tfold[kcut];
   double ll;
@@ -210,6 +251,7 @@ mbis_status rb_fail(mbis_ctx* c, mbis_status st, const std::string& msg) {
 void rb_free(mbis_ctx* c) {
   rfree(c->d_rb_edges);
   rfree(c->d_rb_rec);
+  rfree(c->d_rb_q);
   rfree(c->d_rb_prefix);
   c->rb_n = 0;
 }
@@ -260,7 +302,8 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
   cudaError_t e = cudaMalloc(&d_w, sizeof(double) * 4 * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_prefix, sizeof(double) * 4 * ((size_t)n + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_edges, sizeof(int32_t) * (n_rb + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_rec, sizeof(RbRec) * (n_rb + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_rec, sizeof(float4) * kEdgeVec * (n_rb + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_q, sizeof(float2) * n_rb);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_rb_edges, edges, sizeof(int32_t) * (n_rb + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     rb_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_cfold64, c->d_basis, pc0, c->f_lo, c->df, d_w);
@@ -284,7 +327,8 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
   if (e == cudaSuccess) {
     rb_summary_kernel<<<(n_rb + 1 + 127) / 128, 128, 0, s>>>(n_rb, n, c->d_rb_edges, c->d_rb_prefix, c->f_lo,
                                                              c->df, 1.0 / c->rb_scale,
-                                                             static_cast<RbRec*>(c->d_rb_rec));
+                                                             static_cast<float4*>(c->d_rb_rec),
+                                                             static_cast<float2*>(c->d_rb_q));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -313,13 +357,15 @@ mbis_status mbis_rb_loglike(mbis_ctx* c, int64_t n, const double* theta, double*
   RbArgs r;
   r.la = make_like_args(c, n, theta, loglike);
   r.n_rb = c->rb_n;
-  r.rec = static_cast<const RbRec*>(c->d_rb_rec);
+  r.rec = static_cast<const float4*>(c->d_rb_rec);
+  r.q = static_cast<const float2*>(c->d_rb_q);
+  r.edges = c->d_rb_edges;
   r.prefix = c->d_rb_prefix;
   r.scale = c->rb_scale;
   for (int j = 0; j < kNumBasis; ++j) r.C0[j] = c->rb_C0[j];
   r.cst0 = c->rb_cst0;
   // the records in shared memory when they fit (a few CTAs per SM still), else through L1
-  const size_t sh = sizeof(RbRec) * (size_t)(c->rb_n + 1);
+  const size_t sh = sizeof(float4) * kEdgeVec * (size_t)(c->rb_n + 1);
   r.rec_smem = sh <= kRbSmemMax ? 1 : 0;
   if (r.rec_smem && sh > 48 * 1024) {
     static bool attr = false;
