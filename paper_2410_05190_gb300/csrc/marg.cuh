@@ -18,6 +18,9 @@ namespace mbis {
 
 // Gauss-Legendre nodes/weights on [-1, 1]: x48, w48, x8, w8 (host fills, device reads)
 constexpr int kGL48 = 48, kGL8 = 8;
+// a range of the mixed-precision distance rule whose largest log-integrand lies this far below
+// the window's is left out
+constexpr float kDistSkip = 45.0f;
 constexpr int kGLSize = 2 * kGL48 + 2 * kGL8;
 
 #ifdef __CUDACC__
@@ -86,12 +89,31 @@ __device__ __forceinline__ double log_distance_marginal(double Z, double H, doub
   return L.value();
 }
 
-// ln I0(x) - x in FP32 (x >= 0): slowly varying, so FP32 keeps its absolute accuracy
+// ln I0(x) - x in FP32 (x >= 0), slowly varying, so FP32 keeps its absolute accuracy.  The
+// polynomial approximations of Abramowitz & Stegun 9.8.1 (x < 3.75: I0 in (x/3.75)^2) and
+// 9.8.2 (x >= 3.75: x^(1/2) e^(-x) I0(x) in 3.75/x) give |error| < 5e-7 in the logarithm
+// over all x >= 0, with one fast logarithm and no division.
 __device__ __forceinline__ float log_i0_minus_x_f(float x) {
-  if (x < 15.0f) return logf(cyl_bessel_i0f(x)) - x;
-  const float t = 1.0f / (8.0f * x);
-  const float s = t * (1.0f + t * (4.5f + t * (37.5f + t * 459.375f)));
-  return -0.5f * logf(6.28318530717958647692f * x) + log1pf(s);
+  if (x < 3.75f) {
+    const float t = x * x * (1.0f / 14.0625f);
+    const float p =
+        fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, 0.0045813f, 0.0360768f), 0.2659732f), 1.2067492f), 3.0899424f),
+                     3.5156229f),
+             1.0f);
+    return __logf(p) - x;
+  }
+  const float t = __fdividef(3.75f, x);
+  const float p = fmaf(
+      t,
+      fmaf(t,
+           fmaf(t,
+                fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, 0.00392377f, -0.01647633f), 0.02635537f), -0.02057706f),
+                             0.00916281f),
+                     -0.00157565f),
+                0.00225319f),
+           0.01328592f),
+      0.39894228f);
+  return __logf(p * rsqrtf(x));
 }
 
 struct LogSumExpF {
@@ -106,21 +128,21 @@ struct LogSumExpF {
   }
 };
 
-// One composite rule over [lo, hi] (offsets from the reference point s_ref) with the nodes
-// evaluated in FP32 as differences G(s) - G(s_ref): u - u_ref = u_ref expm1(s - s_ref)
-// keeps the differences small, so FP32 carries ~1e-6 relative accuracy on each weight.
+// G(s) - G(s_ref) at the offset d = s - s_ref, in FP32: u - u_ref = u_ref expm1(d) keeps the
+// differences small, so FP32 carries ~1e-6 relative accuracy on each weight.
+__device__ __forceinline__ float dist_node_g(float d, float Z, float H, float u_ref, float phi_ref) {
+  const float du = u_ref * expm1f(d);
+  const float u = u_ref + du;
+  return Z * du - 0.5f * H * du * (2.0f * u_ref + du) - 3.0f * d + (log_i0_minus_x_f(Z * u) - phi_ref);
+}
+
+// One composite rule over [lo, hi] (offsets from the reference point s_ref).
 __device__ __forceinline__ void dist_rule_f(LogSumExpF& L, float lo, float hi, int panels, int n, const float* x,
                                             const float* w, float Z, float H, float u_ref, float phi_ref) {
   const float h = (hi - lo) * (1.0f / (float)panels), half = 0.5f * h;
   for (int p = 0; p < panels; ++p) {
     const float mid = fmaf((float)p + 0.5f, h, lo);
-    for (int i = 0; i < n; ++i) {
-      const float d = fmaf(half, __ldg(x + i), mid);  // s - s_ref
-      const float du = u_ref * expm1f(d);
-      const float u = u_ref + du;
-      const float g = Z * du - 0.5f * H * du * (2.0f * u_ref + du) - 3.0f * d + (log_i0_minus_x_f(Z * u) - phi_ref);
-      L.add(g, half * __ldg(w + i));
-    }
+    for (int i = 0; i < n; ++i) L.add(dist_node_g(fmaf(half, __ldg(x + i), mid), Z, H, u_ref, phi_ref), half * __ldg(w + i));
   }
 }
 #endif
@@ -176,8 +198,18 @@ __device__ __forceinline__ double log_distance_marginal_mixed(double Z, double H
   LogSumExpF L;
   if (window) {
     dist_rule_f(L, wlo - r_ref, whi - r_ref, 1, kGL48, x48, w48, Zf, Hf, uf, phi_ref);
-    if (wlo > 0.0f) dist_rule_f(L, -r_ref, wlo - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
-    if (whi < span) dist_rule_f(L, whi - r_ref, span - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
+    // Outside the window: G has at most one local maximum (G' = f(x) - 3 with
+    // f(x) = x I1(x)/I0(x) - (H/Z^2) x^2 rising then falling in x = Z e^s), so a range that
+    // does not hold it takes its largest value at its ends.  A range whose ends lie more than
+    // kDistSkip below the window's largest node is left out: its share of the integral is
+    // below e^-40.  (Were the maximum inside the range, the window's nearest end would be
+    // within kDistSkip of the window's largest node and the range would be summed.)
+    if (wlo > 0.0f) {
+      const float g_end = fmaxf(dist_node_g(-r_ref, Zf, Hf, uf, phi_ref), dist_node_g(wlo - r_ref, Zf, Hf, uf, phi_ref));
+      if (g_end > L.m - kDistSkip) dist_rule_f(L, -r_ref, wlo - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
+    }
+    if (whi < span && dist_node_g(whi - r_ref, Zf, Hf, uf, phi_ref) > L.m - kDistSkip)
+      dist_rule_f(L, whi - r_ref, span - r_ref, 4, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
   } else {
     dist_rule_f(L, -r_ref, span - r_ref, 24, kGL8, x8, w8, Zf, Hf, uf, phi_ref);
   }
