@@ -154,10 +154,11 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   {
     PhaseCoeffs pc;
     if (valid) {
-      const MassSetup ms = mass_setup(par[kMc], par[kQ], par[kDl]);
-      pc = phase_coeffs_a(par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], ms.a, ms.la, ms.a13);
-      kcut = live_bins_m(ms.m_sec, a.f_lo, a.df, a.n_bins);
-      A = ms.amp;
+      const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], par[kDl],
+                                          a.f_lo, a.df, a.n_bins);
+      pc = ss.pc;
+      kcut = ss.kcut;
+      A = ss.amp;
     } else {
 #pragma unroll
       for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;

@@ -185,10 +185,11 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     stp[d] = 0;
   }
   if (valid) {
-    const MassSetup ms = mass_setup(par[kMc], par[kQ], par[kDl]);
-    pc = phase_coeffs_a(par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], ms.a, ms.la, ms.a13);
-    kcut = live_bins_m(ms.m_sec, a.f_lo, a.df, a.n_bins);
-    amp = ms.amp;
+    const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], par[kDl],
+                                        a.f_lo, a.df, a.n_bins);
+    pc = ss.pc;
+    kcut = ss.kcut;
+    amp = ss.amp;
     if (a.fold) {
       pmag[0] = 1.f;
       H = amp * amp * a.tfold[kcut];

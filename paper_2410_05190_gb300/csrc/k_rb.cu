@@ -154,9 +154,11 @@ __global__ void __launch_bounds__(kRbThreads, 3) rb_loglike_kernel(RbArgs r) {
     return;
   }
   const double dl = (a.marg & MBIS_MARG_DISTANCE) ? 1.0 : par[kDl];
-  const MassSetup ms = mass_setup(par[kMc], par[kQ], dl);
-  const PhaseCoeffs pc = phase_coeffs_a(par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], ms.a, ms.la, ms.a13);
-  const int32_t kcut = live_bins_m(ms.m_sec, a.f_lo, a.df, a.n_bins);
+  const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], dl, a.f_lo,
+                                      a.df, a.n_bins);
+  const PhaseCoeffs& pc = ss.pc;
+  const int32_t kcut = ss.kcut;
+  const double amp = ss.amp;
   float dC[kNumBasis];
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) dC[j] = (float)(pc.C[j] - r.C0[j]);
@@ -222,15 +224,15 @@ __global__ void __launch_bounds__(kRbThreads, 3) rb_loglike_kernel(RbArgs r) {
     zr64 += (double)rho_n.x * a0r - (double)rho_n.y * a0i + sr * a1r - si * a1i;
     zi64 += (double)rho_n.x * a0i + (double)rho_n.y * a0r + sr * a1i + si * a1r;
   }
-  const double z = ms.amp * hypot(zr64, zi64);
-  const double H = ms.amp * ms.amp * a.tfold[kcut];
+  const double z = amp * hypot(zr64, zi64);
+  const double H = amp * amp * a.tfold[kcut];
   double ll;
   if (a.marg == MBIS_MARG_PHASE)
     ll = log_i0(z) - 0.5 * H;
   else if (a.marg == (MBIS_MARG_PHASE | MBIS_MARG_DISTANCE))
     ll = log_distance_marginal_mixed(z, H, a.dist, a.glf);  // as the fused kernel
   else
-    ll = ms.amp * zr64 - 0.5 * H;  // no marginalisation: Re (d|h) - <h|h> / 2
+    ll = amp * zr64 - 0.5 * H;  // no marginalisation: Re (d|h) - <h|h> / 2
   a.out[s] = ll;
 }
 

@@ -45,50 +45,58 @@ MBIS_HD double total_mass_seconds(double mc, double q) {
   return mc * kTsun * pow(1.0 + q, 1.2) * pow(q, -0.6);
 }
 
+// The PN phase coefficients' mass-ratio and spin factors (eta, delta = (m1 - m2) / M, chi_s,
+// chi_a): phi2, phi3, phi4, the 2.5PN factor c5 (phi5(v) = c5 (1 + 3 ln v)), the 3PN constant
+// a6 (phi6(v) = a6 - (6848/21) ln v) and phi7.
+struct PNTerms {
+  double phi2, phi3, phi4, c5, a6, phi7;
+};
+
+MBIS_HD PNTerms pn_terms(double eta, double dm, double xs, double xa) {
+  const double e2 = eta * eta, e3 = e2 * eta, pi2 = kPi * kPi;
+  constexpr double kLn4 = 1.3862943611198906188344642429164;
+  PNTerms t;
+  t.phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+  t.phi3 = -16.0 * kPi + 113.0 / 3.0 * dm * xa + (113.0 / 3.0 - 76.0 / 3.0 * eta) * xs;
+  t.phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * e2 +
+           (-405.0 / 8.0 + 200.0 * eta) * xa * xa - 405.0 / 4.0 * dm * xa * xs +
+           (-405.0 / 8.0 + 5.0 / 2.0 * eta) * xs * xs;
+  t.c5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) + dm * (-732985.0 / 2268.0 + 140.0 / 9.0 * eta) * xa +
+         (-732985.0 / 2268.0 + 24260.0 / 81.0 * eta + 340.0 / 9.0 * e2) * xs;
+  t.a6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * (kEulerGamma + kLn4) +
+         (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta + 76055.0 / 1728.0 * e2 - 127825.0 / 1296.0 * e3 +
+         kPi * (2270.0 / 3.0 * dm * xa + (2270.0 / 3.0 - 520.0 * eta) * xs) +
+         (75515.0 / 144.0 - 8225.0 / 18.0 * eta) * dm * xa * xs +
+         (75515.0 / 288.0 - 263245.0 / 252.0 * eta - 480.0 * e2) * xa * xa +
+         (75515.0 / 288.0 - 232415.0 / 504.0 * eta + 1255.0 / 9.0 * e2) * xs * xs;
+  t.phi7 = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * e2) +
+           (-25150083775.0 / 3048192.0 + 10566655595.0 / 762048.0 * eta - 1042165.0 / 3024.0 * e2 +
+            5345.0 / 36.0 * e3) * xs +
+           dm * (-25150083775.0 / 3048192.0 + 26804935.0 / 6048.0 * eta - 1985.0 / 48.0 * e2) * xa;
+  return t;
+}
+
 // a = pi M (M the total mass in seconds), la = ln a, a13 = a^(1/3), taken by the caller
 MBIS_HD PhaseCoeffs phase_coeffs_a(double q, double chi1, double chi2, double tc, double phic, double a, double la,
                                    double a13) {
   const double eta = q / ((1.0 + q) * (1.0 + q));
   const double dm = (q - 1.0) / (q + 1.0);  // (m1 - m2) / M
-  const double xs = 0.5 * (chi1 + chi2), xa = 0.5 * (chi1 - chi2);
-  const double e2 = eta * eta, e3 = e2 * eta, pi2 = kPi * kPi;
-
-  const double phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
-  const double phi3 = -16.0 * kPi + 113.0 / 3.0 * dm * xa + (113.0 / 3.0 - 76.0 / 3.0 * eta) * xs;
-  const double phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * e2 +
-                      (-405.0 / 8.0 + 200.0 * eta) * xa * xa - 405.0 / 4.0 * dm * xa * xs +
-                      (-405.0 / 8.0 + 5.0 / 2.0 * eta) * xs * xs;
-  // 2.5PN: phi5(v) = c5 (1 + 3 ln v)
-  const double c5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) +
-                    dm * (-732985.0 / 2268.0 + 140.0 / 9.0 * eta) * xa +
-                    (-732985.0 / 2268.0 + 24260.0 / 81.0 * eta + 340.0 / 9.0 * e2) * xs;
-  // 3PN: phi6(v) = a6 - (6848/21) ln v
-  const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 -
-                    6848.0 / 21.0 * (kEulerGamma + log(4.0)) +
-                    (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta + 76055.0 / 1728.0 * e2 -
-                    127825.0 / 1296.0 * e3 + kPi * (2270.0 / 3.0 * dm * xa + (2270.0 / 3.0 - 520.0 * eta) * xs) +
-                    (75515.0 / 144.0 - 8225.0 / 18.0 * eta) * dm * xa * xs +
-                    (75515.0 / 288.0 - 263245.0 / 252.0 * eta - 480.0 * e2) * xa * xa +
-                    (75515.0 / 288.0 - 232415.0 / 504.0 * eta + 1255.0 / 9.0 * e2) * xs * xs;
-  const double phi7 = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * e2) +
-                      (-25150083775.0 / 3048192.0 + 10566655595.0 / 762048.0 * eta - 1042165.0 / 3024.0 * e2 +
-                       5345.0 / 36.0 * e3) * xs +
-                      dm * (-25150083775.0 / 3048192.0 + 26804935.0 / 6048.0 * eta - 1985.0 / 48.0 * e2) * xa;
+  const PNTerms t = pn_terms(eta, dm, 0.5 * (chi1 + chi2), 0.5 * (chi1 - chi2));
 
   // v = (a f)^(1/3) with a = pi M;  v^n = a^(n/3) f^(n/3);  3 ln v = ln a + ln f
   const double a23 = a13 * a13;
   const double pre = 3.0 / (128.0 * eta) / kTwoPi;  // turns
   PhaseCoeffs pc;
   pc.C[0] = pre / (a23 * a23 * a13);                 // a^(-5/3)   f^(-5/3)
-  pc.C[1] = pre * phi2 / a;                          // a^(-1)     f^(-1)
-  pc.C[2] = pre * phi3 / a23;                        // a^(-2/3)   f^(-2/3)
-  pc.C[3] = pre * phi4 / a13;                        // a^(-1/3)   f^(-1/3)
-  pc.C[4] = pre * c5;                                // ln f
-  pc.C[5] = pre * a13 * (a6 - 6848.0 / 63.0 * la);   // f^(1/3)
+  pc.C[1] = pre * t.phi2 / a;                        // a^(-1)     f^(-1)
+  pc.C[2] = pre * t.phi3 / a23;                      // a^(-2/3)   f^(-2/3)
+  pc.C[3] = pre * t.phi4 / a13;                      // a^(-1/3)   f^(-1/3)
+  pc.C[4] = pre * t.c5;                              // ln f
+  pc.C[5] = pre * a13 * (t.a6 - 6848.0 / 63.0 * la); // f^(1/3)
   pc.C[6] = -pre * a13 * (6848.0 / 63.0);            // f^(1/3) ln f
-  pc.C[7] = pre * phi7 * a23;                        // f^(2/3)
+  pc.C[7] = pre * t.phi7 * a23;                      // f^(2/3)
   pc.C[8] = tc;                                      // f
-  pc.cst = -phic / kTwoPi - 0.125 + pre * c5 * (1.0 + la);
+  pc.cst = -phic / kTwoPi - 0.125 + pre * t.c5 * (1.0 + la);
   return pc;
 }
 
@@ -178,35 +186,88 @@ MBIS_HD void antenna(const double* x, const double* y, double ra, double dec, do
   *fc = xX * xY - yX * yY;
 }
 
-// Mass-dependent set-up with few FP64 operations (the GB300 runs FP64 at ~1/64 of FP32):
-// a power or root is seeded in FP32 and refined by one FP64 Newton step, which squares the
-// seed's ~1e-7 relative error; only ln(pi M) is an FP64 library call.
-//   M = Mc T_sun u^(3/5), u = (1 + q)^2 / q:  y = u^(3/5) solves y^5 = u^3
-//   a = pi M, a^(1/3) solves y^3 = a
-//   A = K (Mc T_sun)^(5/6) / d_L:  y = x^(5/6) solves y^6 = x^5
-// (log L of a poor sample can reach 10^4 in magnitude, so A and H keep ~1e-15 accuracy).
-struct MassSetup {
-  double m_sec, a, la, a13, amp;
+// 1/x to FP64 accuracy from an FP32 reciprocal refined by two Newton steps (four FMA; x and
+// 1/x inside the FP32 range).  A library FP64 division costs about twice as much, and the
+// GB300 runs FP64 at ~1/64 of FP32.
+MBIS_HD float rcp_f32(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+
+MBIS_HD double rcp_refined(double x) {
+  double r = (double)rcp_f32((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Per-sample set-up of the mixed-precision likelihood kernels: amplitude, phase coefficients
+// (the same series as phase_coeffs_a, to FP64 rounding) and ISCO cut, with four reciprocals
+// and one FP64 logarithm.  A power or root is seeded in FP32 and refined by one Newton step
+// written as a correction, y -= (y^n - x) / (n y^(n-1)), whose small numerator makes an FP32
+// divisor enough: the seed's ~1e-7 relative error squares.
+//   M = Mc T_sun u^(3/5), u = (1 + q)^2 / q = q + 2 + 1/q = 1/eta:  y = u^(3/5) solves y^5 = u^3
+//   a = pi M, a^(1/3) solves y^3 = a;  a^(-n/3) from 1/a and a^(1/3)
+//   A = K (Mc T_sun)^(5/6) / d_L:  z = x^(5/6) solves z^6 = x^5
+//   f_isco = 1 / (6^(3/2) a)
+// (log L of a poor sample can reach 10^4 in magnitude, so A and H keep ~1e-14 accuracy.)
+struct SampleSetup {
+  PhaseCoeffs pc;
+  double amp;    // A at d_L = dl_mpc
+  int32_t kcut;  // grid points f_lo + k df strictly below the ISCO
 };
 
-MBIS_HD MassSetup mass_setup(double mc, double q, double dl_mpc) {
-  MassSetup o;
-  const double u = (1.0 + q) * (1.0 + q) / q, u3 = u * u * u;
+MBIS_HD SampleSetup sample_setup(double mc, double q, double chi1, double chi2, double tc, double phic,
+                                 double dl_mpc, double f_lo, double df, int32_t n_bins) {
+  SampleSetup o;
+  const double w = rcp_refined(1.0 + q);
+  const double u = q + 2.0 + rcp_refined(q), u3 = u * u * u;
+  const double eta = q * w * w, dm = (q - 1.0) * w;
   double y = (double)powf((float)u, 0.6f);
-  const double y4 = (y * y) * (y * y);
-  y = 0.8 * y + u3 / (5.0 * y4);
-  o.m_sec = mc * kTsun * y;
-  o.a = kPi * o.m_sec;
-  o.la = log(o.a);
-  double c = (double)cbrtf((float)o.a);
-  c = (2.0 * c + o.a / (c * c)) * (1.0 / 3.0);
-  o.a13 = c;
-  // (Mc T_sun)^(5/6) solves y^6 = x^5
-  const double x = mc * kTsun, x5 = (x * x) * (x * x) * x;
+  {
+    const double y2 = y * y, y4 = y2 * y2;
+    y -= (y4 * y - u3) * (0.2 * (double)rcp_f32((float)y4));
+  }
+  const double a = kPi * kTsun * mc * y;
+  const double la = log(a);
+  double a13 = (double)cbrtf((float)a);
+  {
+    const double c2 = a13 * a13;
+    a13 -= (c2 * a13 - a) * ((1.0 / 3.0) * (double)rcp_f32((float)c2));
+  }
+  const double a23 = a13 * a13, inv_a = rcp_refined(a);
+  const double x = mc * kTsun, x2 = x * x, x5 = x2 * x2 * x;
   double z = (double)powf((float)x, 5.0f / 6.0f);
-  const double z5 = (z * z) * (z * z) * z;
-  z = (5.0 / 6.0) * z + x5 / (6.0 * z5);
-  o.amp = 0.45643546458763845 * 0.46619407703541166 * z / (dl_mpc * kMpcSeconds);
+  {
+    const double z2 = z * z, z5 = z2 * z2 * z;
+    z -= (z5 * z - x5) * ((1.0 / 6.0) * (double)rcp_f32((float)z5));
+  }
+  o.amp = 0.45643546458763845 * 0.46619407703541166 * z * rcp_refined(dl_mpc * kMpcSeconds);
+
+  const PNTerms t = pn_terms(eta, dm, 0.5 * (chi1 + chi2), 0.5 * (chi1 - chi2));
+  const double pre = (3.0 / (256.0 * kPi)) * u;  // 3 / (128 eta) / (2 pi), turns
+  const double pa = pre * inv_a;
+  o.pc.C[0] = pa * inv_a * a13;                       // a^(-5/3)
+  o.pc.C[1] = pa * t.phi2;                            // a^(-1)
+  o.pc.C[2] = pa * t.phi3 * a13;                      // a^(-2/3)
+  o.pc.C[3] = pa * t.phi4 * a23;                      // a^(-1/3)
+  o.pc.C[4] = pre * t.c5;                             // ln f
+  o.pc.C[5] = pre * a13 * (t.a6 - 6848.0 / 63.0 * la);
+  o.pc.C[6] = -pre * a13 * (6848.0 / 63.0);
+  o.pc.C[7] = pre * t.phi7 * a23;
+  o.pc.C[8] = tc;
+  o.pc.cst = phic * (-1.0 / kTwoPi) - 0.125 + pre * t.c5 * (1.0 + la);
+
+  // the cut: an FP32 estimate of ceil((f_isco - f_lo) / df), then exact FP64 steps to the
+  // first grid point at or above f_isco
+  const double fi = inv_a * (1.0 / 14.696938456699067);
+  const float kf = ceilf((float)(fi - f_lo) * rcp_f32((float)df));
+  int32_t k = !(kf > 0.0f) ? 0 : (kf >= (float)n_bins ? n_bins : (int32_t)kf);
+  while (k > 0 && f_lo + (double)(k - 1) * df >= fi) --k;
+  while (k < n_bins && f_lo + (double)k * df < fi) ++k;
+  o.kcut = k;
   return o;
 }
 
