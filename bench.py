@@ -42,6 +42,9 @@ UNIT = "likelihood evals/s"
 SFU_PER_SM_PER_CLK = 16        # MUFU results per SM per clock (Blackwell)
 SFU_PER_BIN = 2                # one sine and one cosine per (sample, bin)
 N_SM = 152
+# dram__bytes_read.sum + dram__bytes_write.sum of one loglike_mixed_fold_kernel launch at this
+# workload (2^20 samples), from the full ncu capture in profiles/loglike_mixed_fold_kernel_bns.md
+FOLD_TRAFFIC_BYTES = 44_004_864 + 120_576
 
 
 def peaks():
@@ -281,7 +284,7 @@ def run_gpu(args, rank, world):
             "fisher_proposal_efficiency": {"median": statistics.median(eff), "ess_median": statistics.median(ess),
                                            "seconds_to_1e4_at_this_efficiency_median": statistics.median(per_event_s)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbin/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": FOLD_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
                          "kernel": "loglike_mixed_fold_kernel", "launch_ms": statistics.mean(like_ms),
                          "note": "peak = 152 SM x 16 MUFU/clk x sm_max_mhz / 2 MUFU per (sample, bin)"},
             "gpu_launches": launches_per_step * args.steps,
