@@ -127,6 +127,20 @@ MBIS_HD double basis(int j, double f) {
   }
 }
 
+// all nine basis functions at f, each bit-identical to basis(j, f)
+MBIS_HD void basis_all(double f, double* b) {
+  const double c = cbrt(f), lf = log(f);
+  b[0] = 1.0 / (f * c * c);
+  b[1] = 1.0 / f;
+  b[2] = 1.0 / (c * c);
+  b[3] = 1.0 / c;
+  b[4] = lf;
+  b[5] = c;
+  b[6] = c * lf;
+  b[7] = c * c;
+  b[8] = f;
+}
+
 // d basis_j / df
 MBIS_HD double basis_deriv(int j, double f) {
   const double c = cbrt(f);

@@ -12,6 +12,9 @@
 // keeps ~1e-7-turn resolution.  max|C_j| is bounded over the prior box by the caller.
 #include <algorithm>
 #include <cmath>
+#include <list>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -19,26 +22,33 @@
 namespace mbis {
 namespace {
 
-// solve the (n x n) system A x = b in place (partial pivoting)
-void solve_dense(int n, double* A, double* b) {
+// LU factorisation with partial pivoting of the (n x n) matrix A in place (whole rows swapped,
+// piv: the swap of each step), then solves for any number of right-hand sides
+void lu_factor(int n, double* A, int* piv) {
   for (int c = 0; c < n; ++c) {
-    int piv = c;
+    int p = c;
     for (int r = c + 1; r < n; ++r)
-      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
-    if (piv != c) {
-      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
-      std::swap(b[c], b[piv]);
-    }
+      if (std::fabs(A[r * n + c]) > std::fabs(A[p * n + c])) p = r;
+    piv[c] = p;
+    if (p != c)
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[p * n + k]);
     for (int r = c + 1; r < n; ++r) {
       const double f = A[r * n + c] / A[c * n + c];
-      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
-      b[r] -= f * b[c];
+      A[r * n + c] = f;
+      for (int k = c + 1; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
     }
   }
+}
+
+void lu_solve(int n, const double* LU, const int* piv, double* b) {
+  for (int c = 0; c < n; ++c)
+    if (piv[c] != c) std::swap(b[c], b[piv[c]]);
+  for (int c = 0; c < n; ++c)
+    for (int r = c + 1; r < n; ++r) b[r] -= LU[r * n + c] * b[c];
   for (int c = n - 1; c >= 0; --c) {
     double s = b[c];
-    for (int k = c + 1; k < n; ++k) s -= A[c * n + k] * b[k];
-    b[c] = s / A[c * n + c];
+    for (int k = c + 1; k < n; ++k) s -= LU[c * n + k] * b[k];
+    b[c] = s / LU[c * n + c];
   }
 }
 
@@ -46,6 +56,9 @@ struct Fit {
   AnchorBlock blk;
   double err_bound, r_bound;
 };
+
+// The basis functions with a remainder (B_8 = f is linear)
+constexpr int kRemBasis = kNumBasis - 1;
 
 Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
   constexpr int D = kRemDeg + 1;
@@ -56,60 +69,73 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
   b.kc = k0 + (S - 1) / 2;
   b.pad = 0;
   const double fc = in.f_lo + (double)b.kc * in.df;
+  basis_all(fc, b.B);
   for (int j = 0; j < kNumBasis; ++j) {
-    b.B[j] = basis(j, fc);
     b.dB[j] = basis_deriv(j, fc) * in.df;
     b.Bh[j] = (float)b.B[j];
     b.Bl[j] = (float)(b.B[j] - (double)b.Bh[j]);
     b.dBh[j] = (float)b.dB[j];
     b.dBl[j] = (float)(b.dB[j] - (double)b.dBh[j]);
   }
+  // remainders of every basis function beyond its tangent at fc, at offset w
+  auto rem_all = [&](double w, double* r) {
+    double v[kNumBasis];
+    basis_all(fc + w * in.df, v);
+    for (int j = 0; j < kRemBasis; ++j) r[j] = v[j] - b.B[j] - w * b.dB[j];
+  };
   const double wa = (double)(k0 - b.kc), wb = (double)(k0 + S - 1 - b.kc);
   const double h = std::max(1.0, std::max(std::fabs(wa), std::fabs(wb)));
   const double mid = 0.5 * (wa + wb), half = std::max(0.5 * (wb - wa), 0.5);
-  out.err_bound = 0.0;
-  out.r_bound = 0.0;
-  for (int j = 0; j < kNumBasis - 1; ++j) {
-    auto rem = [&](double w) { return basis(j, fc + w * in.df) - b.B[j] - w * b.dB[j]; };
-    // interpolate at Chebyshev points of the block, monomials in u = w / h
-    double V[D * D], y[D];
-    for (int i = 0; i < D; ++i) {
-      const double w = mid + half * std::cos(kPi * (i + 0.5) / D);
-      const double u = w / h;
-      double p = 1.0;
-      for (int m = 0; m < D; ++m) {
-        V[i * D + m] = p;
-        p *= u;
-      }
-      y[i] = rem(w);
+  // interpolate at Chebyshev points of the block, monomials in u = w / h: one Vandermonde
+  // factorisation serves every basis function
+  double V[D * D], y[kRemBasis][D];
+  int piv[D];
+  for (int i = 0; i < D; ++i) {
+    const double w = mid + half * std::cos(kPi * (i + 0.5) / D);
+    const double u = w / h;
+    double p = 1.0;
+    for (int m = 0; m < D; ++m) {
+      V[i * D + m] = p;
+      p *= u;
     }
-    solve_dense(D, V, y);
+    double r[kRemBasis];
+    rem_all(w, r);
+    for (int j = 0; j < kRemBasis; ++j) y[j][i] = r[j];
+  }
+  lu_factor(D, V, piv);
+  for (int j = 0; j < kRemBasis; ++j) {
+    lu_solve(D, V, piv, y[j]);
     double hm = 1.0;
     for (int m = 0; m < D; ++m) {
-      b.E[j][m] = (float)(y[m] / hm);
+      b.E[j][m] = (float)(y[j][m] / hm);
       hm *= h;
     }
-    // error of the FP32-stored polynomial on the block's bins (all, or 257 evenly spaced)
-    double emax = 0.0, rmax = 0.0;
-    const int32_t npts = std::min<int32_t>(S, 257);
-    for (int32_t i = 0; i < npts; ++i) {
-      const int32_t kk = (npts == S) ? k0 + i : k0 + (int32_t)std::llround((double)i * (S - 1) / (npts - 1));
-      const double w = (double)(kk - b.kc);
+  }
+  // error of the FP32-stored polynomials on the block's bins (all, or 257 evenly spaced)
+  double emax[kRemBasis] = {}, rmax[kRemBasis] = {};
+  const int32_t npts = std::min<int32_t>(S, 257);
+  for (int32_t i = 0; i < npts; ++i) {
+    const int32_t kk = (npts == S) ? k0 + i : k0 + (int32_t)std::llround((double)i * (S - 1) / (npts - 1));
+    const double w = (double)(kk - b.kc);
+    double r[kRemBasis];
+    rem_all(w, r);
+    for (int j = 0; j < kRemBasis; ++j) {
       double p = 0.0;
       for (int m = D - 1; m >= 0; --m) p = p * w + (double)b.E[j][m];
-      const double r = rem(w);
-      emax = std::max(emax, std::fabs(p - r));
-      rmax = std::max(rmax, std::fabs(r));
+      emax[j] = std::max(emax[j], std::fabs(p - r[j]));
+      rmax[j] = std::max(rmax[j], std::fabs(r[j]));
     }
-    out.err_bound += in.cmax[j] * emax;
-    out.r_bound += in.cmax[j] * rmax;
+  }
+  out.err_bound = 0.0;
+  out.r_bound = 0.0;
+  for (int j = 0; j < kRemBasis; ++j) {
+    out.err_bound += in.cmax[j] * emax[j];
+    out.r_bound += in.cmax[j] * rmax[j];
   }
   return out;
 }
 
-}  // namespace
-
-std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
+std::vector<AnchorBlock> build_plan(const PlanInput& in) {
   std::vector<AnchorBlock> blocks;
   int32_t k0 = 0;
   int32_t guess = 64;
@@ -151,6 +177,40 @@ std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
     guess = good;
   }
   return blocks;
+}
+
+bool same_input(const PlanInput& a, const PlanInput& b) {
+  if (a.f_lo != b.f_lo || a.df != b.df || a.n_bins != b.n_bins || a.tol_turns != b.tol_turns ||
+      a.rmax_turns != b.rmax_turns || a.max_block != b.max_block)
+    return false;
+  for (int j = 0; j < kNumBasis; ++j)
+    if (a.cmax[j] != b.cmax[j]) return false;
+  return true;
+}
+
+// Plans of the most recent inputs, shared by every context of the process: a plan depends
+// only on the grid, the coefficient bounds of the prior box and the tolerances, which the
+// contexts of one analysis (events on one grid, the served stream's requests) repeat.
+constexpr size_t kPlanCacheSize = 8;
+std::mutex g_plan_mutex;
+std::list<std::pair<PlanInput, std::vector<AnchorBlock>>> g_plans;  // most recent first
+
+}  // namespace
+
+std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in) {
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
+      if (same_input(it->first, in)) {
+        g_plans.splice(g_plans.begin(), g_plans, it);
+        return g_plans.front().second;
+      }
+  }
+  std::vector<AnchorBlock> plan = build_plan(in);
+  std::lock_guard<std::mutex> lock(g_plan_mutex);
+  g_plans.emplace_front(in, plan);
+  if (g_plans.size() > kPlanCacheSize) g_plans.pop_back();
+  return plan;
 }
 
 }  // namespace mbis
