@@ -74,6 +74,26 @@ def test_tiny_loglike_matches_oracle(m, torch, tiny, precision):
         m.mbis_destroy(ctx)
 
 
+def test_cached_anchor_plan_gives_identical_likelihoods(m, torch, tiny):
+    """The anchor plan depends only on the grid, the prior box and the tolerances, and the
+    library keeps recent plans per process: a context whose plan comes from that cache
+    evaluates every sample bit for bit as the context that built it.  A prior box no other
+    test uses makes the first set-up build its plan afresh."""
+    w, spec, ev, th, prop = tiny
+    prop = dict(prop)
+    prop["hi"] = np.array(prop["hi"], dtype=np.float64) * (1.0 + 1e-9)
+    theta, _ = oracle.draw(spec.draw_seed, 0, 2048, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
+    outs = []
+    for _ in range(2):
+        ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+        try:
+            set_metric(m, ctx, prop)
+            outs.append(gpu_loglike(m, torch, ctx, theta))
+        finally:
+            m.mbis_destroy(ctx)
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_reduce_matches_oracle(m, torch, tiny):
     w, spec, ev, th, prop = tiny
     ctx = gpu_context(m, ev, w, spec, th, m.FP64)
