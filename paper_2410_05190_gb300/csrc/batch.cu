@@ -33,7 +33,7 @@ struct mbis_batch {
   uint64_t* d_ctr = nullptr;
   uint64_t* h_ctr = nullptr;  // pinned
   double* h_res = nullptr;    // pinned, 4 per event
-  int32_t grid = 152 * 8;
+  int32_t grid = 152 * kBatchCtasPerSm;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -302,12 +302,12 @@ mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out)
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int cand[] = {2, 4, 6, 8};
+  const int cand[] = {2, 4, 6, kBatchCtasPerSm};
   cudaEvent_t e0, e1;
   B_TRY(cudaEventCreate(&e0));
   B_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_grid = sms * 8;
+  int best_grid = sms * kBatchCtasPerSm;
   for (int c : cand) {
     b->grid = sms * c;
     float t = 0.f;

@@ -17,6 +17,7 @@ constexpr int kMaxP = 11;
 constexpr int kRemDeg = 5;          // degree of the FP32 remainder polynomial per anchor block
 constexpr int kChunk = 512;         // bins per shared-memory chunk of the mixed kernel
 constexpr int kMixedThreads = 128;  // samples per CTA of the mixed kernel
+constexpr int kBatchCtasPerSm = 7;  // resident CTAs per SM of the persistent multi-event launch
 constexpr int kReduceBlocks = 608;  // 4 x 152 SMs
 constexpr int kReduceThreads = 256;
 
