@@ -303,20 +303,29 @@ def ess_buffers(torch, P, batch):
            [torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(4)]
 
 
-def seconds_to_ess(m, torch, evs, precision, target=1e4, batch=1 << 16, max_samples=1 << 26, refine=4):
-    """Wall time of mbis_run_to_ess (refit after each of the first `refine` batches) per event."""
+def seconds_to_ess(m, torch, evs, precision, target=1e4, batch=1 << 16, max_samples=1 << 26, refine=4, rb=None):
+    """Wall time of mbis_run_to_ess (refit after each of the first `refine` batches) per event;
+    rb = (n_sigma, eps_rad): the loop runs on the relative-binning likelihood (bins from
+    mbis_rb_edges about the injection, set-up timed apart)."""
     out = []
     for ev in evs:
         w = ev["w"]
         ctx = make_ctx(m, w, ev, precision)
         try:
             bufs = ess_buffers(torch, len(ev["prop"]["ids"]), batch)
+            extra = {}
+            if rb is not None:
+                t0 = time.perf_counter()
+                edges = m.mbis_rb_edges(ctx, ev["th"], rb[0], rb[1])
+                m.mbis_rb_setup(ctx, ev["th"], edges)
+                m.mbis_rb_use(ctx, True)
+                extra = dict(rb_setup_seconds=time.perf_counter() - t0, coarse_bins=int(len(edges) - 1))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s, nd, nu = m.mbis_run_to_ess(ctx, *bufs, ess_target=target, batch=batch, max_samples=max_samples,
                                           seed=ev["spec"].draw_seed, refine=refine, refine_scale=1.2)
-            out.append(dict(seconds=time.perf_counter() - t0, ess=s["ess"], drawn=nd, used=nu,
-                            reached=bool(s["ess"] >= target)))
+            out.append(dict(seconds=time.perf_counter() - t0, ess=s["ess"], log_z=s["log_z"], drawn=nd, used=nu,
+                            reached=bool(s["ess"] >= target), **extra))
         finally:
             m.mbis_destroy(ctx)
     return out
@@ -641,7 +650,8 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=256):
 def rb_measurement(m, torch, evs, n=1 << 20, n_sigma=5.0, eps=0.3, reps=3):
     """Relative binning on the BNS benchmark event: bins from mbis_rb_edges, likelihood rate
     (CUDA events) against the exact fused kernel on the same draws, and its error: per
-    sample against the exact log L, and in ESS and log Z."""
+    sample against the exact log L, and in ESS and log Z; then the ESS loop run on it
+    (mbis_rb_use) against the exact loop on every resident event."""
     ev = evs[0]
     w = ev["w"]
     ctx = make_ctx(m, w, ev, m.MIXED)
@@ -675,6 +685,13 @@ def rb_measurement(m, torch, evs, n=1 << 20, n_sigma=5.0, eps=0.3, reps=3):
         t_ex, t_rb = statistics.mean(times["exact"]), statistics.mean(times["rb"])
     finally:
         m.mbis_destroy(ctx)
+    loops = {"exact": seconds_to_ess(m, torch, evs, m.MIXED), "rb": seconds_to_ess(m, torch, evs, m.MIXED, rb=(n_sigma, eps))}
+    ess_loop = {k: {"median_s": statistics.median(x["seconds"] for x in v), "max_s": max(x["seconds"] for x in v),
+                    "reached": sum(x["reached"] for x in v), "events": len(v)} for k, v in loops.items()}
+    ess_loop["rb"]["rb_setup_s_median"] = statistics.median(x["rb_setup_seconds"] for x in loops["rb"])
+    ess_loop["abs_dlogz"] = [abs(a["log_z"] - b["log_z"]) for a, b in zip(loops["rb"], loops["exact"])]
+    ess_loop["measured"] = ("mbis_run_to_ess wall time per event to ESS 1e4 (batches of 2^16, 4 refits), exact "
+                            "likelihood vs the relative-binning likelihood through mbis_rb_use")
     return {"workload": "bns_population event 0, 2^20 proposal samples, 128,513 bins, phase + distance marginalised",
             "coarse_bins": int(len(edges) - 1), "bins_rule": f"mbis_rb_edges: {n_sigma} proposal sigmas, {eps} rad per bin",
             "rb": {"value": n / t_rb, "unit": UNIT, "launch_ms": t_rb * 1e3},
@@ -683,7 +700,8 @@ def rb_measurement(m, torch, evs, n=1 << 20, n_sigma=5.0, eps=0.3, reps=3):
             "abs_dlogl_posterior_samples": {"median": float(np.median(err[heavy])), "max": float(err[heavy].max()),
                                             "n": int(heavy.sum())},
             "abs_dlogl_all_in_prior": {"median": float(np.median(err)), "p99": float(np.quantile(err, 0.99))},
-            "ess_exact": se["ess"], "ess_rb": sr["ess"], "dlogz": sr["log_z"] - se["log_z"]}
+            "ess_exact": se["ess"], "ess_rb": sr["ess"], "dlogz": sr["log_z"] - se["log_z"],
+            "seconds_to_1e4_ess": ess_loop}
 
 
 SERVE_SEED = 0x5E12E

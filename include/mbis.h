@@ -448,7 +448,7 @@ mbis_status mbis_credible_levels(int64_t n, int32_t P, const double* theta, cons
  * edges[n_rb] = n_bins; the last edge is the frequency one past the grid), so a likelihood
  * costs n_rb + 1 phase evaluations instead of n_bins; <h|h> stays exact.  Needs a context
  * with a metric, fixed sky and orientation (the folded table) and no time marginalisation;
- * mbis_set_metric drops the set-up.  Allocates its summary data with cudaMalloc.
+ * mbis_set_metric drops the set-up (a proposal refit keeps it).  Allocates its summary data with cudaMalloc.
  * Errors: MBIS_E_STATE, MBIS_E_UNSUPPORTED, MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
 mbis_status mbis_rb_setup(mbis_ctx* ctx, const double* theta0, int32_t n_rb, const int32_t* edges);
 
@@ -457,6 +457,14 @@ mbis_status mbis_rb_setup(mbis_ctx* ctx, const double* theta0, int32_t n_rb, con
  * square of each bin's phase excursion (see mbis_rb_edges).  Errors: MBIS_E_STATE (no
  * set-up), MBIS_E_INVALID, MBIS_E_CUDA. */
 mbis_status mbis_rb_loglike(mbis_ctx* ctx, int64_t n, const double* theta, double* loglike, void* cuda_stream);
+
+/* on != 0: mbis_loglike, and with it the ESS loop (mbis_run_to_ess and the stepwise loop),
+ * evaluates the relative-binning likelihood of the context's set-up instead of the exact
+ * one, so the importance-sampling loop runs on the faster likelihood (Sec. IV); on = 0
+ * restores the exact likelihood.  Proposal refits keep the set-up; mbis_set_metric drops it
+ * and turns this off.  A context with this on cannot join a multi-event batch.
+ * Errors: MBIS_E_STATE (on without a current set-up), MBIS_E_INVALID. */
+mbis_status mbis_rb_use(mbis_ctx* ctx, int32_t on);
 
 /* Coarse bins for relative binning: each bin's largest change of the template's phase
  * relative to the fiducial, over the box theta0 +- n_sigma proposal standard deviations

@@ -134,6 +134,7 @@ def _load():
         "mbis_rb_setup": [p, p, i32, p],
         "mbis_rb_loglike": [p, i64, p, p, p],
         "mbis_rb_edges": [p, p, d, d, i32, p, p],
+        "mbis_rb_use": [p, i32],
         "mbis_tiling_create": [p, p, p, p],
         "mbis_tiling_bank": [p, i64, p, d, i64, i32, p, p],
         "mbis_tiling_templates": [p, p, p, p, p],
@@ -559,6 +560,12 @@ def mbis_rb_setup(ctx, theta0, edges):
 
 def mbis_rb_loglike(ctx, n, theta, loglike, stream=None):
     _check(_lib.mbis_rb_loglike(ctx, n, _dev(theta), _dev(loglike), _stream(stream)), ctx)
+
+
+def mbis_rb_use(ctx, on=True):
+    """Route mbis_loglike and the ESS loop through the relative-binning likelihood (on) or
+    back to the exact one."""
+    _check(_lib.mbis_rb_use(ctx, 1 if on else 0), ctx)
 
 
 def mbis_rb_edges(ctx, theta0, n_sigma, eps_rad, max_bins=65536):

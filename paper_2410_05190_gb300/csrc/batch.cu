@@ -135,6 +135,7 @@ mbis_status check_ctx(const mbis_ctx* c) {
     return berr(MBIS_E_UNSUPPORTED,
                 "mbis_batch: contexts must be mixed precision with fixed extrinsics and phase "
                 "(or phase + distance) marginalisation");
+  if (c->rb_use) return berr(MBIS_E_UNSUPPORTED, "mbis_batch: a context evaluates relative binning (mbis_rb_use)");
   return MBIS_OK;
 }
 

@@ -141,6 +141,8 @@ mbis_status build_tables(mbis_ctx* c) {
   const bool fold = !(sampled(c, kRa) || sampled(c, kDec) || sampled(c, kPsi) || sampled(c, kIota));
   free_tables(c);
   ++c->gen;
+  ++c->tables_gen;
+  c->rb_use = 0;  // the relative-binning set-up belongs to the old tables
   const int32_t n = c->n_bins, nd = c->n_det;
   cudaStream_t s = c->stream;
   double* d_w = nullptr;
@@ -682,6 +684,7 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
   if (n < 0 || (n > 0 && (!theta || !loglike))) return fail(c, MBIS_E_INVALID, "mbis_loglike: bad n or null buffer");
   if ((c->opts.marg & MBIS_MARG_TIME) && c->opts.precision == MBIS_MIXED && c->d_ttiles == nullptr)
     return fail(c, MBIS_E_UNSUPPORTED, "mbis_loglike: mixed-precision time marginalisation needs n_tshift = 128");
+  if (c->rb_use) return mbis_rb_loglike(c, n, theta, loglike, stream);
   const LikeArgs a = make_like_args(c, n, theta, loglike);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (c->opts.precision == MBIS_FP64) {

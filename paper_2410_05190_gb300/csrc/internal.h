@@ -243,6 +243,7 @@ struct mbis_ctx {
   // tables
   int32_t tables_mode = -1;  // -1 none, 1 fold, 0 per-detector
   uint64_t gen = 0;          // bumped whenever the tables or the proposal change (batches re-capture)
+  uint64_t tables_gen = 0;   // bumped whenever the tables are rebuilt (mbis_set_metric)
   double* d_basis = nullptr;
   double2* d_cfold64 = nullptr;
   double* d_tfold = nullptr;
@@ -262,6 +263,7 @@ struct mbis_ctx {
   // relative binning about a fiducial (mbis_rb_setup)
   int32_t rb_n = 0;                 // coarse bins (0: not set up)
   uint64_t rb_gen = 0;              // tables generation the summary data belong to
+  int32_t rb_use = 0;               // mbis_loglike evaluates the relative-binning likelihood
   int32_t* d_rb_edges = nullptr;    // [rb_n + 1] bin indices of the edges
   void* d_rb_rec = nullptr;         // [rb_n + 1] 48-byte edge records (k_rb.cu)
   void* d_rb_q = nullptr;           // [rb_n] float2 q_b / scale (k_rb.cu)

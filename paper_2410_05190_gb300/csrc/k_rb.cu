@@ -251,6 +251,7 @@ mbis_status rb_fail(mbis_ctx* c, mbis_status st, const std::string& msg) {
 }  // namespace
 
 void rb_free(mbis_ctx* c) {
+  c->rb_use = 0;
   rfree(c->d_rb_edges);
   rfree(c->d_rb_rec);
   rfree(c->d_rb_q);
@@ -343,7 +344,7 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
   for (int j = 0; j < kNumBasis; ++j) c->rb_C0[j] = pc0.C[j];
   c->rb_cst0 = pc0.cst;
   c->rb_n = n_rb;
-  c->rb_gen = c->gen;
+  c->rb_gen = c->tables_gen;
   return MBIS_OK;
 }
 
@@ -352,7 +353,7 @@ mbis_status mbis_rb_loglike(mbis_ctx* c, int64_t n, const double* theta, double*
     set_last_error("mbis_rb_loglike: null context");
     return MBIS_E_INVALID;
   }
-  if (c->rb_n == 0 || c->rb_gen != c->gen)
+  if (c->rb_n == 0 || c->rb_gen != c->tables_gen)
     return rb_fail(c, MBIS_E_STATE, "mbis_rb_loglike: call mbis_rb_setup (after the last mbis_set_metric)");
   if (n < 0 || (n > 0 && (!theta || !loglike))) return rb_fail(c, MBIS_E_INVALID, "mbis_rb_loglike: bad n or buffer");
   if (n == 0) return MBIS_OK;
@@ -379,6 +380,17 @@ mbis_status mbis_rb_loglike(mbis_ctx* c, int64_t n, const double* theta, double*
   rb_loglike_kernel<<<(unsigned)((n + kRbThreads - 1) / kRbThreads), kRbThreads, r.rec_smem ? sh : 0,
                       static_cast<cudaStream_t>(stream)>>>(r);
   RB_TRY(c, cudaGetLastError());
+  return MBIS_OK;
+}
+
+mbis_status mbis_rb_use(mbis_ctx* c, int32_t on) {
+  if (!c) {
+    set_last_error("mbis_rb_use: null context");
+    return MBIS_E_INVALID;
+  }
+  if (on && (c->rb_n == 0 || c->rb_gen != c->tables_gen))
+    return rb_fail(c, MBIS_E_STATE, "mbis_rb_use: call mbis_rb_setup (after the last mbis_set_metric)");
+  c->rb_use = on ? 1 : 0;
   return MBIS_OK;
 }
 

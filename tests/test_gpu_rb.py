@@ -83,3 +83,58 @@ def test_bns_event_matches_the_oracle_and_stays_close_to_the_exact_likelihood(m,
               f"{heavy.sum()} posterior samples: median {np.median(err):.1e}, max {err.max():.1e}")
     finally:
         m.mbis_destroy(ctx)
+
+
+def test_ess_loop_runs_on_the_relative_binning_likelihood(m, torch):
+    """mbis_rb_use routes mbis_loglike (and so the ESS loop) through relative binning: the
+    same draws give the same log L as mbis_rb_loglike, bit for bit; without refits the loop
+    draws the same samples as the exact run, so ESS and log Z agree to the parity tolerance;
+    a proposal refit keeps the set-up, a new metric drops it and restores the exact path."""
+    w = workloads.scaled(workloads.bns_population(n_events=1), f_hi=256.0)
+    spec = w.events[0]
+    ev, th, _ = make_event(w, spec)
+    prop = make_proposal(ev, w, th)
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        with pytest.raises(m.MbisError):
+            m.mbis_rb_use(ctx, True)
+        m.mbis_rb_setup(ctx, th, m.mbis_rb_edges(ctx, th, 5.0, 0.05))
+        theta, _ = draws(prop, 1 << 14, 11)
+        n = theta.shape[1]
+        th_d = torch.tensor(theta, device="cuda")
+        rb, via = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(2))
+        m.mbis_rb_loglike(ctx, n, th_d, rb)
+        m.mbis_rb_use(ctx, True)
+        m.mbis_loglike(ctx, n, th_d, via)
+        torch.cuda.synchronize()
+        assert torch.equal(rb, via)
+
+        P, batch = len(prop["ids"]), 1 << 14
+        bufs = [torch.empty((P, batch), dtype=torch.float64, device="cuda")] + \
+               [torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(4)]
+        runs = {}
+        for use in (True, False):
+            m.mbis_rb_use(ctx, use)
+            runs[use] = m.mbis_run_to_ess(ctx, *bufs, 2000.0, batch, 1 << 18, 77, refine=0)
+        (s_rb, nd_rb, _), (s_ex, nd_ex, _) = runs[True], runs[False]
+        assert nd_rb == nd_ex
+        assert abs(s_rb["ess"] / s_ex["ess"] - 1) < 1e-3
+        assert abs(s_rb["log_z"] - s_ex["log_z"]) < 1e-3 * max(1.0, abs(s_ex["log_z"]))
+
+        # a refit keeps the set-up
+        m.mbis_set_proposal(ctx, prop["mean"], prop["chol"], prop["scale"] * 0.9)
+        m.mbis_rb_use(ctx, True)
+        m.mbis_loglike(ctx, n, th_d, via)
+        # a new metric drops it: mbis_loglike is the exact likelihood again
+        set_metric(m, ctx, prop)
+        with pytest.raises(m.MbisError):
+            m.mbis_rb_loglike(ctx, n, th_d, rb)
+        ex = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.mbis_loglike(ctx, n, th_d, ex)
+        torch.cuda.synchronize()
+        assert not torch.equal(ex, via)
+        print(f"ESS loop on relative binning: ESS {s_rb['ess']:.1f} vs {s_ex['ess']:.1f}, "
+              f"log Z {s_rb['log_z']:.5f} vs {s_ex['log_z']:.5f}, {nd_rb} drawn")
+    finally:
+        m.mbis_destroy(ctx)
