@@ -10,7 +10,8 @@
 // (large-argument I1/I0 ~ 1 - 1/(2x)) of width 1/sqrt(Z1 u - 7).  A 48-point Gauss-Legendre
 // rule covers +-12 widths about the peak and 8-point composite rules the rest of the
 // range; without a peak the whole range gets a 24-panel composite 8-point rule.  Sums run
-// as an online log-sum-exp in FP64.
+// as an online log-sum-exp: in FP64 in log_distance_marginal (the FP64 path), in FP32 about
+// an FP64 reference value in log_distance_marginal_mixed (the mixed-precision kernels).
 #pragma once
 #include "physics.cuh"
 
