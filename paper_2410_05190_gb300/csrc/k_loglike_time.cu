@@ -17,7 +17,7 @@
 //   * one thread issues 3 x 4 x 2 tcgen05.mma.kind::tf32 (head.head + head.tail + tail.head
 //     for each 8-wide K step and both tiles) accumulating in TMEM and commits to an mbarrier
 //     that frees the double buffer two blocks later.
-// The A operand never touches global memory.  Every few blocks each thread reads its own
+// The A operand never touches global memory.  After every block each thread reads its own
 // row (its 128 shifts) back from TMEM into FP32 registers; after the last block it applies
 // the log-mean-exp.
 #include "internal.h"
@@ -37,14 +37,13 @@ constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [2 buf
 constexpr uint32_t kSmemBytes = kOffB + 2 * 2 * kTileBytes + 1024;
 constexpr uint32_t kIdesc = tc::idesc_tf32(128, kTimeShifts);
 // The tensor core aligns and truncates when it accumulates, which biases a long FP32
-// accumulation toward zero by a fraction of an ulp per step.  The head.head products
-// therefore accumulate in a "main" TMEM accumulator over segments of kSegBlocks K-blocks
-// only; a segment is drained into FP32 registers with round-to-nearest adds one block after
-// its last MMA (after the threads computed the next block's A rows, so the MMA has long
-// finished), before the next segment's first MMA overwrites it.  The two split corrections,
-// ~2^-11 smaller, accumulate over the whole K range in a second accumulator.
-// TMEM: per tile [main 128 | correction 128] columns.
-constexpr int kSegBlocks = 1;
+// accumulation toward zero by a fraction of an ulp per step.  Each K-block therefore
+// accumulates in TMEM on its own: its two split corrections (head.tail, tail.head, ~2^-11
+// smaller) first, into a fresh accumulator, then its four head.head products; the threads
+// add the block's result into FP32 registers with round-to-nearest adds.  Two accumulators
+// per tile alternate by block, so the drain of block kb - 1 runs while the tensor core works
+// on block kb, and block kb + 1's MMAs wait only for that drain, not for the tensor core.
+// TMEM: per tile [block kb even | block kb odd], 128 columns each.
 constexpr float kTwoPiF = 6.28318530717958647692f;
 // Added to the 32-bit turn count: 256 rounds (rather than truncates) when its top 23 bits
 // become a float mantissa f1 in [1, 2); 2^31 (half a turn) with the -3 pi in the remainder's
@@ -276,7 +275,8 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   float zacc[kTimeShifts];  // this sample's Re z_j, summed over drained segments (round to nearest)
 #pragma unroll
   for (int j = 0; j < kTimeShifts; ++j) zacc[j] = 0.f;
-  // this thread's row (its tile, its warp's lane quarter): main at column 0, correction at 128
+  // this thread's row (its tile, its warp's lane quarter): the even blocks' accumulator at
+  // column 0, the odd blocks' at 128
   const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(tile * 2 * kTimeShifts);
   auto drain = [&](int which) {
     const uint32_t base = tbase + (uint32_t)(which * kTimeShifts);
@@ -386,18 +386,6 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
         *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;
       }
-    if (kb >= 1 && kb % kSegBlocks == 0) {
-      // the segment that ended with block kb - 1: drain the main accumulator before the MMAs
-      // of block kb start it afresh
-      const bool ok = tc::mbar_wait(&mbar[(kb - 1) & 1], (uint32_t)(((kb - 1) >> 1) & 1));
-      if (__any_sync(0xffffffffu, !ok || s_bad)) {
-        bad = true;
-        break;
-      }
-      tc::fence_after_sync();
-      drain(0);
-      tc::fence_before_sync();
-    }
     tc::fence_proxy_async();
     tc::mbar_arrive(&full[b]);
     if (atomicAdd(&s_done[b], 1) == kCompute - 1) {
@@ -413,20 +401,22 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         tc::fence_after_sync();
         const uint32_t a_base = tc::smem_addr(sA + b * kTilesPerCta * 2 * kTileBytes);
         const uint32_t b_base = tc::smem_addr(sB + b * 2 * kTileBytes);
-        const bool seg_first = (kb % kSegBlocks) == 0;
 #pragma unroll
-        for (int t = 0; t < kTilesPerCta; ++t)
+        for (int t = 0; t < kTilesPerCta; ++t) {
+          // block kb's accumulator of tile t: the two split corrections (head.tail, tail.head)
+          // first, started afresh, then the head.head products
+          const uint32_t d = tmem + t * 2 * kTimeShifts + (uint32_t)(b * kTimeShifts);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
+          for (int term = 1; term <= 3; ++term)
 #pragma unroll
-            for (int term = 0; term < 3; ++term) {
-              // head.head into the main accumulator, head.tail and tail.head into the correction
-              const uint32_t aa = a_base + t * 2 * kTileBytes + (term == 2 ? kTileBytes : 0) + ks * 32;
-              const uint32_t bb = b_base + (term == 1 ? kTileBytes : 0) + ks * 32;
-              const uint32_t d = tmem + t * 2 * kTimeShifts + (term == 0 ? 0 : kTimeShifts);
-              const bool fresh = ks == 0 && (term == 0 ? seg_first : (kb == 0 && term == 1));
+            for (int ks = 0; ks < 4; ++ks) {
+              const int tt = term % 3;  // 1: head.tail, 2: tail.head, 0: head.head
+              const uint32_t aa = a_base + t * 2 * kTileBytes + (tt == 2 ? kTileBytes : 0) + ks * 32;
+              const uint32_t bb = b_base + (tt == 1 ? kTileBytes : 0) + ks * 32;
+              const bool fresh = term == 1 && ks == 0;
               tc::mma_tf32(d, tc::desc_k_sw128(aa), tc::desc_k_sw128(bb), kIdesc, fresh ? 0u : 1u);
             }
+        }
         tc::commit(&mbar[b]);
         ++s_issued_m[b];
         // buffer b ^ 1 is free once the MMAs of block kb - 1 completed
@@ -440,16 +430,27 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
       }
     }
+    if (kb >= 1) {
+      // block kb - 1's accumulator, while the tensor core runs block kb into the other one;
+      // every thread drains it before it arrives for block kb + 1, whose MMAs reuse it
+      const bool ok = tc::mbar_wait(&mbar[(kb - 1) & 1], (uint32_t)(((kb - 1) >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok || s_bad)) {
+        bad = true;
+        break;
+      }
+      tc::fence_after_sync();
+      drain((kb - 1) & 1);
+      tc::fence_before_sync();
+    }
   }
   if (!bad && nkb > 0) {
-    // the last segment and the corrections, once the last MMAs (and so all) completed
+    // the last block's accumulator, once its MMAs (and so all) completed
     const bool ok = tc::mbar_wait(&mbar[(nkb - 1) & 1], (uint32_t)(((nkb - 1) >> 1) & 1));
     if (__any_sync(0xffffffffu, !ok || s_bad)) {
       bad = true;
     } else {
       tc::fence_after_sync();
-      drain(0);
-      drain(1);
+      drain((nkb - 1) & 1);
       tc::fence_before_sync();
     }
   }
