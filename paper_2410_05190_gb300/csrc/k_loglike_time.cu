@@ -14,9 +14,10 @@
 //     one 64-bit fixed-point turn counter) and writes them, split into a TF32 head and an
 //     FP32 tail, into its row of a 128-byte-swizzled K-major shared-memory tile;
 //   * the pre-swizzled twiddle tiles (head, tail) of the block arrive by cp.async.bulk;
-//   * one thread issues 3 x 4 x 2 tcgen05.mma.kind::tf32 (head.head + head.tail + tail.head
-//     for each 8-wide K step and both tiles) accumulating in TMEM and commits to an mbarrier
-//     that frees the double buffer two blocks later.
+//   * one thread issues 3 x 4 tcgen05.mma.kind::tf32 of 128 shifts (M, the twiddle tile) by
+//     256 samples (N, both sample tiles at once) -- head.head + head.tail + tail.head for
+//     each 8-wide K step -- accumulating in TMEM, and commits to an mbarrier that frees the
+//     double buffer two blocks later.
 // The A operand never touches global memory.  After every block each thread reads its own
 // row (its 128 shifts) back from TMEM into FP32 registers; after the last block it applies
 // the log-mean-exp.
@@ -35,7 +36,10 @@ constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
 constexpr uint32_t kOffA = 0;           // [2 buf][2 tile][2 head/tail][tile]
 constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [2 buf][2 head/tail][tile]
 constexpr uint32_t kSmemBytes = kOffB + 2 * 2 * kTileBytes + 1024;
-constexpr uint32_t kIdesc = tc::idesc_tf32(128, kTimeShifts);
+static_assert(kTimeShifts * (kCompute + 1) * 4 <= kSmemBytes - 1024, "the final transpose fits the tiles' memory");
+// D[shift][sample] = twiddle tile (M = 128 shifts) x sample tile (N = 256 samples, both
+// tiles of the CTA in one MMA)
+constexpr uint32_t kIdesc = tc::idesc_tf32(kTimeShifts, kCompute);
 // The tensor core aligns and truncates when it accumulates, which biases a long FP32
 // accumulation toward zero by a fraction of an ulp per step.  Each K-block therefore
 // accumulates in TMEM on its own: its two split corrections (head.tail, tail.head, ~2^-11
@@ -275,11 +279,13 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   float zacc[kTimeShifts];  // this sample's Re z_j, summed over drained segments (round to nearest)
 #pragma unroll
   for (int j = 0; j < kTimeShifts; ++j) zacc[j] = 0.f;
-  // this thread's row (its tile, its warp's lane quarter): the even blocks' accumulator at
-  // column 0, the odd blocks' at 128
-  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(tile * 2 * kTimeShifts);
+  // TMEM lanes are the shifts, columns the samples: the even blocks' accumulator at column 0,
+  // the odd blocks' at 256.  This thread drains lane 32 (warp % 4) + lane (its warp's lane
+  // quarter) over the 128 samples of half warp / 4: zacc[c] is shift (32 (warp % 4) + lane)
+  // of sample 128 (warp / 4) + c, transposed through shared memory at the end.
+  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kTimeShifts);
   auto drain = [&](int which) {
-    const uint32_t base = tbase + (uint32_t)(which * kTimeShifts);
+    const uint32_t base = tbase + (uint32_t)(which * kCompute);
 #pragma unroll
     for (int c0 = 0; c0 < kTimeShifts; c0 += 32) {
       uint32_t r[32];
@@ -319,7 +325,8 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     const float4* tab = reinterpret_cast<const float4*>(a.cdet32) + (int64_t)kb * (kKBlockBins / 2);
       // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes.
       // Bins go in pairs (plan blocks have even starts), two lanes of f32x2 arithmetic.
-      unsigned char* rowA = sA + (b * kTilesPerCta + tile) * 2 * kTileBytes + row * 128;
+      // [buffer][head, tail][tile]: the heads (and tails) of both tiles are one 256-row operand
+      unsigned char* rowA = sA + ((b * 2) * kTilesPerCta + tile) * kTileBytes + row * 128;
 #pragma unroll 1
       for (int kk = 0; kk < kKBlockBins; kk += 2) {
         const int32_t k = kb * kKBlockBins + kk;
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         hi.w = tc::tf32_round(im.y); lo.w = tc::tf32_round(im.y - hi.w);
         const int chunk = (kk >> 1) ^ (row & 7);
         *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
-        *reinterpret_cast<float4*>(rowA + kTileBytes + (chunk << 4)) = lo;
+        *reinterpret_cast<float4*>(rowA + kTilesPerCta * kTileBytes + (chunk << 4)) = lo;
       }
     tc::fence_proxy_async();
     tc::mbar_arrive(&full[b]);
@@ -399,22 +406,21 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
       bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar[b], par);
       if (ok) {
         tc::fence_after_sync();
-        const uint32_t a_base = tc::smem_addr(sA + b * kTilesPerCta * 2 * kTileBytes);
-        const uint32_t b_base = tc::smem_addr(sB + b * 2 * kTileBytes);
-#pragma unroll
-        for (int t = 0; t < kTilesPerCta; ++t) {
-          // block kb's accumulator of tile t: the two split corrections (head.tail, tail.head)
-          // first, started afresh, then the head.head products
-          const uint32_t d = tmem + t * 2 * kTimeShifts + (uint32_t)(b * kTimeShifts);
+        const uint32_t s_base = tc::smem_addr(sA + b * 2 * kTilesPerCta * kTileBytes);  // samples (N)
+        const uint32_t w_base = tc::smem_addr(sB + b * 2 * kTileBytes);                 // twiddles (M)
+        {
+          // block kb's accumulator: the two split corrections (twiddle tail x sample head,
+          // twiddle head x sample tail) first, started afresh, then the head x head products
+          const uint32_t d = tmem + (uint32_t)(b * kCompute);
 #pragma unroll
           for (int term = 1; term <= 3; ++term)
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-              const int tt = term % 3;  // 1: head.tail, 2: tail.head, 0: head.head
-              const uint32_t aa = a_base + t * 2 * kTileBytes + (tt == 2 ? kTileBytes : 0) + ks * 32;
-              const uint32_t bb = b_base + (tt == 1 ? kTileBytes : 0) + ks * 32;
+              const int tt = term % 3;  // 1: twiddle tail, 2: sample tail, 0: head x head
+              const uint32_t ww = w_base + (tt == 1 ? kTileBytes : 0) + ks * 32;
+              const uint32_t ss = s_base + (tt == 2 ? kTilesPerCta * kTileBytes : 0) + ks * 32;
               const bool fresh = term == 1 && ks == 0;
-              tc::mma_tf32(d, tc::desc_k_sw128(aa), tc::desc_k_sw128(bb), kIdesc, fresh ? 0u : 1u);
+              tc::mma_tf32(d, tc::desc_k_sw128(ww), tc::desc_k_sw128(ss), kIdesc, fresh ? 0u : 1u);
             }
         }
         tc::commit(&mbar[b]);
@@ -467,17 +473,23 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     }
   }
   double ll = 0.0;
-  if (!bad && nkb > 0) {
-    float m = -INFINITY;
+  if (nkb > 0 && !s_bad) {
+    // every MMA and copy completed: the tiles' shared memory takes the transpose
+    // [shift][sample] (rows padded to 257 floats, conflict-free both ways)
+    constexpr int kT = kCompute + 1;
+    float* zt = reinterpret_cast<float*>(sm);
+    const int shift = 32 * (warp & 3) + (tid & 31), col0 = (warp >> 2) * kTimeShifts;
 #pragma unroll
-    for (int j = 0; j < kTimeShifts; ++j) m = fmaxf(m, zacc[j]);
+    for (int c = 0; c < kTimeShifts; ++c) zt[shift * kT + col0 + c] = zacc[c];
+    __syncthreads();
+    float m = -INFINITY;
+    for (int j = 0; j < kTimeShifts; ++j) m = fmaxf(m, zt[j * kT + tid]);
     const double g = amp * a.cscale;  // Re z_j = g * accumulator_j
     const float gf = (float)g;
     float sum = 0.f;
-#pragma unroll
-    for (int j = 0; j < kTimeShifts; ++j) sum += __expf(gf * (zacc[j] - m));
+    for (int j = 0; j < kTimeShifts; ++j) sum += __expf(gf * (zt[j * kT + tid] - m));
     ll = g * (double)m + log((double)sum / kTimeShifts) - 0.5 * H;
-  } else if (!bad) {
+  } else if (!s_bad) {
     ll = -0.5 * H;
   }
   tc::fence_before_sync();
