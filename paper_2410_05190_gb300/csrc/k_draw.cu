@@ -42,7 +42,8 @@ __global__ void draw_kernel(DrawArgs a, DrawConsts k) {
       const Philox4 w = philox4x32_10((uint32_t)g, (uint32_t)(g >> 32), 2u, (uint32_t)blk, (uint32_t)a.seed,
                                       (uint32_t)(a.seed >> 32));
       box_muller(w.v[0], w.v[1], z[4 * blk], z[4 * blk + 1]);
-      box_muller(w.v[2], w.v[3], z[4 * blk + 2], z[4 * blk + 3]);
+      // the block's second pair only when a slot uses it (FP64 logarithms dominate the draw)
+      if (4 * blk + 2 < a.P) box_muller(w.v[2], w.v[3], z[4 * blk + 2], z[4 * blk + 3]);
     }
   }
   double zz = 0.0;
@@ -81,8 +82,9 @@ __global__ void draw_kernel(DrawArgs a, DrawConsts k) {
     }
   }
   if ((a.flags & MBIS_PRIOR_M1M2) && inside) {
-    // |d(m1, m2)/d(Mc, q)| = Mc (1 + q)^(2/5) q^(-6/5)
-    lp += log(mc) + 0.4 * log1p(q) - 1.2 * log(q) - a.log_mass_norm;
+    // |d(m1, m2)/d(Mc, q)| = Mc (1 + q)^(2/5) q^(-6/5) = [Mc^(5/2) (1 + q) / q^3]^(2/5): one
+    // FP64 logarithm of a product instead of three
+    lp += 0.4 * log(mc * mc * sqrt(mc) * (1.0 + q) / (q * q * q)) - a.log_mass_norm;
   }
   if (a.logp) a.logp[i] = inside ? lp : -INFINITY;
   if (a.logq) a.logq[i] = -0.5 * zz + a.log_q_const;
