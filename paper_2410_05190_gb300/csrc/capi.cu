@@ -196,6 +196,7 @@ mbis_status build_tables(mbis_ctx* c) {
     pin.tol_turns = 2e-8;
     pin.rmax_turns = 1.0;
     pin.max_block = 4096;
+    pin.deg = (c->opts.marg & MBIS_MARG_TIME) ? kTimeRemDeg : kFoldRemDeg;  // the launching kernel's degree
     const std::vector<AnchorBlock> plan = plan_anchor_blocks(pin);
     c->n_blocks = (int32_t)plan.size();
     // float-float block entry when every phase term, its per-bin slope times the block

@@ -14,7 +14,13 @@ namespace mbis {
 
 constexpr int kMaxDet = 4;
 constexpr int kMaxP = 11;
-constexpr int kRemDeg = 5;          // degree of the FP32 remainder polynomial per anchor block
+constexpr int kRemDegMax = 5;       // largest degree of the FP32 remainder polynomial per anchor block
+// The degree each kernel family runs at (the plan of a context is built for its kernel's):
+// a lower degree saves per-bin FMAs at the cost of shorter blocks, which pays in the folded
+// kernel (one block entry per block) but not in the time-marginalised one (whose block entry
+// also re-anchors every detector's turn counter).
+constexpr int kFoldRemDeg = 4;
+constexpr int kTimeRemDeg = 5;
 constexpr int kChunk = 512;         // bins per shared-memory chunk of the mixed kernel
 constexpr int kMixedThreads = 128;  // samples per CTA of the mixed kernel
 constexpr int kBatchCtasPerSm = 7;  // resident CTAs per SM of the persistent multi-event launch
@@ -28,7 +34,7 @@ struct AnchorBlock {
   int32_t k0, k1, kc, pad;
   double B[kNumBasis];     // basis_j(f_kc)
   double dB[kNumBasis];    // basis_j'(f_kc) * df
-  float E[kNumBasis - 1][kRemDeg + 1];  // basis 8 (f) is linear: no remainder
+  float E[kNumBasis - 1][kRemDegMax + 1];  // basis 8 (f) is linear: no remainder; degree of the plan
   // B and dB as unevaluated float pairs (hi + lo) for the float-float block entry
   float Bh[kNumBasis], Bl[kNumBasis], dBh[kNumBasis], dBl[kNumBasis];
 };
@@ -166,6 +172,7 @@ struct PlanInput {
   double tol_turns;        // bound on the fit error of the phase
   double rmax_turns;       // bound on |remainder| kept in FP32
   int32_t max_block;
+  int32_t deg;             // degree of the remainder polynomials (<= kRemDegMax)
 };
 std::vector<AnchorBlock> plan_anchor_blocks(const PlanInput& in);
 

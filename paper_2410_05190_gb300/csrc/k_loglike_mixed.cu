@@ -39,7 +39,7 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 struct BlockState {
   uint32_t acc, step;
-  float c[kRemDeg + 1];
+  float c[kFoldRemDeg + 1];
   float w;
 };
 
@@ -65,7 +65,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.acc = (uint32_t)p0 + kTurnOffset;
   st.step = (uint32_t)p1;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) {
+  for (int m = 0; m <= kFoldRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j * kMixedThreads], B.E[j][m], s);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.c[1] += (float)r1;
   // angle = 2 pi (acc / 2^32) + 2 pi R = 2 pi f1 + (2 pi R - 3 pi), f1 = 1 + (acc + 2^31) / 2^32
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  for (int m = 0; m <= kFoldRemDeg; ++m) st.c[m] *= kTwoPiF;
   st.c[0] -= 1.5f * kTwoPiF;
   st.w = (float)w0;
 }
@@ -102,7 +102,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.acc = ff_frac32(xh, xl, r0) + kTurnOffset;
   st.step = ff_frac32(yh, yl, r1);
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) {
+  for (int m = 0; m <= kFoldRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * S], B.E[j][m], s);
@@ -111,7 +111,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.c[0] += r0 - w0 * r1;
   st.c[1] += r1;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  for (int m = 0; m <= kFoldRemDeg; ++m) st.c[m] *= kTwoPiF;
   st.c[0] -= 1.5f * kTwoPiF;
   st.w = w0;
 }
@@ -240,8 +240,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
       const int32_t seg_end = min(ke, blk_end);
       const int32_t my_end = min(seg_end, kcut);
       if (k < my_end) {
-        const float2 c0 = f2(st.c[0]), c1 = f2(st.c[1]), c2 = f2(st.c[2]), c3 = f2(st.c[3]), c4 = f2(st.c[4]),
-                     c5 = f2(st.c[5]);
+        float2 cr[kFoldRemDeg + 1];  // remainder coefficients, both lanes
+#pragma unroll
+        for (int m = 0; m <= kFoldRemDeg; ++m) cr[m] = f2(st.c[m]);
         const float2 two = f2(2.0f), twopi = f2(kTwoPiF);
         const uint32_t step = st.step, step2 = 2u * st.step;
         uint32_t acc = st.acc;
@@ -250,11 +251,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
         const float4* cp = cb + ((k - kb) >> 1);
 #pragma unroll 1
         for (int32_t p = 0; p < npair; ++p) {
-          float2 R = __ffma2_rn(c5, w, c4);
-          R = __ffma2_rn(R, w, c3);
-          R = __ffma2_rn(R, w, c2);
-          R = __ffma2_rn(R, w, c1);
-          R = __ffma2_rn(R, w, c0);
+          float2 R = cr[kFoldRemDeg];
+#pragma unroll
+          for (int m = kFoldRemDeg - 1; m >= 0; --m) R = __ffma2_rn(R, w, cr[m]);
           const float2 f1 = make_float2(mantissa_turn(acc), mantissa_turn(acc + step));
           const float2 ang = __ffma2_rn(f1, twopi, R);
           float2 sn, cs;
@@ -270,8 +269,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
         }
         int32_t kk = k + 2 * npair;
         if (kk < my_end) {  // one bin left (odd cut): the even half of the pair
-          const float R = fmaf(fmaf(fmaf(fmaf(fmaf(st.c[5], w.x, st.c[4]), w.x, st.c[3]), w.x, st.c[2]), w.x, st.c[1]),
-                               w.x, st.c[0]);
+          float R = st.c[kFoldRemDeg];
+#pragma unroll
+          for (int m = kFoldRemDeg - 1; m >= 0; --m) R = fmaf(R, w.x, st.c[m]);
           const float ang = fmaf(mantissa_turn(acc), kTwoPiF, R);
           float sn, cs;
           __sincosf(ang, &sn, &cs);

@@ -57,7 +57,7 @@ constexpr uint32_t kTurnOffset = 0x80000000u + 256u;
 
 struct State {
   uint32_t acc, step;
-  float c[kRemDeg + 1];
+  float c[kTimeRemDeg + 1];
   float w;
 };
 
@@ -80,7 +80,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.acc = (uint32_t)p0 + kTurnOffset;
   st.step = (uint32_t)p1;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) {
+  for (int m = 0; m <= kTimeRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j], B.E[j][m], s);
@@ -89,7 +89,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.c[0] += (float)(r0 - w0 * r1);
   st.c[1] += (float)r1;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  for (int m = 0; m <= kTimeRemDeg; ++m) st.c[m] *= kTwoPiF;
   st.c[0] -= 1.5f * kTwoPiF;
   st.w = (float)w0;
 }
@@ -116,7 +116,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.acc = ff_frac32(xh, xl, r0) + kTurnOffset;
   st.step = ff_frac32(yh, yl, r1);
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) {
+  for (int m = 0; m <= kTimeRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * kCompute], B.E[j][m], s);
@@ -125,7 +125,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   st.c[0] += r0 - w0 * r1;
   st.c[1] += r1;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) st.c[m] *= kTwoPiF;
+  for (int m = 0; m <= kTimeRemDeg; ++m) st.c[m] *= kTwoPiF;
   st.c[0] -= 1.5f * kTwoPiF;
   st.w = w0;
 }
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   st.step = 0;
   st.w = 0.f;
 #pragma unroll
-  for (int m = 0; m <= kRemDeg; ++m) st.c[m] = 0.f;
+  for (int m = 0; m <= kTimeRemDeg; ++m) st.c[m] = 0.f;
   int blk = -1;
   int32_t blk_end = 0;
   uint32_t cnt[nrow], stepd[nrow];
@@ -351,11 +351,9 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
         if (k < kcut) {
           const float2 w = make_float2(st.w, st.w + 1.0f);
-          float2 R = __ffma2_rn(f2(st.c[5]), w, f2(st.c[4]));
-          R = __ffma2_rn(R, w, f2(st.c[3]));
-          R = __ffma2_rn(R, w, f2(st.c[2]));
-          R = __ffma2_rn(R, w, f2(st.c[1]));
-          R = __ffma2_rn(R, w, f2(st.c[0]));
+          float2 R = f2(st.c[kTimeRemDeg]);
+#pragma unroll
+          for (int m = kTimeRemDeg - 1; m >= 0; --m) R = __ffma2_rn(R, w, f2(st.c[m]));
 #pragma unroll
           for (int d = 0; d < nrow; ++d) {
             {

@@ -60,9 +60,11 @@ struct Fit {
 // The basis functions with a remainder (B_8 = f is linear)
 constexpr int kRemBasis = kNumBasis - 1;
 
-Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
-  constexpr int D = kRemDeg + 1;
-  Fit out;
+// The fit of one block; its error is checked on every bin, or on max_pts evenly spaced bins.
+Fit fit_block(const PlanInput& in, int32_t k0, int32_t S, int32_t max_pts) {
+  const int D = in.deg + 1;
+  constexpr int DM = kRemDegMax + 1;
+  Fit out = {};
   AnchorBlock& b = out.blk;
   b.k0 = k0;
   b.k1 = k0 + S;
@@ -88,8 +90,8 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
   const double mid = 0.5 * (wa + wb), half = std::max(0.5 * (wb - wa), 0.5);
   // interpolate at Chebyshev points of the block, monomials in u = w / h: one Vandermonde
   // factorisation serves every basis function
-  double V[D * D], y[kRemBasis][D];
-  int piv[D];
+  double V[DM * DM], y[kRemBasis][DM];
+  int piv[DM];
   for (int i = 0; i < D; ++i) {
     const double w = mid + half * std::cos(kPi * (i + 0.5) / D);
     const double u = w / h;
@@ -111,9 +113,9 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
       hm *= h;
     }
   }
-  // error of the FP32-stored polynomials on the block's bins (all, or 257 evenly spaced)
+  // error of the FP32-stored polynomials on the block's bins (all, or max_pts evenly spaced)
   double emax[kRemBasis] = {}, rmax[kRemBasis] = {};
-  const int32_t npts = std::min<int32_t>(S, 257);
+  const int32_t npts = std::min<int32_t>(S, max_pts);
   for (int32_t i = 0; i < npts; ++i) {
     const int32_t kk = (npts == S) ? k0 + i : k0 + (int32_t)std::llround((double)i * (S - 1) / (npts - 1));
     const double w = (double)(kk - b.kc);
@@ -135,6 +137,8 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S) {
   return out;
 }
 
+constexpr int32_t kSearchPoints = 33, kCheckPoints = 257;
+
 std::vector<AnchorBlock> build_plan(const PlanInput& in) {
   std::vector<AnchorBlock> blocks;
   int32_t k0 = 0;
@@ -142,10 +146,13 @@ std::vector<AnchorBlock> build_plan(const PlanInput& in) {
   while (k0 < in.n_bins) {
     const int32_t remaining = in.n_bins - k0;
     const int32_t cap = std::min(remaining, in.max_block);
-    auto ok = [&](int32_t S) {
-      const Fit f = fit_block(in, k0, S);
+    // the search checks 33 bins per trial block; the chosen size is then verified on 257
+    // (every bin of a shorter block) and shrunk until that holds
+    auto ok_at = [&](int32_t S, int32_t pts) {
+      const Fit f = fit_block(in, k0, S, pts);
       return f.err_bound <= in.tol_turns && f.r_bound <= in.rmax_turns;
     };
+    auto ok = [&](int32_t S) { return ok_at(S, kSearchPoints); };
     int32_t good = std::min<int32_t>(cap, 8);  // short blocks are interpolated exactly
     if (good < remaining && (good & 1)) good -= 1;
     int32_t S = std::min(cap, std::max(good, guess));
@@ -170,9 +177,10 @@ std::vector<AnchorBlock> build_plan(const PlanInput& in) {
         if (ok(m)) good = m; else bad = m;
       }
     }
+    while (good > 8 && !ok_at(good, kCheckPoints)) good -= std::max<int32_t>(2, good / 16);
     // even sizes keep every block start even, so the kernel can take bins in pairs
     if (good < remaining && good > 2) good &= ~1;
-    blocks.push_back(fit_block(in, k0, good).blk);
+    blocks.push_back(fit_block(in, k0, good, kCheckPoints).blk);
     k0 += good;
     guess = good;
   }
@@ -181,7 +189,7 @@ std::vector<AnchorBlock> build_plan(const PlanInput& in) {
 
 bool same_input(const PlanInput& a, const PlanInput& b) {
   if (a.f_lo != b.f_lo || a.df != b.df || a.n_bins != b.n_bins || a.tol_turns != b.tol_turns ||
-      a.rmax_turns != b.rmax_turns || a.max_block != b.max_block)
+      a.rmax_turns != b.rmax_turns || a.max_block != b.max_block || a.deg != b.deg)
     return false;
   for (int j = 0; j < kNumBasis; ++j)
     if (a.cmax[j] != b.cmax[j]) return false;
