@@ -731,21 +731,26 @@ def serve_requests(m, n_req, rate_hz, seed=SERVE_SEED):
     return reqs
 
 
-def submit_request(m, srv, r, precision=None, tag=0):
+RB_RULE = (5.0, 0.3)  # relative-binning bins: proposal sigmas, radians per bin
+
+
+def submit_request(m, srv, r, precision=None, tag=0, rb_bns=False):
+    """rb_bns: a BNS request runs its ESS loop on relative binning about its injection."""
     ev, w, p = r["ev"], r["w"], r["ev"]["prop"]
+    rb = dict(rb_fiducial=ev["th"], rb_n_sigma=RB_RULE[0], rb_eps_rad=RB_RULE[1]) if rb_bns and r["kind"] == 1 else {}
     return m.mbis_server_submit(srv, ev["strain"], ev["psd"], ev["dets"], w.f_lo, w.df, ev["th"], p["ids"], p["mean"],
                                 p["chol"], p["scale"], p["lo"], p["hi"], prior_flags=p["flags"],
                                 gmst=ev["spec"].gmst, precision=r["precision"] if precision is None else precision,
                                 marg=w.marg, n_tshift=w.n_tshift, dt_shift=w.dt_shift, dmin=w.dmin, dmax=w.dmax,
-                                tag=tag, **r["ess"])
+                                tag=tag, **r["ess"], **rb)
 
 
 def percentile(x, q):
     return float(np.percentile(np.asarray(x), q)) if len(x) else None
 
 
-def serve_measurement(m, torch, n_req=48, rate_hz=2.0, max_active=8, cap=150 * 10**9):
-    reqs = serve_requests(m, n_req, rate_hz)
+def serve_measurement(m, torch, n_req=48, rate_hz=2.0, max_active=8, cap=150 * 10**9, rb_bns=False, reqs=None):
+    reqs = serve_requests(m, n_req, rate_hz) if reqs is None else reqs
     srv = m.mbis_server_create(hbm_cap_bytes=cap, max_active=max_active)
     try:
         t0 = time.perf_counter()
@@ -754,7 +759,7 @@ def serve_measurement(m, torch, n_req=48, rate_hz=2.0, max_active=8, cap=150 * 1
             delay = r["arrival"] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            ids.append(submit_request(m, srv, r, tag=k)[0])
+            ids.append(submit_request(m, srv, r, tag=k, rb_bns=rb_bns)[0])
         res = [m.mbis_server_wait(srv, i, 600.0) for i in ids]
         wall = time.perf_counter() - t0
         st = m.mbis_server_stats_get(srv)
@@ -771,7 +776,9 @@ def serve_measurement(m, torch, n_req=48, rate_hz=2.0, max_active=8, cap=150 * 1
                              "reached_1e4": sum(res[i]["summary"]["ess"] >= 1e4 for i in sel)}
     return {"workload": f"{n_req} requests, Poisson arrivals at {rate_hz}/s, kinds drawn uniformly from the "
                         "plain-method tiny event (FP64), the BNS population and the BBH population (mixed), "
-                        "each run to ESS >= 1e4 with 4 proposal refits (sample caps 2^24, BBH 2^25)",
+                        "each run to ESS >= 1e4 with 4 proposal refits (sample caps 2^24, BBH 2^25)" +
+                        (f"; BNS requests on relative binning about their injection (bins: {RB_RULE[0]} proposal "
+                         f"sigmas, {RB_RULE[1]} rad per bin)" if rb_bns else ""),
             "p50_s": percentile(ttr, 50), "p99_s": percentile(ttr, 99), "mean_s": statistics.mean(ttr),
             "throughput_req_s": n_req / wall, "evals_per_s": sum(x["n_drawn"] for x in res) / wall,
             "wall_s": wall, "failed": sum(x["status"] != 0 for x in res), "by_kind": by_kind,
@@ -869,6 +876,11 @@ def main():
                                                     "served_p50_s": percentile(mix, 50),
                                                     "served_p99_s": percentile(mix, 99)}
             out["served"] = served
+            # the same stream with the BNS requests on relative binning (the faster likelihood
+            # plugged into the served ESS loops)
+            served_rb, _, _ = serve_measurement(m, torch, n_req=args.serve_requests, rb_bns=True, reqs=reqs)
+            out["served_rb_bns"] = {k: served_rb[k] for k in ("workload", "p50_s", "p99_s", "mean_s",
+                                                              "throughput_req_s", "failed", "by_kind")}
     if rank == 0:
         if world == 1 and args.cpu_budget > 0:
             leg = OracleLeg(w, w.events[:1])

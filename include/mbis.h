@@ -276,6 +276,13 @@ typedef struct {
   uint32_t prior_flags;
   mbis_ess_options ess;
   uint64_t tag;               /* returned unchanged in the result */
+  /* Optional relative binning (mbis_rb_edges / mbis_rb_setup / mbis_rb_use): when
+   * rb_fiducial (host, 11 slots) is not NULL the request's ESS loop runs on the
+   * relative-binning likelihood about that fiducial, with bins from mbis_rb_edges(rb_n_sigma,
+   * rb_eps_rad, at most rb_max_bins).  Needs a folded, not time-marginalised context. */
+  const double* rb_fiducial;
+  double rb_n_sigma, rb_eps_rad;
+  int32_t rb_max_bins;
 } mbis_request;
 
 typedef struct {
@@ -448,7 +455,8 @@ mbis_status mbis_credible_levels(int64_t n, int32_t P, const double* theta, cons
  * edges[n_rb] = n_bins; the last edge is the frequency one past the grid), so a likelihood
  * costs n_rb + 1 phase evaluations instead of n_bins; <h|h> stays exact.  Needs a context
  * with a metric, fixed sky and orientation (the folded table) and no time marginalisation;
- * mbis_set_metric drops the set-up (a proposal refit keeps it).  Allocates its summary data with cudaMalloc.
+ * mbis_set_metric drops the set-up (a proposal refit keeps it).  Allocates its summary data
+ * from the context's allocator (stream-ordered from the server's pool for a served request).
  * Errors: MBIS_E_STATE, MBIS_E_UNSUPPORTED, MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
 mbis_status mbis_rb_setup(mbis_ctx* ctx, const double* theta0, int32_t n_rb, const int32_t* edges);
 

@@ -73,7 +73,8 @@ class Request(C.Structure):
     _fields_ = [("event", Event), ("psd", C.c_void_p), ("dets", C.c_void_p), ("grid", FreqGrid), ("opts", Options),
                 ("P", C.c_int32), ("ids", C.c_void_p), ("mean", C.c_void_p), ("chol", C.c_void_p),
                 ("scale", C.c_double), ("lo", C.c_void_p), ("hi", C.c_void_p), ("prior_flags", C.c_uint32),
-                ("ess", EssOptions), ("tag", C.c_uint64)]
+                ("ess", EssOptions), ("tag", C.c_uint64), ("rb_fiducial", C.c_void_p), ("rb_n_sigma", C.c_double),
+                ("rb_eps_rad", C.c_double), ("rb_max_bins", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -342,9 +343,11 @@ def mbis_server_create(hbm_cap_bytes=150 * 10**9, max_active=8, device=0):
 def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_ids, mean, chol_lower, scale,
                        prior_lo, prior_hi, prior_flags=0, gmst=0.0, precision=MIXED, marg=MARG_PHASE, n_tshift=128,
                        dt_shift=1e-4, dmin=10.0, dmax=1000.0, ess_target=1e4, batch=1 << 16, max_samples=1 << 24,
-                       seed=0, refine=0, refine_scale=0.0, tag=0):
+                       seed=0, refine=0, refine_scale=0.0, tag=0, rb_fiducial=None, rb_n_sigma=5.0, rb_eps_rad=0.3,
+                       rb_max_bins=None):
     """Queue one request (the arguments of mbis_create, mbis_set_metric and
-    mbis_run_to_ess).  Returns (request id, footprint bytes)."""
+    mbis_run_to_ess; rb_fiducial (11 slots) runs its ESS loop on relative binning about it).
+    Returns (request id, footprint bytes)."""
     strain = np.ascontiguousarray(strain)
     psd = np.ascontiguousarray(psd, dtype=np.float64)
     if strain.dtype == np.complex128:
@@ -363,6 +366,10 @@ def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_id
                   psd.ctypes.data, C.cast(detectors, C.c_void_p), FreqGrid(f_lo, df, n_bins),
                   Options(precision, marg, n_tshift, dt_shift, dmin, dmax, 0), len(ids), pid, pm, pL, scale, plo, phi,
                   prior_flags, EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed), tag)
+    if rb_fiducial is not None:
+        fid, pfid = _host(rb_fiducial, np.float64)
+        req.rb_fiducial, req.rb_n_sigma, req.rb_eps_rad = pfid, rb_n_sigma, rb_eps_rad
+        req.rb_max_bins = n_bins if rb_max_bins is None else rb_max_bins
     rid, fp = C.c_uint64(), C.c_int64()
     _check(_lib.mbis_server_submit(server, C.byref(req), C.byref(rid), C.byref(fp)))
     return rid.value, fp.value

@@ -30,37 +30,6 @@ mbis_status fail(mbis_ctx* ctx, mbis_status st, const std::string& msg) {
     }                                                                                            \
   } while (0)
 
-// Device memory of a context: stream-ordered from the context's pool when it has one
-// (no device-wide synchronisation), plain cudaMalloc / cudaFree otherwise.
-template <typename T>
-cudaError_t dalloc(mbis_ctx* c, T** p, size_t bytes) {
-  void* q = nullptr;
-  const cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&q, bytes, c->pool, c->stream) : cudaMalloc(&q, bytes);
-  if (e == cudaSuccess) {
-    *p = static_cast<T*>(q);
-    c->dev_bytes += bytes;
-    c->dev_peak = std::max(c->dev_peak, c->dev_bytes);
-    c->allocs.push_back({q, bytes});
-  }
-  return e;
-}
-
-template <typename T>
-void dfree(mbis_ctx* c, T*& p) {
-  if (!p) return;
-  for (size_t i = 0; i < c->allocs.size(); ++i)
-    if (c->allocs[i].first == (void*)p) {
-      c->dev_bytes -= c->allocs[i].second;
-      c->allocs.erase(c->allocs.begin() + i);
-      break;
-    }
-  if (c->pool)
-    cudaFreeAsync((void*)p, c->stream);
-  else
-    cudaFree((void*)p);
-  p = nullptr;
-}
-
 bool is_periodic(int id) { return id == kRa || id == kPsi || id == kPhic; }
 
 // integral of (1 + q)^(2/5) q^(-6/5) over [a, b]: composite 8-point Gauss-Legendre

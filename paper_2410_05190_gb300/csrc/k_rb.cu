@@ -236,12 +236,6 @@ __global__ void __launch_bounds__(kRbThreads, 3) rb_loglike_kernel(RbArgs r) {
   a.out[s] = ll;
 }
 
-template <typename T>
-void rfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
-}
-
 mbis_status rb_fail(mbis_ctx* c, mbis_status st, const std::string& msg) {
   c->err = msg;
   set_last_error(msg);
@@ -252,10 +246,10 @@ mbis_status rb_fail(mbis_ctx* c, mbis_status st, const std::string& msg) {
 
 void rb_free(mbis_ctx* c) {
   c->rb_use = 0;
-  rfree(c->d_rb_edges);
-  rfree(c->d_rb_rec);
-  rfree(c->d_rb_q);
-  rfree(c->d_rb_prefix);
+  dfree(c, c->d_rb_edges);
+  dfree(c, c->d_rb_rec);
+  dfree(c, c->d_rb_q);
+  dfree(c, c->d_rb_prefix);
   c->rb_n = 0;
 }
 
@@ -295,18 +289,15 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
   const int32_t n = c->n_bins;
   const PhaseCoeffs pc0 = phase_coeffs(theta0[kMc], theta0[kQ], theta0[kChi1], theta0[kChi2], theta0[kTc],
                                        theta0[kPhic]);
+  // device memory from the context's allocator (stream-ordered from its pool when it has
+  // one, as in the request server), copies on its stream
   double* d_w = nullptr;
-  double* d_max = nullptr;
-  auto cleanup = [&]() {
-    if (d_w) cudaFree(d_w);
-    if (d_max) cudaFree(d_max);
-  };
   cudaStream_t s = c->stream;
-  cudaError_t e = cudaMalloc(&d_w, sizeof(double) * 4 * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_prefix, sizeof(double) * 4 * ((size_t)n + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_edges, sizeof(int32_t) * (n_rb + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_rec, sizeof(float4) * kEdgeVec * (n_rb + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_rb_q, sizeof(float2) * n_rb);
+  cudaError_t e = dalloc(c, &d_w, sizeof(double) * 4 * (size_t)n);
+  if (e == cudaSuccess) e = dalloc(c, &c->d_rb_prefix, sizeof(double) * 4 * ((size_t)n + 1));
+  if (e == cudaSuccess) e = dalloc(c, &c->d_rb_edges, sizeof(int32_t) * (n_rb + 1));
+  if (e == cudaSuccess) e = dalloc(c, &c->d_rb_rec, sizeof(float4) * kEdgeVec * (n_rb + 1));
+  if (e == cudaSuccess) e = dalloc(c, &c->d_rb_q, sizeof(float2) * n_rb);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_rb_edges, edges, sizeof(int32_t) * (n_rb + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     rb_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_cfold64, c->d_basis, pc0, c->f_lo, c->df, d_w);
@@ -319,7 +310,8 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
   double mx = 0.0;
   if (e == cudaSuccess) {
     std::vector<double> T((size_t)4 * (n + 1));
-    e = cudaMemcpy(T.data(), c->d_rb_prefix, sizeof(double) * T.size(), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(T.data(), c->d_rb_prefix, sizeof(double) * T.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     const int64_t m = (int64_t)n + 1;
     for (int32_t b = 0; b < n_rb && e == cudaSuccess; ++b) {
       const int32_t k0 = edges[b], k1 = edges[b + 1];
@@ -335,7 +327,7 @@ mbis_status mbis_rb_setup(mbis_ctx* c, const double* theta0, int32_t n_rb, const
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cleanup();
+  dfree(c, d_w);
   if (e != cudaSuccess) {
     rb_free(c);
     return rb_fail(c, e == cudaErrorMemoryAllocation ? MBIS_E_OOM : MBIS_E_CUDA,
@@ -434,15 +426,13 @@ mbis_status mbis_rb_edges(const mbis_ctx* cc, const double* theta0, double n_sig
   const int32_t n = c->n_bins;
   int32_t nb = 0, k0 = 0;
   edges[0] = 0;
-  double b0[kNumBasis];
-  auto load_b0 = [&]() {
-    for (int j = 0; j < kNumBasis; ++j) b0[j] = basis(j, c->f_lo + (double)k0 * c->df);
-  };
+  double b0[kNumBasis], bk[kNumBasis];
+  auto load_b0 = [&]() { basis_all(c->f_lo + (double)k0 * c->df, b0); };
   load_b0();
   for (int32_t k = 1; k < n; ++k) {
-    const double f = c->f_lo + (double)k * c->df;
+    basis_all(c->f_lo + (double)k * c->df, bk);
     double dphi = 0.0;
-    for (int j = 0; j < kNumBasis; ++j) dphi += dC[j] * std::fabs(basis(j, f) - b0[j]);
+    for (int j = 0; j < kNumBasis; ++j) dphi += dC[j] * std::fabs(bk[j] - b0[j]);
     if (kTwoPi * dphi > eps_rad && k - 1 > k0) {
       if (nb + 1 >= max_bins) return rb_fail(c, MBIS_E_INVALID, "mbis_rb_edges: more bins than max_bins");
       edges[++nb] = k - 1;

@@ -36,7 +36,7 @@ struct Request {
   uint64_t id = 0;
   mbis_request r = {};
   std::vector<unsigned char> strain;
-  std::vector<double> psd, mean, chol, lo, hi;
+  std::vector<double> psd, mean, chol, lo, hi, rb_fiducial;
   std::vector<mbis_detector> dets;
   std::vector<int32_t> ids;
   int64_t footprint = 0;
@@ -94,6 +94,12 @@ int64_t request_footprint(const Request& q) {
   const mbis_request& r = q.r;
   size_t t = ctx_footprint_bytes(r.event.n_det, r.grid.n_bins, r.event.dtype, r.opts, is_fold(q.ids));
   t += round_alloc(sizeof(double) * (size_t)r.ess.batch * r.P) + 4 * round_alloc(sizeof(double) * (size_t)r.ess.batch);
+  if (r.rb_fiducial) {
+    // relative binning: prefix tables, their build scratch, edge records, weights, edges
+    const size_t n = (size_t)r.grid.n_bins, nb = (size_t)r.rb_max_bins;
+    t += round_alloc(32 * (n + 1)) + round_alloc(32 * n) + round_alloc(48 * (nb + 1)) + round_alloc(8 * nb) +
+         round_alloc(4 * (nb + 1));
+  }
   return (int64_t)t;
 }
 
@@ -166,6 +172,14 @@ void start(mbis_server* s, ServerSlot& sl) {
   if (st != MBIS_OK) return finish(s, sl, st, ctx_message(nullptr));
   st = mbis_set_metric(sl.ctx, r.P, r.ids, r.mean, r.chol, r.scale, r.lo, r.hi, r.prior_flags);
   if (st != MBIS_OK) return finish(s, sl, st, ctx_message(sl.ctx));
+  if (r.rb_fiducial) {
+    std::vector<int32_t> edges((size_t)r.rb_max_bins + 1);
+    int32_t n_rb = 0;
+    st = mbis_rb_edges(sl.ctx, r.rb_fiducial, r.rb_n_sigma, r.rb_eps_rad, r.rb_max_bins, edges.data(), &n_rb);
+    if (st == MBIS_OK) st = mbis_rb_setup(sl.ctx, r.rb_fiducial, n_rb, edges.data());
+    if (st == MBIS_OK) st = mbis_rb_use(sl.ctx, 1);
+    if (st != MBIS_OK) return finish(s, sl, st, ctx_message(sl.ctx));
+  }
   const size_t nb = (size_t)r.ess.batch;
   cudaError_t e = palloc(s, sl, &sl.buf.theta, sizeof(double) * nb * r.P);
   if (e == cudaSuccess) e = palloc(s, sl, &sl.buf.log_q, sizeof(double) * nb);
@@ -289,6 +303,11 @@ bool copy_request(const mbis_request* r, Request* q, std::string* why) {
     *why = "ess.batch and ess.max_samples must be >= 1";
     return false;
   }
+  if (r->rb_fiducial && (!(r->rb_n_sigma > 0.0) || !(r->rb_eps_rad > 0.0) || r->rb_max_bins < 1 ||
+                         r->rb_max_bins > r->grid.n_bins)) {
+    *why = "relative binning needs rb_n_sigma > 0, rb_eps_rad > 0 and 1 <= rb_max_bins <= n_bins";
+    return false;
+  }
   const size_t nb = (size_t)ev.n_det * r->grid.n_bins, P = (size_t)r->P;
   const size_t csz = ev.dtype == MBIS_C128 ? 16 : 8;
   q->r = *r;
@@ -308,6 +327,10 @@ bool copy_request(const mbis_request* r, Request* q, std::string* why) {
   q->r.chol = q->chol.data();
   q->r.lo = q->lo.data();
   q->r.hi = q->hi.data();
+  if (r->rb_fiducial) {
+    q->rb_fiducial.assign(r->rb_fiducial, r->rb_fiducial + kNumSlots);
+    q->r.rb_fiducial = q->rb_fiducial.data();
+  }
   return true;
 }
 

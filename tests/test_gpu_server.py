@@ -1,8 +1,9 @@
 """Served stream: requests run to a target ESS under continuous admission, through the C ABI.
 
-Each request's result must be the same alone (mbis_run_to_ess on a context of its own) and
-in a mix with other requests on the device (bitwise: the request's arithmetic does not
-depend on what else runs); admission must respect the HBM-footprint cap; a served
+Each request's result must be the same alone (mbis_run_to_ess on a context of its own, with
+relative binning set up the same way for a request that asks for it) and in a mix with
+other requests on the device (bitwise: the request's arithmetic does not depend on what
+else runs); admission must respect the HBM-footprint cap; a served
 request's ESS and log Z must match the oracle's on the same draws (FP64: 1e-9 relative;
 mixed precision: 1e-3 relative, the stated bound).
 """
@@ -30,18 +31,22 @@ def host_inputs(mod, ev, w, spec, th):
 class Req:
     """One request: host inputs, proposal, precision and ESS-loop options."""
 
+    rb = None
+
     def __init__(self, mod, w, spec, ev, th, prop, precision, ess_target, batch, max_samples, seed, refine=0,
-                 refine_scale=0.0):
+                 refine_scale=0.0, rb=None):
         self.inp = host_inputs(mod, ev, w, spec, th)
         self.prop, self.precision = prop, precision
+        self.rb = rb  # (fiducial, n_sigma, eps_rad): the ESS loop on relative binning
         self.ess = dict(ess_target=ess_target, batch=batch, max_samples=max_samples, seed=seed, refine=refine,
                         refine_scale=refine_scale)
 
     def submit(self, mod, server, tag=0):
         p = self.prop
+        rb = {} if self.rb is None else dict(rb_fiducial=self.rb[0], rb_n_sigma=self.rb[1], rb_eps_rad=self.rb[2])
         return mod.mbis_server_submit(server, param_ids=p["ids"], mean=p["mean"], chol_lower=p["chol"],
                                       scale=p["scale"], prior_lo=p["lo"], prior_hi=p["hi"], prior_flags=p["flags"],
-                                      precision=self.precision, tag=tag, **self.inp, **self.ess)
+                                      precision=self.precision, tag=tag, **self.inp, **self.ess, **rb)
 
     def alone(self, mod, torch):
         i = self.inp
@@ -51,6 +56,11 @@ class Req:
         try:
             p = self.prop
             mod.mbis_set_metric(ctx, p["ids"], p["mean"], p["chol"], p["scale"], p["lo"], p["hi"], p["flags"])
+            if self.rb is not None:
+                fid, ns, eps = self.rb
+                edges = mod.mbis_rb_edges(ctx, fid, ns, eps, max_bins=len(i["psd"][0]))
+                mod.mbis_rb_setup(ctx, fid, edges)
+                mod.mbis_rb_use(ctx, True)
             P, b = len(p["ids"]), self.ess["batch"]
             bufs = [torch.empty((P, b), dtype=torch.float64, device="cuda")] + \
                    [torch.empty(b, dtype=torch.float64, device="cuda") for _ in range(4)]
@@ -69,18 +79,22 @@ def requests(m):
     out.append(Req(m, w, spec, ev, th, prop, m.FP64, 2000.0, 1 << 14, 1 << 19, 11))
     out.append(Req(m, w, spec, ev, th, prop, m.MIXED, 2000.0, 1 << 14, 1 << 19, 12, refine=1, refine_scale=1.2))
     wb = workloads.scaled(workloads.bns_population(n_events=2), f_hi=512.0)
+    rb_reqs = []
     for k, sp in enumerate(wb.events):
         evb, thb, _ = make_event(wb, sp)
         to_fp32_data(evb)
-        out.append(Req(m, wb, sp, evb, thb, make_proposal(evb, wb, thb), m.MIXED, 1000.0, 1 << 15, 1 << 18,
-                       sp.draw_seed, refine=k))
+        propb = make_proposal(evb, wb, thb)
+        out.append(Req(m, wb, sp, evb, thb, propb, m.MIXED, 1000.0, 1 << 15, 1 << 18, sp.draw_seed, refine=k))
+        if k == 0:  # the same event with its ESS loop on relative binning about the injection
+            rb_reqs.append(Req(m, wb, sp, evb, thb, propb, m.MIXED, 1000.0, 1 << 15, 1 << 18, sp.draw_seed,
+                               refine=1, rb=(thb, 5.0, 0.1)))
     wt = workloads.bbh_population(n_events=1)
     sp = wt.events[0]
     evt, tht, _ = make_event(wt, sp)
     to_fp32_data(evt)
     out.append(Req(m, wt, sp, evt, tht, make_proposal(evt, wt, tht), m.MIXED, 1000.0, 1 << 14, 1 << 16,
                    sp.draw_seed, refine=1))
-    return out
+    return out + rb_reqs
 
 
 def same(a, b):
