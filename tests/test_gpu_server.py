@@ -202,3 +202,32 @@ def test_served_request_matches_the_oracle(m, torch, requests, precision, rtol):
     want = oracle.reduce(ll, lp, lq)
     assert res["summary"]["ess"] == pytest.approx(want["ess"], rel=rtol)
     assert abs(res["summary"]["log_z"] - want["log_z"]) <= rtol
+
+
+def test_relative_binning_requests_are_checked(m, torch, requests):
+    """A served request's relative-binning parameters are checked at submission; asking for
+    relative binning on a time-marginalised event (which it does not support) fails that
+    request alone with MBIS_E_UNSUPPORTED, and the server goes on."""
+    bns = requests[2]
+    bbh = next(r for r in requests if r.inp["marg"] & m.MARG_TIME)
+    srv = m.mbis_server_create(hbm_cap_bytes=150 * 10**9, max_active=2)
+    try:
+        for bad in (dict(rb_eps_rad=0.0), dict(rb_n_sigma=-1.0), dict(rb_max_bins=len(bns.inp["psd"][0]) + 1)):
+            p = bns.prop
+            kw = dict(rb_fiducial=bns.inp["fixed"], **bad)
+            with pytest.raises(m.MbisError) as e:
+                m.mbis_server_submit(srv, param_ids=p["ids"], mean=p["mean"], chol_lower=p["chol"], scale=p["scale"],
+                                     prior_lo=p["lo"], prior_hi=p["hi"], prior_flags=p["flags"], precision=m.MIXED,
+                                     **bns.inp, **bns.ess, **kw)
+            assert e.value.status == m.MBIS_E_INVALID
+        p = bbh.prop
+        rid, _ = m.mbis_server_submit(srv, param_ids=p["ids"], mean=p["mean"], chol_lower=p["chol"], scale=p["scale"],
+                                      prior_lo=p["lo"], prior_hi=p["hi"], prior_flags=p["flags"], precision=m.MIXED,
+                                      rb_fiducial=bbh.inp["fixed"], **bbh.inp, **bbh.ess)
+        good, _ = bns.submit(m, srv)
+        r_bad = m.mbis_server_wait(srv, rid, 300.0)
+        r_good = m.mbis_server_wait(srv, good, 300.0)
+    finally:
+        m.mbis_server_destroy(srv)
+    assert r_bad["status"] == m.MBIS_E_UNSUPPORTED and "relative binning" in r_bad["message"]
+    same(r_good, bns.alone(m, torch))
