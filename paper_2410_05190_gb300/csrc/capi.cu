@@ -328,6 +328,12 @@ mbis_status mbis::create_ctx(const mbis_event* ev, const double* psd, const mbis
   c->opts = *opts;
   c->stream = env.stream;
   c->pool = env.pool;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->n_sms = sms > 0 ? sms : 152;
+  }
   auto bail = [&](mbis_status st) {
     std::string m = c->err;
     mbis_destroy(c);
@@ -574,6 +580,9 @@ void mbis_destroy(mbis_ctx* c) {
   if (!c) return;
   rb_free(c);
   free_tables(c);
+  dfree(c, c->d_zpart);
+  dfree(c, c->d_amp);
+  dfree(c, c->d_kcut);
   dfree(c, c->d_strain);
   dfree(c, c->d_psd64);
   dfree(c, c->d_basis);
@@ -665,7 +674,28 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
     if (!a.fold)
       return fail(c, MBIS_E_UNSUPPORTED,
                   "mbis_loglike: mixed precision with sampled sky/orientation needs MBIS_MARG_TIME");
-    CU_TRY(c, launch_loglike_mixed(a, s));
+    // a launch with fewer tiles than the device has CTA slots splits each tile's bins over
+    // several CTAs (whole parts each), so small batches still fill the GPU
+    LikeArgs b = a;
+    const int64_t tiles = (n + kMixedThreads - 1) / kMixedThreads, slots = (int64_t)c->n_sms * 8;
+    const int32_t parts = (c->n_bins + kPartBins - 1) / kPartBins;
+    b.split = (tiles < slots && parts > 1) ? (int32_t)std::min<int64_t>(parts, slots / tiles) : 1;
+    if (b.split > 1) {
+      if (c->split_cap < n) {
+        dfree(c, c->d_zpart);
+        dfree(c, c->d_amp);
+        dfree(c, c->d_kcut);
+        c->split_cap = 0;
+        CU_TRY(c, dalloc(c, &c->d_zpart, sizeof(double2) * (size_t)parts * (size_t)n));
+        CU_TRY(c, dalloc(c, &c->d_amp, sizeof(double) * (size_t)n));
+        CU_TRY(c, dalloc(c, &c->d_kcut, sizeof(int32_t) * (size_t)n));
+        c->split_cap = n;
+      }
+      b.zpart = c->d_zpart;
+      b.amp_out = c->d_amp;
+      b.kcut_out = c->d_kcut;
+    }
+    CU_TRY(c, launch_loglike_mixed(b, s));
   }
   return MBIS_OK;
 }

@@ -23,6 +23,11 @@ constexpr int kRemDegMax = 5;       // largest degree of the FP32 remainder poly
 constexpr int kFoldRemDeg = 4;
 constexpr int kTimeRemDeg = 5;
 constexpr int kChunk = 512;         // bins per shared-memory chunk of the mixed kernel
+// The folded kernel sums the overlap in fixed parts of the grid, kPartChunks chunks each,
+// one float pair per part added in order: the sum does not depend on how many CTAs share a
+// tile's bins (small launches split them to fill the GPU).
+constexpr int kPartChunks = 16;
+constexpr int kPartBins = kPartChunks * kChunk;
 constexpr int kMixedThreads = 128;  // samples per CTA of the mixed kernel
 constexpr int kBatchCtasPerSm = 7;  // resident CTAs per SM of the persistent multi-event launch
 constexpr int kReduceBlocks = 608;  // 4 x 152 SMs
@@ -89,6 +94,12 @@ struct LikeArgs {
   const double* gl;           // Gauss-Legendre nodes / weights (marg.cuh layout)
   const float* glf;           // the same nodes / weights in FP32 (mixed-precision marginal)
   DistConst dist;             // distance-marginal constants of [dmin, dmax]
+  // folded kernel split over CTAs (split > 1): per-part overlap sums and the per-sample
+  // amplitude (negative: outside the model) and ISCO cut, read by the epilogue kernel
+  int32_t split;
+  double2* zpart;             // [n_parts][n]
+  double* amp_out;            // [n]
+  int32_t* kcut_out;          // [n]
 };
 
 struct DrawArgs {
@@ -254,6 +265,12 @@ struct mbis_ctx {
   int32_t tables_mode = -1;  // -1 none, 1 fold, 0 per-detector
   uint64_t gen = 0;          // bumped whenever the tables or the proposal change (batches re-capture)
   uint64_t tables_gen = 0;   // bumped whenever the tables are rebuilt (mbis_set_metric)
+  int32_t n_sms = 0;         // SMs of the context's device
+  // scratch of split folded launches (grown on demand)
+  double2* d_zpart = nullptr;
+  double* d_amp = nullptr;
+  int32_t* d_kcut = nullptr;
+  int64_t split_cap = 0;     // samples x parts the scratch holds
   double* d_basis = nullptr;
   double2* d_cfold64 = nullptr;
   double* d_tfold = nullptr;

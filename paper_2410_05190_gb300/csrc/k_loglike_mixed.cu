@@ -128,10 +128,23 @@ struct FoldSmem {
   int s_kmax;
 };
 
+// log L of one sample from its overlap sums (in units of cscale / A) and its set-up:
+// the marginalisations of Sec. III.  Shared by the kernel and the split launch's epilogue.
+__device__ __forceinline__ double fold_loglike(const LikeArgs& a, double A, int32_t kcut, double Zr, double Zi) {
+  const double zr = A * a.cscale * Zr, zi = A * a.cscale * Zi;
+  const double H = A * A * a.tfold[kcut];
+  if (a.marg == 0) return zr - 0.5 * H;
+  if (a.marg == MBIS_MARG_PHASE) return log_i0(hypot(zr, zi)) - 0.5 * H;
+  return log_distance_marginal_mixed(hypot(zr, zi), H, a.dist, a.glf);
+}
+
 // One tile of 128 samples of one event.  `first` is false when the CTA has already run a
 // tile (persistent launch): the mbarriers are then invalidated and initialised afresh.
+// piece / split: this CTA sums the parts [n_parts piece / split, n_parts (piece + 1) / split)
+// of the tile's bins; with split > 1 it writes their sums for the epilogue kernel.
 template <bool kFF>
-__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first, FoldSmem& sm) {
+__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first, FoldSmem& sm, int piece = 0,
+                                          int split = 1) {
   float4 (&sC)[kNbuf][kChunk / 2] = sm.sC;
   uint64_t* bar = sm.bar;
   double* sPC = sm.sPC;
@@ -199,25 +212,46 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   __syncthreads();
   const int32_t kmax = s_kmax;
   const int32_t nch = (kmax + kChunk - 1) / kChunk;
+  const int32_t n_parts = (a.n_bins + kPartBins - 1) / kPartBins;
+  const int32_t part_lo = (int32_t)((int64_t)n_parts * piece / split);
+  const int32_t part_hi = (int32_t)((int64_t)n_parts * (piece + 1) / split);
+  const int32_t ch_lo = min(part_lo * kPartChunks, nch), ch_hi = min(part_hi * kPartChunks, nch);
   constexpr uint32_t kBytes = kChunk * sizeof(float2);
   int issued[kNbuf] = {};  // copies issued per buffer (thread 0)
   if (tid == 0) {
-    for (int b = 0; b < kNbuf && b < nch; ++b) {
+    for (int b = 0; b < kNbuf && ch_lo + b < ch_hi; ++b) {
       tc::mbar_expect_tx(&bar[b], kBytes);
-      tc::bulk_g2s(sC[b], a.cfold32 + (int64_t)b * (kChunk / 2), kBytes, &bar[b]);
+      tc::bulk_g2s(sC[b], a.cfold32 + (int64_t)(ch_lo + b) * (kChunk / 2), kBytes, &bar[b]);
       ++issued[b];
     }
   }
 
   // ---- sweep over frequency
-  FFSum Zr, Zi;  // the chunks' FP32 sums, added without FP64 arithmetic
+  FFSum Zr, Zi;  // the part's chunk sums (FP32), added without FP64 arithmetic
+  double Zr_tot = 0.0, Zi_tot = 0.0;  // the parts, in order
+  int32_t part = part_lo;
   BlockState st;
   int32_t blk_end = 0;
   int blk = -1;
+  if (ch_lo > 0) {
+    // start inside the grid: the anchor block that holds the range's first bin (entered,
+    // then advanced to that bin below)
+    const int32_t k0 = ch_lo * kChunk;
+    int lo = 0, hi = a.n_blocks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.plan[mid].k0 <= k0)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    blk = lo - 1;
+    blk_end = k0;
+  }
   bool timed_out = false;
-  for (int32_t ch = 0; ch < nch; ++ch) {
-    const int b = ch % kNbuf;
-    const bool got = tc::mbar_wait(&bar[b], (uint32_t)((ch / kNbuf) & 1));
+  for (int32_t ch = ch_lo; ch < ch_hi; ++ch) {
+    const int b = (ch - ch_lo) % kNbuf;
+    const bool got = tc::mbar_wait(&bar[b], (uint32_t)(((ch - ch_lo) / kNbuf) & 1));
     if (__syncthreads_or(!got)) {
       timed_out = true;
       break;
@@ -234,6 +268,11 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
             enter_block_ff(a.plan, blk, my_pf, st);
           else
             enter_block(a.plan, blk, my_pc, my_cf, st);
+          // a range that starts inside the block: the state at bin k, exactly as a sweep
+          // from the block's first bin reaches it (integer turn counter, integer offset)
+          const int32_t adv = k - a.plan[blk].k0;
+          st.acc += (uint32_t)adv * st.step;
+          st.w += (float)adv;
         }
         blk_end = a.plan[blk].k1;
       }
@@ -294,8 +333,20 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
     Zi.add(zi.y);
     Zi.add(-zn.x);
     Zi.add(-zn.y);
+    if ((ch + 1) % kPartChunks == 0 || ch + 1 == ch_hi) {
+      // the part ends here
+      if (split > 1) {
+        if (active) a.zpart[(int64_t)part * a.n + s] = make_double2(Zr.value(), Zi.value());
+      } else {
+        Zr_tot += Zr.value();
+        Zi_tot += Zi.value();
+      }
+      Zr = FFSum{};
+      Zi = FFSum{};
+      ++part;
+    }
     __syncthreads();  // every thread is done with buffer b
-    if (tid == 0 && ch + kNbuf < nch) {
+    if (tid == 0 && ch + kNbuf < ch_hi) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::mbar_expect_tx(&bar[b], kBytes);
       tc::bulk_g2s(sC[b], a.cfold32 + (int64_t)(ch + kNbuf) * (kChunk / 2), kBytes, &bar[b]);
@@ -310,32 +361,59 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
       for (int bb = 0; bb < kNbuf; ++bb)
         if (issued[bb] > 0) (void)tc::mbar_wait(&bar[bb], (uint32_t)((issued[bb] - 1) & 1));
     }
-    if (active) a.out[s] = NAN;
+    if (active) {
+      if (split > 1) {
+        for (int32_t q = part_lo; q < part_hi; ++q) a.zpart[(int64_t)q * a.n + s] = make_double2(NAN, NAN);
+        if (piece == 0) a.amp_out[s] = NAN;
+      } else {
+        a.out[s] = NAN;
+      }
+    }
     return;
   }
   if (!active) return;
+  if (split > 1) {
+    // parts of this piece beyond the tile's last live bin are empty; the first piece passes on
+    // the sample's set-up
+    for (; part < part_hi; ++part) a.zpart[(int64_t)part * a.n + s] = make_double2(0.0, 0.0);
+    if (piece == 0) {
+      a.amp_out[s] = valid ? A : -1.0;
+      a.kcut_out[s] = kcut;
+    }
+    return;
+  }
   if (!valid) {
     a.out[s] = -INFINITY;
     return;
   }
   // ---- marginalisation (Sec. III)
-  const double zr = A * a.cscale * Zr.value(), zi = A * a.cscale * Zi.value();
-  const double H = A * A * a.tfold[kcut];
-  double ll;
-  if (a.marg == 0) {
-    ll = zr - 0.5 * H;
-  } else if (a.marg == MBIS_MARG_PHASE) {
-    ll = log_i0(hypot(zr, zi)) - 0.5 * H;
-  } else {
-    ll = log_distance_marginal_mixed(hypot(zr, zi), H, a.dist, a.glf);
+  a.out[s] = fold_loglike(a, A, kcut, Zr_tot, Zi_tot);
+}
+
+// The split launch's epilogue: a sample's parts in order, then its log L.
+__global__ void fold_epilogue_kernel(LikeArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const double A = a.amp_out[s];
+  if (!(A >= 0.0)) {
+    a.out[s] = A < 0.0 ? -INFINITY : NAN;
+    return;
   }
-  a.out[s] = ll;
+  const int32_t n_parts = (a.n_bins + kPartBins - 1) / kPartBins;
+  double Zr = 0.0, Zi = 0.0;
+  for (int32_t q = 0; q < n_parts; ++q) {
+    const double2 z = a.zpart[(int64_t)q * a.n + s];
+    Zr += z.x;
+    Zi += z.y;
+  }
+  a.out[s] = fold_loglike(a, A, a.kcut_out[s], Zr, Zi);
 }
 
 template <bool kFF>
 __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
   __shared__ FoldSmem sm;
-  fold_tile<kFF>(a, blockIdx.x, true, sm);
+  const int split = a.split > 1 ? a.split : 1;
+  fold_tile<kFF>(a, blockIdx.x / split, true, sm, (int)(blockIdx.x % split), split);
 }
 
 // Persistent launch over the tiles of many events: each CTA takes (event, tile) items from a
@@ -380,11 +458,17 @@ cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* it
 
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int64_t blocks = (a.n + kMixedThreads - 1) / kMixedThreads;
+  const int split = a.split > 1 ? a.split : 1;
+  const int64_t blocks = (a.n + kMixedThreads - 1) / kMixedThreads * split;
   if (a.ff_phase)
     loglike_mixed_fold_kernel<true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(a);
   else
     loglike_mixed_fold_kernel<false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(a);
+  if (split > 1) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_epilogue_kernel<<<(unsigned)((a.n + 255) / 256), 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -94,6 +94,11 @@ int64_t request_footprint(const Request& q) {
   const mbis_request& r = q.r;
   size_t t = ctx_footprint_bytes(r.event.n_det, r.grid.n_bins, r.event.dtype, r.opts, is_fold(q.ids));
   t += round_alloc(sizeof(double) * (size_t)r.ess.batch * r.P) + 4 * round_alloc(sizeof(double) * (size_t)r.ess.batch);
+  if (r.opts.precision == MBIS_MIXED && !(r.opts.marg & MBIS_MARG_TIME) && is_fold(q.ids)) {
+    // scratch of a split folded launch: per-part sums, amplitude and cut per sample
+    const size_t parts = ((size_t)r.grid.n_bins + kPartBins - 1) / kPartBins, nb = (size_t)r.ess.batch;
+    t += round_alloc(16 * parts * nb) + round_alloc(8 * nb) + round_alloc(4 * nb);
+  }
   if (r.rb_fiducial) {
     // relative binning: prefix tables, their build scratch, edge records, weights, edges
     const size_t n = (size_t)r.grid.n_bins, nb = (size_t)r.rb_max_bins;

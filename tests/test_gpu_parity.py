@@ -183,6 +183,29 @@ def bns():
     return w, spec, ev, th, prop
 
 
+def test_split_launches_equal_the_full_launch(m, torch, bns):
+    """A small launch (fewer tiles than the GPU has CTA slots) splits each tile's bins over
+    several CTAs; the overlap is summed in fixed parts of the grid, so every sample's log L
+    equals, bit for bit, the one from a launch too large to split, for ragged and tiny
+    batches too."""
+    w, spec, ev, th, prop = bns
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        n = 1 << 18
+        theta = torch.empty((len(prop["ids"]), n), dtype=torch.float64, device="cuda")
+        lq, lp, full = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+        m.mbis_draw(ctx, spec.draw_seed, 0, n, theta, lq, lp)
+        m.mbis_loglike(ctx, n, theta, full)
+        for k in (1 << 16, 5000, 129, 1):
+            part = torch.empty(k, dtype=torch.float64, device="cuda")
+            m.mbis_loglike(ctx, k, theta[:, :k].contiguous(), part)
+            torch.cuda.synchronize()
+            assert torch.equal(part, full[:k]), k
+    finally:
+        m.mbis_destroy(ctx)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_bns_full_grid_matches_oracle(m, torch, bns, precision):
     w, spec, ev, th, prop = bns
