@@ -44,7 +44,7 @@ SFU_PER_BIN = 2                # one sine and one cosine per (sample, bin)
 N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one loglike_mixed_fold_kernel launch at this
 # workload (2^20 samples), from the full ncu capture in profiles/loglike_mixed_fold_kernel_bns.md
-FOLD_TRAFFIC_BYTES = 44_040_448 + 99_072
+FOLD_TRAFFIC_BYTES = 44_097_792 + 264_192
 
 
 def peaks():
