@@ -133,8 +133,12 @@ mbis_status mbis_draw(mbis_ctx* ctx, uint64_t seed, uint64_t ctr0, int64_t n, do
  * marginalised as the options say: PHASE -> ln I0(|Z|) - H/2; PHASE|DISTANCE ->
  * ln int p(d) I0(|Z1|/d) e^(-H1/(2 d^2)) dd; TIME -> ln mean_j e^(Re z_j - H/2).  theta
  * (device, [P][n] SoA as written by mbis_draw), loglike (device, n).  Samples with an
- * unphysical parameter (Mc <= 0, q <= 0, |chi| >= 1, d_L <= 0) get -inf.
- * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_UNSUPPORTED, MBIS_E_CUDA. */
+ * unphysical parameter (Mc <= 0, q <= 0, |chi| >= 1, d_L <= 0) get -inf.  A call with fewer
+ * samples than fill the GPU shares each sample's bins among several CTAs through scratch the
+ * context owns (allocated on first need, from its pool in the server), with results equal bit
+ * for bit to an unsplit launch; calls on one context are therefore ordered on one stream (or
+ * synchronised), like its reductions.
+ * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_UNSUPPORTED, MBIS_E_OOM, MBIS_E_CUDA. */
 mbis_status mbis_loglike(mbis_ctx* ctx, int64_t n, const double* theta, double* loglike, void* cuda_stream);
 
 /* Importance weights and Kish ESS (Eqs. 5-6), evidence Z = mean(w).  Two passes on the
