@@ -554,7 +554,7 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
             "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
 
 
-def pp_measurement(m, torch, n_tiled=256, n_bns=256):
+def pp_measurement(m, torch, n_tiled=256, n_bns=512):
     """P-P self-consistency (Sec. III A): credible levels of the true parameters over
     simulated populations, KS p-value per parameter and Fisher's combination.
     (1) the tiled demonstration: sources drawn from the (x, q) prior, tiled proposal;
