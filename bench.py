@@ -554,12 +554,59 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
             "efficiency": statistics.mean(x["ess"] / x["drawn"] for x in runs)}
 
 
-def pp_measurement(m, torch, n_tiled=256, n_bns=512):
+def pp_population(m, torch, wb, box, n_final=1 << 18, refine=4, refine_scale=1.2, batch=1 << 16,
+                  max_samples=1 << 20, ess_ok=2000.0):
+    """Credible levels of a population drawn from its analysis prior (box: the prior's
+    (Mc, q, t_c) ranges): per source the ESS loop refits the Fisher Gaussian, then one batch
+    of n_final draws gives the weighted posterior; KS p-values per parameter and combined,
+    over all sources and over those whose final batch reached ESS >= ess_ok (the sources a
+    user would accept; the others are proposal failures, counted)."""
+    from paper_2410_05190_gb300 import pp
+    dn = workloads.network(wb.detectors)
+    lv, effs = [], []
+    names = [workloads.PARAM_NAMES[i] for i in wb.sampled]
+    t0 = time.perf_counter()
+    for spec in wb.events:
+        ev = event_setup(m, wb, spec, dn)
+        for k, slot in enumerate(wb.sampled):   # the population's prior, not a box about the truth
+            if slot in box:
+                ev["prop"]["lo"][k], ev["prop"]["hi"][k] = box[slot]
+        ctx = make_ctx(m, wb, ev, m.MIXED)
+        try:
+            P = len(ev["prop"]["ids"])
+            bufs = ess_buffers(torch, P, batch)
+            m.mbis_run_to_ess(ctx, *bufs, ess_target=ess_ok, batch=batch, max_samples=max_samples,
+                              seed=spec.draw_seed, refine=refine, refine_scale=refine_scale)
+            th_s = torch.empty((P, n_final), dtype=torch.float64, device="cuda")
+            lq, lp, ll, wt = (torch.empty(n_final, dtype=torch.float64, device="cuda") for _ in range(4))
+            m.mbis_draw(ctx, spec.draw_seed ^ 0x5EED, 0, n_final, th_s, lq, lp)
+            m.mbis_loglike(ctx, n_final, th_s, ll)
+            summ = m.mbis_reduce(ctx, n_final, ll, lp, lq, wt)
+            lv.append(pp.levels(m, torch, n_final, th_s, wt, [ev["th"][i] for i in wb.sampled]))
+            effs.append(summ["ess"] / n_final)
+        finally:
+            m.mbis_destroy(ctx)
+    secs = time.perf_counter() - t0
+    lv, ok = np.array(lv), np.array(effs) * n_final >= ess_ok
+    pv = {nm: pp.ks_pvalue(lv[:, k]) for k, nm in enumerate(names)}
+    pv_ok = {nm: pp.ks_pvalue(lv[ok, k]) for k, nm in enumerate(names)}
+    return {"events": len(wb.events), "samples_per_event": n_final, "ks_pvalue": pv,
+            "combined_pvalue": pp.combined_pvalue(list(pv.values())),
+            "converged": {"ess_at_least": ess_ok, "events": int(ok.sum()), "ks_pvalue": pv_ok,
+                          "combined_pvalue": pp.combined_pvalue(list(pv_ok.values()))},
+            "median_efficiency": float(np.median(effs)), "seconds": secs,
+            "proposal": f"Fisher Gaussian refitted {refine} times (x{refine_scale}) by the ESS loop, "
+                        f"batches of {batch}, at most {max_samples} draws",
+            "population": wb.name, "detectors": wb.detectors, "n_bins": wb.n_bins}
+
+
+def pp_measurement(m, torch, n_tiled=256, n_bns=512, n_bbh=512):
     """P-P self-consistency (Sec. III A): credible levels of the true parameters over
     simulated populations, KS p-value per parameter and Fisher's combination.
     (1) the tiled demonstration: sources drawn from the (x, q) prior, tiled proposal;
-    (2) BNS sources drawn from the analysis prior (workloads.bns_pp_population): the Fisher
-    Gaussian refitted by the ESS loop, then one batch."""
+    (2) BNS sources drawn from the analysis prior (workloads.bns_pp_population) and (3) BBH
+    sources (workloads.bbh_pp_population, intrinsic parameters sampled): the Fisher Gaussian
+    refitted by the ESS loop, then one batch."""
     from paper_2410_05190_gb300 import pp
     out = {}
     # (1) tiled
@@ -610,40 +657,12 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=512):
                              "sources_per_s": n_tiled / secs}
     finally:
         m.mbis_tiling_destroy(t)
-    # (2) BNS drawn from the analysis prior, the refitted Gaussian proposal
-    wb = workloads.bns_pp_population(n_events=n_bns)
-    dn = workloads.network(wb.detectors)
-    lv, effs = [], []
-    names = [workloads.PARAM_NAMES[i] for i in wb.sampled]
-    n_final = 1 << 18
-    t0 = time.perf_counter()
-    for spec in wb.events:
-        ev = event_setup(m, wb, spec, dn)
-        for k, slot in enumerate(wb.sampled):   # the population's prior, not a box about the truth
-            if slot in workloads.PP_BOX:
-                ev["prop"]["lo"][k], ev["prop"]["hi"][k] = workloads.PP_BOX[slot]
-        ctx = make_ctx(m, wb, ev, m.MIXED)
-        try:
-            P = len(ev["prop"]["ids"])
-            bufs = ess_buffers(torch, P, 1 << 16)
-            m.mbis_run_to_ess(ctx, *bufs, ess_target=2000.0, batch=1 << 16, max_samples=1 << 20,
-                              seed=spec.draw_seed, refine=4, refine_scale=1.2)
-            th_s = torch.empty((P, n_final), dtype=torch.float64, device="cuda")
-            lq, lp, ll, wt = (torch.empty(n_final, dtype=torch.float64, device="cuda") for _ in range(4))
-            m.mbis_draw(ctx, spec.draw_seed ^ 0x5EED, 0, n_final, th_s, lq, lp)
-            m.mbis_loglike(ctx, n_final, th_s, ll)
-            summ = m.mbis_reduce(ctx, n_final, ll, lp, lq, wt)
-            lv.append(pp.levels(m, torch, n_final, th_s, wt, [ev["th"][i] for i in wb.sampled]))
-            effs.append(summ["ess"] / n_final)
-        finally:
-            m.mbis_destroy(ctx)
-    secs = time.perf_counter() - t0
-    lv = np.array(lv)
-    pv = {nm: pp.ks_pvalue(lv[:, k]) for k, nm in enumerate(names)}
-    out["bns_population"] = {"events": n_bns, "samples_per_event": n_final, "ks_pvalue": pv,
-                             "combined_pvalue": pp.combined_pvalue(list(pv.values())),
-                             "median_efficiency": float(np.median(effs)), "seconds": secs,
-                             "proposal": "Fisher Gaussian refitted 4 times by the ESS loop"}
+    # (2) BNS, and (3) BBH intrinsic parameters, drawn from their analysis priors, the
+    # refitted Gaussian proposal
+    out["bns_population"] = pp_population(m, torch, workloads.bns_pp_population(n_events=n_bns), workloads.PP_BOX)
+    out["bbh_intrinsic_population"] = pp_population(m, torch, workloads.bbh_pp_population(n_events=n_bbh),
+                                                    workloads.PP_BOX_BBH, n_final=1 << 21, refine=8,
+                                                    refine_scale=1.5, batch=1 << 18, max_samples=1 << 22)
     return out
 
 

@@ -271,19 +271,21 @@ def tiled_population(demo: "TiledDemo", n_events, seed=POPULATION_SEED + 6):
 
 
 PP_BOX = {MC: (1.1, 1.5), Q: (1.0, 1.6), TC: (-5e-4, 5e-4)}
+PP_MASS_SQUARE = (1.0, 2.2)       # component masses drawn in this square, then cut to the box
 
 
 def bns_pp_population(n_events=64, seed=POPULATION_SEED + 7):
     """BNS sources drawn from the fixed prior that their analysis uses, for the P-P test:
     flat in (m1, m2) inside Mc in [1.1, 1.5], q = m1/m2 in [1, 1.6] (by rejection from
-    m ~ U[1.0, 2.0] sorted), chi ~ U[-0.05, 0.05], t_c ~ U[-0.5, 0.5] ms, isotropic sky and
+    m ~ U[1.0, 2.2] sorted, a square that holds the whole box: m2 >= 1.004, m1 <= 2.19 there),
+    chi ~ U[-0.05, 0.05], t_c ~ U[-0.5, 0.5] ms, isotropic sky and
     orientation, SNR ~ U[10, 30], coloured noise; H1+L1, 20-1024 Hz at 1/128 Hz; sampled
     (Mc, q, chi1, chi2, t_c); phase and distance marginalised.  The analysis box is PP_BOX."""
     rng = np.random.Generator(np.random.PCG64(seed))
     events = []
     for e in range(n_events):
         while True:
-            m = np.sort(rng.uniform(1.0, 2.0, size=2))[::-1]
+            m = np.sort(rng.uniform(*PP_MASS_SQUARE, size=2))[::-1]
             mc = (m[0] * m[1]) ** 0.6 / (m[0] + m[1]) ** 0.2
             if PP_BOX[MC][0] <= mc <= PP_BOX[MC][1] and m[0] / m[1] <= PP_BOX[Q][1]:
                 break
@@ -299,6 +301,40 @@ def bns_pp_population(n_events=64, seed=POPULATION_SEED + 7):
                                 gmst, snr, noise_seed=(seed << 8) + 2 * e + 1, draw_seed=(seed << 8) + 2 * e + 2))
     return Workload("bns_pp_population", ["H1", "L1"], 20.0, 1024.0, 1.0 / 128, [MC, Q, CHI1, CHI2, TC],
                     MARG_PHASE | MARG_DISTANCE, 1 << 18, "mixed", "c64", 1.5, PRIOR_M1M2, 0.05, events)
+
+
+PP_BOX_BBH = {MC: (15.0, 30.0), Q: (1.0, 4.0), TC: (-1e-3, 1e-3)}
+PP_MASS_SQUARE_BBH = (9.0, 75.0)
+
+
+def bbh_pp_population(n_events=64, seed=POPULATION_SEED + 8):
+    """BBH sources for the P-P test of the intrinsic parameters, drawn from the fixed prior
+    their analysis uses: flat in (m1, m2) inside Mc in [15, 30], q = m1/m2 in [1, 4] (by
+    rejection from m ~ U[9, 75] sorted, a square that holds the whole box: m2 >= 9.008,
+    m1 <= 72.07 there), chi ~ U[-0.8, 0.8],
+    t_c ~ U[-1, 1] ms, isotropic sky and orientation held fixed in the analysis, SNR ~
+    U[10, 40], coloured noise; H1+L1+V1, 20-1024 Hz at 1/8 Hz; sampled (Mc, q, chi1, chi2,
+    t_c); phase and distance marginalised.  The analysis box is PP_BOX_BBH."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    events = []
+    for e in range(n_events):
+        while True:
+            m = np.sort(rng.uniform(*PP_MASS_SQUARE_BBH, size=2))[::-1]
+            mc = (m[0] * m[1]) ** 0.6 / (m[0] + m[1]) ** 0.2
+            if PP_BOX_BBH[MC][0] <= mc <= PP_BOX_BBH[MC][1] and m[0] / m[1] <= PP_BOX_BBH[Q][1]:
+                break
+        chi = rng.uniform(-0.8, 0.8, size=2)
+        ra, dec, psi, iota = _isotropic(rng)
+        gmst = rng.uniform(0.0, 2 * math.pi)
+        phic = rng.uniform(0.0, 2 * math.pi)
+        tc = rng.uniform(*PP_BOX_BBH[TC])
+        snr = rng.uniform(10.0, 40.0)
+        events.append(EventSpec(float(m[0]), float(m[1]),
+                                dict(chi1=float(chi[0]), chi2=float(chi[1]), ra=ra, dec=dec, psi=psi, iota=iota,
+                                     tc=tc, phic=phic),
+                                gmst, snr, noise_seed=(seed << 8) + 2 * e + 1, draw_seed=(seed << 8) + 2 * e + 2))
+    return Workload("bbh_pp_population", ["H1", "L1", "V1"], 20.0, 1024.0, 1.0 / 8, [MC, Q, CHI1, CHI2, TC],
+                    MARG_PHASE | MARG_DISTANCE, 1 << 18, "mixed", "c64", 1.5, PRIOR_M1M2, 0.8, events)
 
 
 def scaled(w: Workload, n_events=None, n_samples=None, f_hi=None):
