@@ -1,5 +1,7 @@
 """Helpers shared by the GPU test modules: contexts built from oracle events, the FP32
 rounding of the stored data, and the per-sample log L comparison."""
+import os
+
 import numpy as np
 import pytest
 
@@ -54,5 +56,9 @@ def compare_loglike(got, ref, logp):
     inside = np.isfinite(logp)
     assert np.all(np.isfinite(ref[inside]))
     d = np.abs(got[inside] - ref[inside])
+    # the observed error per case, for the per-configuration statement (pytest -s shows it)
+    case = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    print(f"\n[log L vs oracle] {case}: max |delta| = {d.max():.2e}, "
+          f"mean signed = {np.mean(got[inside] - ref[inside]):+.2e}, n = {int(inside.sum())}")
     assert d.max() <= LOGL_TOL, (d.max(), int(np.argmax(d)))
     return d.max()
