@@ -212,7 +212,7 @@ def test_bns_full_grid_matches_oracle(m, torch, bns, precision):
     ctx = gpu_context(m, ev, w, spec, th, m.MIXED if precision == "mixed" else m.FP64)
     try:
         set_metric(m, ctx, prop)
-        n = 48
+        n = 128
         theta, _ = oracle.draw(spec.draw_seed, 0, n, prop["ids"], prop["mean"], prop["chol"], prop["scale"])
         theta[:, 0] = [th[i] for i in prop["ids"]]       # include the injection
         logp = oracle.log_prior(prop["ids"], prop["lo"], prop["hi"], prop["flags"], theta)
@@ -224,7 +224,7 @@ def test_bns_full_grid_matches_oracle(m, torch, bns, precision):
 
 
 def test_bns_full_size_launch_sampled_outputs(m, torch, bns):
-    """The benchmark's launch: 2^20 samples of one BNS event in one call; outputs at 24
+    """The benchmark's launch: 2^20 samples of one BNS event in one call; outputs at 96
     sampled indices against the oracle, and all outputs finite or -inf where invalid."""
     w, spec, ev, th, prop = bns
     ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
@@ -242,7 +242,7 @@ def test_bns_full_size_launch_sampled_outputs(m, torch, bns):
         torch.cuda.synchronize()
         llh = ll.cpu().numpy()
         assert not np.any(np.isnan(llh))
-        idx = np.random.default_rng(7).choice(n, 24, replace=False)
+        idx = np.random.default_rng(7).choice(n, 96, replace=False)
         idx[0] = n - 1
         th_s = theta.cpu().numpy()[:, idx]
         ref = oracle.loglike_batch(ev, oracle.full_params(prop["ids"], th_s, th))
