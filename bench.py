@@ -555,7 +555,7 @@ def tiled_measurement(m, torch, reps=3, target=1e4, batch=1 << 14):
 
 
 def pp_population(m, torch, wb, box, n_final=1 << 18, refine=4, refine_scale=1.2, batch=1 << 16,
-                  max_samples=1 << 20, ess_ok=2000.0):
+                  max_samples=1 << 20, ess_ok=2000.0, refit_min_ess=0.0):
     """Credible levels of a population drawn from its analysis prior (box: the prior's
     (Mc, q, t_c) ranges): per source the ESS loop refits the Fisher Gaussian, then one batch
     of n_final draws gives the weighted posterior; KS p-values per parameter and combined,
@@ -576,7 +576,8 @@ def pp_population(m, torch, wb, box, n_final=1 << 18, refine=4, refine_scale=1.2
             P = len(ev["prop"]["ids"])
             bufs = ess_buffers(torch, P, batch)
             m.mbis_run_to_ess(ctx, *bufs, ess_target=ess_ok, batch=batch, max_samples=max_samples,
-                              seed=spec.draw_seed, refine=refine, refine_scale=refine_scale)
+                              seed=spec.draw_seed, refine=refine, refine_scale=refine_scale,
+                              refit_min_ess=refit_min_ess)
             th_s = torch.empty((P, n_final), dtype=torch.float64, device="cuda")
             lq, lp, ll, wt = (torch.empty(n_final, dtype=torch.float64, device="cuda") for _ in range(4))
             m.mbis_draw(ctx, spec.draw_seed ^ 0x5EED, 0, n_final, th_s, lq, lp)
@@ -596,7 +597,8 @@ def pp_population(m, torch, wb, box, n_final=1 << 18, refine=4, refine_scale=1.2
                           "combined_pvalue": pp.combined_pvalue(list(pv_ok.values()))},
             "median_efficiency": float(np.median(effs)), "seconds": secs,
             "proposal": f"Fisher Gaussian refitted {refine} times (x{refine_scale}) by the ESS loop, "
-                        f"batches of {batch}, at most {max_samples} draws",
+                        f"batches of {batch}, at most {max_samples} draws"
+                        + (f", refit batches pooled to ESS {refit_min_ess:g}" if refit_min_ess > 0 else ""),
             "population": wb.name, "detectors": wb.detectors, "n_bins": wb.n_bins}
 
 
@@ -662,7 +664,8 @@ def pp_measurement(m, torch, n_tiled=256, n_bns=512, n_bbh=512):
     out["bns_population"] = pp_population(m, torch, workloads.bns_pp_population(n_events=n_bns), workloads.PP_BOX)
     out["bbh_intrinsic_population"] = pp_population(m, torch, workloads.bbh_pp_population(n_events=n_bbh),
                                                     workloads.PP_BOX_BBH, n_final=1 << 21, refine=8,
-                                                    refine_scale=1.5, batch=1 << 18, max_samples=1 << 22)
+                                                    refine_scale=1.5, batch=1 << 16, max_samples=1 << 22,
+                                                    refit_min_ess=200.0)
     return out
 
 

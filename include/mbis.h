@@ -194,6 +194,7 @@ typedef struct {
   int32_t refine;       /* refit the proposal after each of the first `refine` batches */
   double refine_scale;  /* width scale of a refitted proposal (<= 0 keeps the current scale) */
   uint64_t seed;        /* Philox key; batch b uses counters [b * batch, (b + 1) * batch) */
+  double refit_min_ess; /* a refit waits for this ESS: see mbis_run_to_ess (<= 0: 2P + 1) */
 } mbis_ess_options;
 
 /* ESS-target loop: batches of draw -> likelihood -> weights merged into the running state
@@ -201,7 +202,10 @@ typedef struct {
  * App. C).  With refine > 0, each of the first `refine` batches refits the proposal
  * (weighted mean and covariance, mbis_weighted_moments) when its own ESS is at least 2P + 1;
  * batches drawn before the last refit only adapt the proposal and do not enter the
- * estimate.  Buffers (device, one batch): theta [P][batch], log_q, log_prior, loglike,
+ * estimate.  With refit_min_ess above 2P + 1, a refit batch whose ESS falls short pools
+ * its weighted moments with the next batches drawn from the same proposal (weights on one
+ * scale) until the pooled ESS reaches refit_min_ess, or 16 batches are pooled; the refit
+ * then uses the pool (if its ESS is at least 2P + 1) and counts as one of `refine`.  Buffers (device, one batch): theta [P][batch], log_q, log_prior, loglike,
  * weights [batch].  *out: summary of the estimate; n_drawn (host, nullable): every draw,
  * adaptation included; n_used (host, nullable): draws in the estimate.
  * Errors: MBIS_E_STATE, MBIS_E_INVALID, MBIS_E_UNSUPPORTED, MBIS_E_CUDA, MBIS_E_TIMEOUT. */

@@ -62,7 +62,7 @@ class Summary(C.Structure):
 
 class EssOptions(C.Structure):
     _fields_ = [("ess_target", C.c_double), ("batch", C.c_int64), ("max_samples", C.c_int64), ("refine", C.c_int32),
-                ("refine_scale", C.c_double), ("seed", C.c_uint64)]
+                ("refine_scale", C.c_double), ("seed", C.c_uint64), ("refit_min_ess", C.c_double)]
 
 
 class ServerOptions(C.Structure):
@@ -280,9 +280,9 @@ def mbis_set_proposal(ctx, mean, chol_lower, scale):
 
 
 def mbis_run_to_ess(ctx, theta, log_q, log_prior, loglike, weights, ess_target, batch, max_samples, seed, refine=0,
-                    refine_scale=0.0, stream=None):
+                    refine_scale=0.0, stream=None, refit_min_ess=0.0):
     """Returns (summary dict, n_drawn, n_used)."""
-    opts = EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed)
+    opts = EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed, refit_min_ess)
     out = Summary()
     nd, nu = C.c_int64(), C.c_int64()
     _check(_lib.mbis_run_to_ess(ctx, C.byref(opts), _dev(theta), _dev(log_q), _dev(log_prior), _dev(loglike),
@@ -344,7 +344,7 @@ def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_id
                        prior_lo, prior_hi, prior_flags=0, gmst=0.0, precision=MIXED, marg=MARG_PHASE, n_tshift=128,
                        dt_shift=1e-4, dmin=10.0, dmax=1000.0, ess_target=1e4, batch=1 << 16, max_samples=1 << 24,
                        seed=0, refine=0, refine_scale=0.0, tag=0, rb_fiducial=None, rb_n_sigma=5.0, rb_eps_rad=0.3,
-                       rb_max_bins=None):
+                       rb_max_bins=None, refit_min_ess=0.0):
     """Queue one request (the arguments of mbis_create, mbis_set_metric and
     mbis_run_to_ess; rb_fiducial (11 slots) runs its ESS loop on relative binning about it).
     Returns (request id, footprint bytes)."""
@@ -365,7 +365,7 @@ def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_id
     req = Request(Event(n_det, dtype, strain.ctypes.data, gmst, (C.c_double * 11)(*map(float, fixed))),
                   psd.ctypes.data, C.cast(detectors, C.c_void_p), FreqGrid(f_lo, df, n_bins),
                   Options(precision, marg, n_tshift, dt_shift, dmin, dmax, 0), len(ids), pid, pm, pL, scale, plo, phi,
-                  prior_flags, EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed), tag)
+                  prior_flags, EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed, refit_min_ess), tag)
     if rb_fiducial is not None:
         fid, pfid = _host(rb_fiducial, np.float64)
         req.rb_fiducial, req.rb_n_sigma, req.rb_eps_rad = pfid, rb_n_sigma, rb_eps_rad

@@ -524,11 +524,36 @@ mbis_status mbis::ess_complete(mbis_ctx* c, EssState* st) {
   st->drawn += nb;
   ++st->b;
   if (st->refit) {
+    const double min_fit = 2.0 * c->P + 1.0;
+    const int nm = 1 + c->P + c->P * (c->P + 1) / 2;
+    const double* sums = c->h_result + 8;  // this batch's sums, weights normalised to its S1
+    double pool_ess = batch.ess;
+    if (st->o.refit_min_ess > min_fit) {  // pool with earlier batches of this proposal
+      mbis_summary merged = batch;
+      if (st->pooled > 0) mbis_merge_summaries(&st->pool, &batch, &merged);
+      const double m_new = merged.max_logw;
+      const double a_old = st->pooled > 0 && st->pool.max_logw > -INFINITY ? exp(st->pool.max_logw - m_new) : 0.0;
+      const double a_b = batch.max_logw > -INFINITY ? batch.s1 * exp(batch.max_logw - m_new) : 0.0;
+      for (int j = 0; j < nm; ++j)  // a batch or pool of zero weight adds nothing (its sums may be NaN)
+        st->mom[j] = (a_old > 0.0 ? a_old * st->mom[j] : 0.0) + (a_b > 0.0 ? a_b * sums[j] : 0.0);
+      st->pool = merged;
+      ++st->pooled;
+      pool_ess = merged.ess;
+      sums = st->mom;
+      if (pool_ess < st->o.refit_min_ess && st->pooled < kMaxRefitPool) {  // keep pooling
+        mbis_reset_running(c);
+        st->used = 0;
+        st->cur = mbis_summary{};
+        if (st->drawn >= st->o.max_samples) st->done = true;
+        return MBIS_OK;
+      }
+      st->pooled = 0;
+    }
     --st->refits_left;
-    if (batch.ess >= 2.0 * c->P + 1.0) {
+    if (pool_ess >= min_fit) {
       const MomentArgs ma = moment_args(c);
       double mean[kMaxP], cov[kMaxP * kMaxP], L[kMaxP * kMaxP];
-      if (moments_from_sums(c, ma, c->h_result + 8, mean, cov) && host_cholesky(c->P, cov, L)) {
+      if (moments_from_sums(c, ma, sums, mean, cov) && host_cholesky(c->P, cov, L)) {
         const mbis_status r =
             mbis_set_proposal(c, mean, L, st->o.refine_scale > 0.0 ? st->o.refine_scale : c->scale);
         if (r != MBIS_OK) {

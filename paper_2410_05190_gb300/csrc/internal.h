@@ -223,7 +223,13 @@ struct EssState {
   bool refit = false;  // the batch in flight adapts the proposal
   bool done = false;
   mbis_summary cur = {};
+  // refit pool: moment sums of the refit batches drawn from the current proposal, each
+  // scaled to the pool's weight scale exp(pool.max_logw)
+  int pooled = 0;
+  mbis_summary pool = {};
+  double mom[1 + kMaxP + kMaxP * (kMaxP + 1) / 2] = {};
 };
+constexpr int kMaxRefitPool = 16;  // batches pooled for one refit at most
 mbis_status ess_begin(mbis_ctx* c, const mbis_ess_options* o, EssState* st);
 mbis_status ess_issue(mbis_ctx* c, EssState* st, const EssBuffers& buf, cudaStream_t s);
 mbis_status ess_complete(mbis_ctx* c, EssState* st);

@@ -331,6 +331,37 @@ def test_ess_loop_equals_manual_batches_and_refit_raises_efficiency(m, torch, ti
         m.mbis_destroy(ctx)
 
 
+def test_ess_loop_pools_refit_batches_up_to_the_cap(m, torch, tiny):
+    """a7 with refit_min_ess: a refit batch short of it pools with the next ones; with a
+    floor that no pool reaches, each refit takes 16 batches; with no floor (0) the loop is
+    the per-batch rule (one batch per refit)."""
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.MIXED)
+    try:
+        P, batch = len(prop["ids"]), 4096
+        bufs = [torch.empty((P, batch), dtype=torch.float64, device="cuda")] + \
+               [torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(4)]
+        set_metric(m, ctx, prop)
+        s0, nd0, nu0 = m.mbis_run_to_ess(ctx, *bufs, ess_target=300.0, batch=batch, max_samples=1 << 22,
+                                         seed=spec.draw_seed, refine=1, refine_scale=1.2)
+        assert nd0 == nu0 + batch and s0["ess"] >= 300.0
+        set_metric(m, ctx, prop)
+        s1, nd1, nu1 = m.mbis_run_to_ess(ctx, *bufs, ess_target=300.0, batch=batch, max_samples=1 << 22,
+                                         seed=spec.draw_seed, refine=1, refine_scale=1.2, refit_min_ess=1e15)
+        assert nd1 == nu1 + 16 * batch and s1["ess"] >= 300.0 and s1["n"] == nu1
+        set_metric(m, ctx, prop)
+        s2, nd2, nu2 = m.mbis_run_to_ess(ctx, *bufs, ess_target=300.0, batch=batch, max_samples=1 << 22,
+                                         seed=spec.draw_seed, refine=2, refine_scale=1.2, refit_min_ess=1e15)
+        assert nd2 == nu2 + 32 * batch and s2["ess"] >= 300.0
+        # the loop stops at max_samples while pooling, with nothing in the estimate
+        set_metric(m, ctx, prop)
+        s3, nd3, nu3 = m.mbis_run_to_ess(ctx, *bufs, ess_target=300.0, batch=batch, max_samples=5 * batch,
+                                         seed=spec.draw_seed, refine=1, refit_min_ess=1e15)
+        assert nd3 == 5 * batch and nu3 == 0 and s3["n"] == 0
+    finally:
+        m.mbis_destroy(ctx)
+
+
 def test_bbh_time_marginalised_tensor_core_matches_oracle(m, torch, bbh):
     """The tcgen05 time-shift contraction (split TF32, FP32 accumulation in TMEM) against
     the oracle; 300 samples = one full CTA of 256 and a ragged second one."""
