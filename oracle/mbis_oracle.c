@@ -19,8 +19,12 @@
  *   masses / Jacobian .......... round trip through an independent chirp-mass formula;
  *                                finite-difference determinant
  *   TaylorF2 non-spinning ...... series of -E'(v)/F(v) from the PN energy and flux
+ *   TaylorF2 spin-orbit ........ 1.5, 2.5, 3 and 3.5PN terms re-derived from the
+ *                                spin-orbit PN energy and flux, every mass ratio
+ *   TaylorF2 spins, test mass .. every spin term at eta -> 0 re-derived from the Kerr
+ *                                circular-orbit energy and the perturbative flux
  *   TaylorF2 1.5PN/2PN spins ... chi_s/chi_a form vs the (beta, sigma) form used here
- *   TaylorF2 spins, all orders . test-mass limit (secondary spin drops out); label swap
+ *   TaylorF2 3PN spin-spin ..... the per-body (kappa = 1) form; label swap
  *   amplitude .................. SPA of the quadrupole chirp; flat-PSD closed-form <h|h>
  *   antenna / delays ........... zenith, arm and bisector special cases; psi invariance;
  *                                baseline light-travel time; delay == shifted t_c
@@ -42,8 +46,6 @@
  *                                Gaussian posterior of a linear model (normal CDF)
  *   relative binning ........... exact at the fiducial and with one frequency per bin;
  *                                second-order convergence in the bin width
- * Parity unpinned: the physical values of the 2.5PN, 3PN and 3.5PN aligned-spin
- * coefficients (only their test-mass limit and label symmetry are pinned).
  */
 #include <complex.h>
 #include <math.h>
@@ -162,8 +164,9 @@ double or_mass_jacobian(double mc, double q) {
  * the spin terms.  The 1.5PN and 2PN spin terms are written here in the (beta, sigma)
  * form so that a test can compare them with the chi_s/chi_a form.  Readings: the GW
  * phase convention h ~ exp(-i Psi); the 2.5PN log term is (1 + 3 ln v) with no v_lso;
- * phi_c is the GW phase; spin-cubed 3.5PN and quadrupole-monopole (kappa != 1) terms
- * are omitted.
+ * phi_c is the GW phase; the spin-squared (tail) and spin-cubed 3.5PN terms and the
+ * quadrupole-monopole (kappa != 1) terms are omitted.  The delta chi_a term of the 2.5PN
+ * factor carries -140/9 eta: the sign that the spin-orbit energy and flux imply.
  *
  * Returns sum_n phi_n(v) v^n for n = 0..7, the bracket of
  *   Psi(f) = 2 pi f t_c - phi_c - pi/4 + 3 / (128 eta v^5) * bracket,  v = (pi M f)^(1/3). */
@@ -184,7 +187,7 @@ double or_pn_bracket(double v, double m1, double m2, double chi1, double chi2) {
   double p4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta2 - 10.0 * sigma;
   double p5 = (1.0 + 3.0 * log(v)) *
               (pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) +
-               delta * (-732985.0 / 2268.0 + 140.0 / 9.0 * eta) * chia +
+               delta * (-732985.0 / 2268.0 - 140.0 / 9.0 * eta) * chia +
                (-732985.0 / 2268.0 + 24260.0 / 81.0 * eta + 340.0 / 9.0 * eta2) * chis);
   double p6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 -
               6848.0 / 21.0 * (OR_EULER_GAMMA + log(4.0 * v)) +

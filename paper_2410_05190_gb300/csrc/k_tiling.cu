@@ -251,7 +251,7 @@ __device__ __forceinline__ void phase_coeffs_f32(float q, float chi1, float chi2
   const float phi4 = (float)(15293365.0 / 508032.0) + (float)(27145.0 / 504.0) * eta + (float)(3085.0 / 72.0) * e2 +
                      (-50.625f + 200.f * eta) * xa * xa - 101.25f * dm * xa * xs + (-50.625f + 2.5f * eta) * xs * xs;
   const float c5 = pi * ((float)(38645.0 / 756.0) - (float)(65.0 / 9.0) * eta) +
-                   dm * ((float)(-732985.0 / 2268.0) + (float)(140.0 / 9.0) * eta) * xa +
+                   dm * ((float)(-732985.0 / 2268.0) - (float)(140.0 / 9.0) * eta) * xa +
                    ((float)(-732985.0 / 2268.0) + (float)(24260.0 / 81.0) * eta + (float)(340.0 / 9.0) * e2) * xs;
   const float a6 = (float)(11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * kPi * kPi -
                            6848.0 / 21.0 * (kEulerGamma + 1.3862943611198906)) +

@@ -61,7 +61,7 @@ MBIS_HD PNTerms pn_terms(double eta, double dm, double xs, double xa) {
   t.phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * e2 +
            (-405.0 / 8.0 + 200.0 * eta) * xa * xa - 405.0 / 4.0 * dm * xa * xs +
            (-405.0 / 8.0 + 5.0 / 2.0 * eta) * xs * xs;
-  t.c5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) + dm * (-732985.0 / 2268.0 + 140.0 / 9.0 * eta) * xa +
+  t.c5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) + dm * (-732985.0 / 2268.0 - 140.0 / 9.0 * eta) * xa +
          (-732985.0 / 2268.0 + 24260.0 / 81.0 * eta + 340.0 / 9.0 * e2) * xs;
   t.a6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * (kEulerGamma + kLn4) +
          (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta + 76055.0 / 1728.0 * e2 - 127825.0 / 1296.0 * e3 +
