@@ -102,7 +102,6 @@ class ClockSampler:
 def event_setup(m, w, spec, dets_np):
     """Synthetic data and proposal for one event through the library's own helpers:
     injection + noise (mbis_inject), Fisher-metric Gaussian proposal (mbis_fisher)."""
-    from paper_2410_05190_gb300.proposal import fisher_proposal
     n = w.n_bins
     psd1 = m.mbis_psd_aligo(w.f_lo, w.df, n)
     psd = np.tile(psd1, (w.n_det, 1))
@@ -121,8 +120,8 @@ def event_setup(m, w, spec, dets_np):
     ctx = m.mbis_create(strain, psd, dets, w.f_lo, w.df, th, gmst=spec.gmst, precision=m.FP64, marg=w.marg,
                         dmin=w.dmin, dmax=w.dmax)
     try:
-        prop = fisher_proposal(m, ctx, th, w.sampled, w.marg, scale=w.scale, box_sigmas=w.box_sigmas,
-                               chi_max=w.chi_max, dmin=w.dmin, dmax=w.dmax, prior_flags=w.prior_flags)
+        prop = m.fisher_proposal(ctx, th, w.sampled, scale=w.scale, box_sigmas=w.box_sigmas, chi_max=w.chi_max,
+                                 dmin=w.dmin, dmax=w.dmax, prior_flags=w.prior_flags)
     finally:
         m.mbis_destroy(ctx)
     return dict(spec=spec, th=th, strain=strain, psd=psd, dets=dets, prop=prop, w=w)

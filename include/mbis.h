@@ -87,7 +87,6 @@ typedef struct {
   int32_t n_tshift;     /* TIME: number of shifts J (tau_j = (j - J/2) dt_shift) */
   double dt_shift;      /* TIME: shift spacing, s */
   double dmin_mpc, dmax_mpc;  /* DISTANCE: prior p(d) ~ d^2 on [dmin, dmax] */
-  int32_t debug_checks; /* nonzero: kernels check indices and report MBIS_E_INVALID */
 } mbis_options;
 
 /* Running reducer state and its derived summary (Eq. 6).  max_logw = -inf and ess = 0
@@ -163,7 +162,11 @@ mbis_status mbis_reduce(mbis_ctx* ctx, int64_t n, const double* loglike, const d
  * loads it, kept until exit) with room for MBIS_NOALLOC_MAX_SAMPLES samples per call;
  * larger n returns MBIS_E_INVALID with a message in mbis_last_error(NULL).  The first call
  * on each device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls share the
+ * device current; make that first call before any stream capture.  A lookup that fails is
+ * not remembered: the next call tries again.  With lazy module loading (the CUDA default)
+ * that first call also loads the library's module onto the device, a one-time device
+ * allocation of about 128 KiB that may synchronise: warm the entry point up once at
+ * start-up (for example with n = 1) to keep it off the critical path.  All calls share the
  * array and it keeps the last call's contents; each call zeroes the part that must start
  * at zero.  Calls that overlap on the GPU (other streams or threads) race on it.
  * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
@@ -186,6 +189,12 @@ mbis_status mbis_weighted_moments(mbis_ctx* ctx, int64_t n, const double* theta,
  * sampled slots and prior of the last mbis_set_metric; no table is rebuilt.
  * Errors: MBIS_E_STATE, MBIS_E_INVALID. */
 mbis_status mbis_set_proposal(mbis_ctx* ctx, const double* mean, const double* chol_lower, double scale);
+
+/* The current Gaussian proposal (as set by mbis_set_metric / mbis_set_proposal, or refitted
+ * by the ESS loop): mean_out (host, P), chol_out (host, P x P row-major lower), scale_out
+ * (host); each may be NULL.  Errors: MBIS_E_INVALID (null context), MBIS_E_STATE (no
+ * metric; reported by mbis_last_error(NULL)). */
+mbis_status mbis_get_proposal(const mbis_ctx* ctx, double* mean_out, double* chol_out, double* scale_out);
 
 typedef struct {
   double ess_target;    /* stop once the running ESS reaches this */
@@ -237,8 +246,9 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
  * summaries (this step alone).  Synchronises the batch's own stream. */
 mbis_status mbis_batch_step(mbis_batch* b, uint64_t step, mbis_summary* out);
 
-/* Times the persistent launch for 2, 4, 6 and 8 CTAs per SM on the current samples and keeps
- * the fastest (re-capturing the step graph).  grid_out / ms_out (host, nullable). */
+/* Times the persistent launch for 2, 4, 6 and 7 CTAs per SM (7 is the most that fit) on the
+ * current samples and keeps the fastest (re-capturing the step graph).  grid_out / ms_out
+ * (host, nullable). */
 mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out);
 
 /* The persistent likelihood launch alone, on the batch's current samples, on a caller
@@ -490,6 +500,19 @@ mbis_status mbis_rb_use(mbis_ctx* ctx, int32_t on);
 mbis_status mbis_rb_edges(const mbis_ctx* ctx, const double* theta0, double n_sigma, double eps_rad, int32_t max_bins,
                           int32_t* edges, int32_t* n_rb);
 
+/* What mbis_set_metric built for the context (diagnostics; not in the paper). */
+typedef struct {
+  int32_t tables;    /* -1: none yet; 1: one folded table (sky and orientation fixed); 0: per detector */
+  int32_t n_rows;    /* rows of the likelihood tables: 1 folded, n_det per detector, 0 none */
+  int32_t ff_phase;  /* MBIS_MIXED: 1 when anchor blocks are entered in float-float arithmetic
+                        (every phase term below 2^16 turns), 0 in FP64; -1 otherwise */
+  int32_t n_blocks;  /* MBIS_MIXED: anchor blocks of the phase plan */
+  int32_t P;         /* sampled slots (0 without a metric) */
+} mbis_ctx_info;
+
+/* Errors: MBIS_E_INVALID (null argument; reported by mbis_last_error(NULL)). */
+mbis_status mbis_get_info(const mbis_ctx* ctx, mbis_ctx_info* out);
+
 /* Running state merged by mbis_reduce(accumulate != 0); mbis_reset_running clears it. */
 mbis_status mbis_get_running(const mbis_ctx* ctx, mbis_summary* out);
 mbis_status mbis_reset_running(mbis_ctx* ctx);
@@ -522,6 +545,46 @@ mbis_status mbis_inject(const mbis_freq_grid* grid, int32_t n_det, const mbis_de
  * Errors: MBIS_E_INVALID, MBIS_E_OOM, MBIS_E_CUDA. */
 mbis_status mbis_fisher(mbis_ctx* ctx, const double* theta, int32_t P, const int32_t* ids, const double* steps,
                         double* gamma_out);
+
+/* Settings of the Gaussian proposal in the Fisher metric (mbis_fisher_proposal). */
+typedef struct {
+  double scale;         /* width scale s: the proposal is N(theta0, s^2 Gamma^-1) (> 0) */
+  double box_sigmas;    /* prior box of Mc, q and t_c: theta0 +- box_sigmas s sigma (> 0) */
+  double chi_max;       /* prior of chi1z, chi2z: [-chi_max, chi_max] (0 < chi_max < 1) */
+  double dmin_mpc, dmax_mpc;  /* prior range of a sampled d_L (0 < dmin < dmax) */
+} mbis_proposal_options;
+
+/* The Gaussian proposal of Sec. II A from a Fisher matrix: the metric of the inner product
+ * of Eq. 1 at the trigger theta0 (host, 11 slots), gamma (host, N x N row-major, N = P +
+ * n_marg) over the sampled slots ids (host, P) followed by the slots the likelihood
+ * marginalises, marg_ids (host, n_marg; phi_c under phase, d_L under distance
+ * marginalisation).  Steps, in this order:
+ *   1. the marginalised slots are projected out: G = A - B C^-1 B^T (Schur complement);
+ *   2. for slots the data barely constrain (q, spins, angles, a sampled d_L) G gains
+ *      12 / width^2 on its diagonal -- the inverse variance of a uniform distribution over
+ *      the slot's prior range (q: 2; chi: 2 chi_max; RA, phi_c: 2 pi; dec, psi, iota: pi;
+ *      d_L: dmax - dmin) -- so the proposal stays inside the prior;
+ *   3. covariance = G^-1 (symmetrised), chol_out = its lower Cholesky factor;
+ *   4. mean_out = theta0 on the sampled slots; the prior box lo_out / hi_out is theta0 +-
+ *      box_sigmas scale sigma_p for Mc and t_c (and for q, whose lower end is at least 1),
+ *      [-chi_max, chi_max] for the spins and the physical range for the other slots.
+ * Outputs (host): mean_out [P], chol_out [P x P] row-major lower, lo_out, hi_out [P]: the
+ * arguments of mbis_set_metric.  Pure host arithmetic: needs no GPU and no context;
+ * failures are reported by mbis_last_error(NULL).
+ * Errors: MBIS_E_INVALID (null, repeated or out-of-range slot, bad option, a matrix that
+ * is not positive definite). */
+mbis_status mbis_proposal_from_fisher(int32_t P, const int32_t* ids, int32_t n_marg, const int32_t* marg_ids,
+                                      const double* gamma, const double* theta0, const mbis_proposal_options* opts,
+                                      double* mean_out, double* chol_out, double* lo_out, double* hi_out);
+
+/* mbis_fisher at theta0 over ids plus the slots the context marginalises (phi_c with
+ * MBIS_MARG_PHASE, d_L with MBIS_MARG_DISTANCE), central-difference steps 1e-6 relative
+ * (Mc), 1e-5 relative (d_L), 1e-5 (chi), 1e-7 s (t_c) and 1e-6 otherwise; then
+ * mbis_proposal_from_fisher.  Same outputs; a slot may not be both sampled and
+ * marginalised.  Errors: as mbis_fisher and mbis_proposal_from_fisher. */
+mbis_status mbis_fisher_proposal(mbis_ctx* ctx, const double* theta0, int32_t P, const int32_t* ids,
+                                 const mbis_proposal_options* opts, double* mean_out, double* chol_out,
+                                 double* lo_out, double* hi_out);
 
 /* Self-test of the bounded device-side wait that every kernel uses on its mbarriers (not
  * in the paper): one thread waits on a barrier that nothing completes, gives up after

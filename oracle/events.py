@@ -47,45 +47,51 @@ FISHER_STEPS = {MC: 1e-6, Q: 1e-6, CHI1: 1e-5, CHI2: 1e-5, RA: 1e-6, DEC: 1e-6, 
                 DL: 1e-5, TC: 1e-7, PHIC: 1e-6}
 
 
-def make_proposal(ev, w: workloads.Workload, th):
-    """Gaussian proposal in the Fisher metric at the trigger (here the injection): the
-    marginalised slots (phi_c, d_L) are projected out by Schur complement; a weak
-    Gaussian term of the prior width keeps directions the data cannot measure inside the
-    prior; the prior box of Mc, q, t_c is +-box_sigmas proposal sigmas."""
-    sampled = list(w.sampled)
+def marginalised_slots(marg):
+    """Slots the likelihood marginalises, in the order the proposal projects them out."""
     extra = []
-    if w.marg & workloads.MARG_PHASE:
+    if marg & workloads.MARG_PHASE:
         extra.append(PHIC)
-    if w.marg & workloads.MARG_DISTANCE:
+    if marg & workloads.MARG_DISTANCE:
         extra.append(DL)
-    ids = sampled + extra
-    steps = np.array([FISHER_STEPS[i] * (th[i] if i in (MC, DL) else 1.0) for i in ids])
-    ev0 = ev.with_marg(0)
-    G = oracle.fisher(ev0, th, ids, steps)
+    return extra
+
+
+def fisher_steps(ids, th):
+    return np.array([FISHER_STEPS[i] * (th[i] if i in (MC, DL) else 1.0) for i in ids])
+
+
+def proposal_from_fisher(G, sampled, th, scale, box_sigmas, chi_max, dmin, dmax, prior_flags=0):
+    """Gaussian proposal from the Fisher matrix G over sampled + marginalised slots (the
+    last len(G) - len(sampled) rows): the marginalised slots are projected out by Schur
+    complement; a weak Gaussian term of the prior width keeps directions the data cannot
+    measure inside the prior; the prior box of Mc, q, t_c is +-box_sigmas proposal sigmas."""
+    sampled = list(sampled)
     P = len(sampled)
-    if extra:
+    G = np.array(G, dtype=np.float64)
+    if len(G) > P:
         A, B, Cm = G[:P, :P], G[:P, P:], G[P:, P:]
         G = A - B @ np.linalg.solve(Cm, B.T)
     else:
-        G = G[:P, :P]
-    width = {Q: 2.0, CHI1: 2 * w.chi_max, CHI2: 2 * w.chi_max, RA: 2 * math.pi, DEC: math.pi, PSI: math.pi,
-             IOTA: math.pi, PHIC: 2 * math.pi, DL: w.dmax - w.dmin}
+        G = G[:P, :P].copy()
+    width = {Q: 2.0, CHI1: 2 * chi_max, CHI2: 2 * chi_max, RA: 2 * math.pi, DEC: math.pi, PSI: math.pi,
+             IOTA: math.pi, PHIC: 2 * math.pi, DL: dmax - dmin}
     for p, i in enumerate(sampled):
         if i in width:
             G[p, p] += 12.0 / width[i] ** 2
     cov = np.linalg.inv(G)
     cov = 0.5 * (cov + cov.T)
     L = np.linalg.cholesky(cov)
-    sig = np.sqrt(np.diag(cov)) * w.scale
+    sig = np.sqrt(np.diag(cov)) * scale
     mean = np.array([th[i] for i in sampled])
     lo, hi = np.zeros(P), np.zeros(P)
     for p, i in enumerate(sampled):
         if i in (CHI1, CHI2):
-            lo[p], hi[p] = -w.chi_max, w.chi_max
+            lo[p], hi[p] = -chi_max, chi_max
         elif i == Q:
-            lo[p], hi[p] = max(1.0, th[i] - w.box_sigmas * sig[p]), th[i] + w.box_sigmas * sig[p]
+            lo[p], hi[p] = max(1.0, th[i] - box_sigmas * sig[p]), th[i] + box_sigmas * sig[p]
         elif i in (MC, TC):
-            lo[p], hi[p] = th[i] - w.box_sigmas * sig[p], th[i] + w.box_sigmas * sig[p]
+            lo[p], hi[p] = th[i] - box_sigmas * sig[p], th[i] + box_sigmas * sig[p]
         elif i in (RA, PHIC):
             lo[p], hi[p] = 0.0, 2 * math.pi
         elif i == PSI:
@@ -95,6 +101,18 @@ def make_proposal(ev, w: workloads.Workload, th):
         elif i == IOTA:
             lo[p], hi[p] = 0.0, math.pi
         elif i == DL:
-            lo[p], hi[p] = w.dmin, w.dmax
-    return dict(ids=np.array(sampled, dtype=np.int32), mean=mean, chol=L, scale=w.scale, lo=lo, hi=hi,
-                flags=w.prior_flags)
+            lo[p], hi[p] = dmin, dmax
+    return dict(ids=np.array(sampled, dtype=np.int32), mean=mean, chol=L, scale=scale, lo=lo, hi=hi,
+                flags=prior_flags)
+
+
+def proposal_fisher(ev, w: workloads.Workload, th):
+    """The oracle's Fisher matrix over the sampled slots followed by the marginalised ones."""
+    ids = list(w.sampled) + marginalised_slots(w.marg)
+    return oracle.fisher(ev.with_marg(0), th, ids, fisher_steps(ids, th))
+
+
+def make_proposal(ev, w: workloads.Workload, th):
+    """Gaussian proposal in the Fisher metric at the trigger (here the injection)."""
+    G = proposal_fisher(ev, w, th)
+    return proposal_from_fisher(G, w.sampled, th, w.scale, w.box_sigmas, w.chi_max, w.dmin, w.dmax, w.prior_flags)

@@ -49,7 +49,17 @@ class Event(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("marg", C.c_uint32), ("n_tshift", C.c_int32), ("dt_shift", C.c_double),
-                ("dmin_mpc", C.c_double), ("dmax_mpc", C.c_double), ("debug_checks", C.c_int32)]
+                ("dmin_mpc", C.c_double), ("dmax_mpc", C.c_double)]
+
+
+class ProposalOptions(C.Structure):
+    _fields_ = [("scale", C.c_double), ("box_sigmas", C.c_double), ("chi_max", C.c_double),
+                ("dmin_mpc", C.c_double), ("dmax_mpc", C.c_double)]
+
+
+class CtxInfo(C.Structure):
+    _fields_ = [("tables", C.c_int32), ("n_rows", C.c_int32), ("ff_phase", C.c_int32), ("n_blocks", C.c_int32),
+                ("P", C.c_int32)]
 
 
 class Summary(C.Structure):
@@ -115,9 +125,13 @@ def _load():
         "mbis_psd_aligo": [p, p],
         "mbis_inject": [p, i32, p, p, d, p, u64, i32, p, p],
         "mbis_fisher": [p, p, i32, p, p, p],
+        "mbis_proposal_from_fisher": [i32, p, i32, p, p, p, p, p, p, p, p],
+        "mbis_fisher_proposal": [p, p, i32, p, p, p, p, p, p],
         "mbis_reduce_noalloc": [i64, p, p, p, p, p, p],
         "mbis_weighted_moments": [p, i64, p, p, p, p, p],
         "mbis_set_proposal": [p, p, p, d],
+        "mbis_get_proposal": [p, p, p, p],
+        "mbis_get_info": [p, p],
         "mbis_run_to_ess": [p, p, p, p, p, p, p, p, p, p, p],
         "mbis_batch_create": [i32, p, p, p, p],
         "mbis_batch_step": [p, u64, p],
@@ -216,7 +230,7 @@ def make_detectors(vertex, xarm, yarm):
 
 # ------------------------------------------------------------------------------- entry points
 def mbis_create(strain, psd, detectors, f_lo, df, fixed, gmst=0.0, precision=MIXED, marg=MARG_PHASE, n_tshift=128,
-                dt_shift=1e-4, dmin=10.0, dmax=1000.0, debug_checks=0):
+                dt_shift=1e-4, dmin=10.0, dmax=1000.0):
     """strain: complex host array [n_det, n_bins] (complex128 or complex64); psd: float64
     host array [n_det, n_bins]; detectors: ctypes array from make_detectors; fixed: 11
     slot values.  Returns the context handle (int)."""
@@ -231,7 +245,7 @@ def mbis_create(strain, psd, detectors, f_lo, df, fixed, gmst=0.0, precision=MIX
     n_det, n_bins = strain.shape
     ev = Event(n_det, dtype, strain.ctypes.data, gmst, (C.c_double * 11)(*map(float, fixed)))
     grid = FreqGrid(f_lo, df, n_bins)
-    opts = Options(precision, marg, n_tshift, dt_shift, dmin, dmax, debug_checks)
+    opts = Options(precision, marg, n_tshift, dt_shift, dmin, dmax)
     out = C.c_void_p()
     _check(_lib.mbis_create(C.byref(ev), psd.ctypes.data, detectors, C.byref(grid), C.byref(opts), C.byref(out)))
     return out.value
@@ -277,6 +291,21 @@ def mbis_set_proposal(ctx, mean, chol_lower, scale):
     m, pm = _host(mean, np.float64)
     L, pL = _host(chol_lower, np.float64)
     _check(_lib.mbis_set_proposal(ctx, pm, pL, scale), ctx)
+
+
+def mbis_get_info(ctx):
+    """What mbis_set_metric built: tables (1 folded, 0 per detector, -1 none), n_rows,
+    ff_phase (1 float-float block entry, 0 FP64, -1 not mixed), n_blocks, P."""
+    out = CtxInfo()
+    _check(_lib.mbis_get_info(ctx, C.byref(out)))
+    return {k: getattr(out, k) for k, _ in out._fields_}
+
+
+def mbis_get_proposal(ctx, P):
+    """The context's current proposal over its P sampled slots: (mean [P], chol [P, P], scale)."""
+    mean, chol, sc = np.zeros(11), np.zeros(121), C.c_double()
+    _check(_lib.mbis_get_proposal(ctx, mean.ctypes.data, chol.ctypes.data, C.byref(sc)), None if ctx is None else ctx)
+    return mean[:P].copy(), chol[:P * P].reshape(P, P).copy(), sc.value
 
 
 def mbis_run_to_ess(ctx, theta, log_q, log_prior, loglike, weights, ess_target, batch, max_samples, seed, refine=0,
@@ -364,7 +393,7 @@ def mbis_server_submit(server, strain, psd, detectors, f_lo, df, fixed, param_id
     hi, phi = _host(prior_hi, np.float64)
     req = Request(Event(n_det, dtype, strain.ctypes.data, gmst, (C.c_double * 11)(*map(float, fixed))),
                   psd.ctypes.data, C.cast(detectors, C.c_void_p), FreqGrid(f_lo, df, n_bins),
-                  Options(precision, marg, n_tshift, dt_shift, dmin, dmax, 0), len(ids), pid, pm, pL, scale, plo, phi,
+                  Options(precision, marg, n_tshift, dt_shift, dmin, dmax), len(ids), pid, pm, pL, scale, plo, phi,
                   prior_flags, EssOptions(ess_target, batch, max_samples, refine, refine_scale, seed, refit_min_ess), tag)
     if rb_fiducial is not None:
         fid, pfid = _host(rb_fiducial, np.float64)
@@ -475,6 +504,40 @@ def mbis_fisher(ctx, theta, ids, steps):
     g = np.zeros((P, P))
     _check(_lib.mbis_fisher(ctx, pth, P, pid, pst, g.ctypes.data), ctx)
     return g
+
+
+def _proposal_dict(ids, mean, chol, lo, hi, scale, prior_flags):
+    return dict(ids=ids, mean=mean, chol=chol, scale=scale, lo=lo, hi=hi, flags=prior_flags)
+
+
+def mbis_proposal_from_fisher(ids, marg_ids, gamma, theta0, scale=1.5, box_sigmas=10.0, chi_max=0.99, dmin=10.0,
+                              dmax=1000.0, prior_flags=0):
+    """Proposal dict (ids, mean, chol, scale, lo, hi, flags) for mbis_set_metric from a
+    Fisher matrix over ids + marg_ids (host arithmetic in the library; no GPU needed)."""
+    ids, pid = _host(ids, np.int32)
+    mids, pmid = _host(marg_ids, np.int32)
+    g, pg = _host(gamma, np.float64)
+    th, pth = _host(theta0, np.float64)
+    P = len(ids)
+    mean, chol, lo, hi = np.zeros(P), np.zeros((P, P)), np.zeros(P), np.zeros(P)
+    o = ProposalOptions(scale, box_sigmas, chi_max, dmin, dmax)
+    _check(_lib.mbis_proposal_from_fisher(P, pid, len(mids), pmid if len(mids) else None, pg, pth, C.byref(o),
+                                          mean.ctypes.data, chol.ctypes.data, lo.ctypes.data, hi.ctypes.data))
+    return _proposal_dict(ids, mean, chol, lo, hi, scale, prior_flags)
+
+
+def fisher_proposal(ctx, theta0, sampled, scale=1.5, box_sigmas=10.0, chi_max=0.99, dmin=10.0, dmax=1000.0,
+                    prior_flags=0):
+    """The Gaussian proposal in the Fisher metric at theta0 (11 slots) over the sampled
+    slots, with the slots the context marginalises projected out (mbis_fisher_proposal)."""
+    th, pth = _host(theta0, np.float64)
+    ids, pid = _host(sampled, np.int32)
+    P = len(ids)
+    mean, chol, lo, hi = np.zeros(P), np.zeros((P, P)), np.zeros(P), np.zeros(P)
+    o = ProposalOptions(scale, box_sigmas, chi_max, dmin, dmax)
+    _check(_lib.mbis_fisher_proposal(ctx, pth, P, pid, C.byref(o), mean.ctypes.data, chol.ctypes.data, lo.ctypes.data,
+                                     hi.ctypes.data), ctx)
+    return _proposal_dict(ids, mean, chol, lo, hi, scale, prior_flags)
 
 
 # ------------------------------------------------------------------------------- tiled proposal

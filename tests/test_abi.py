@@ -53,7 +53,8 @@ def test_binding_structures_match_the_header_layout():
     pairs = {"mbis_freq_grid": m.FreqGrid, "mbis_detector": m.Detector, "mbis_event": m.Event,
              "mbis_options": m.Options, "mbis_summary": m.Summary, "mbis_ess_options": m.EssOptions,
              "mbis_server_options": m.ServerOptions, "mbis_request": m.Request, "mbis_result": m.Result,
-             "mbis_server_stats": m.ServerStats, "mbis_tiling_space": m.TilingSpace}
+             "mbis_server_stats": m.ServerStats, "mbis_tiling_space": m.TilingSpace,
+             "mbis_proposal_options": m.ProposalOptions, "mbis_ctx_info": m.CtxInfo}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mbis.h"', "int main(void) {"]
     for cname, py in pairs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

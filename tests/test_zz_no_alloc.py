@@ -1,7 +1,8 @@
 """mbis_reduce_noalloc: the weight reduction for callers that cannot allocate device memory
 (a latency-critical loop, or a framework that owns all device memory).  Through the C ABI
 it must give the same summary and weights as mbis_reduce (which keeps its scratch in a
-context), on two calls in a row, and reject batches larger than its fixed scratch.
+context) and as the FP64 oracle, on calls in a row of falling size, treat NaN and -inf
+log-weights as mbis_reduce does, and reject batches larger than its fixed scratch.
 
 This file sorts last so that a run stopping at the first failure has already run every
 other test; it also passes when run alone in a fresh process."""
@@ -61,6 +62,55 @@ def test_noalloc_reduce_matches_the_context_reduce_on_two_calls(m, torch):
             assert abs(got["ess"] / ref["ess"] - 1) < TOL
             assert abs(got["log_z"] - ref["log_z"]) < TOL * max(1.0, abs(ref["log_z"]))
             np.testing.assert_allclose(w_new.cpu().numpy(), w_ref.cpu().numpy(), rtol=TOL, atol=1e-300)
+    finally:
+        m.mbis_destroy(ctx)
+
+
+def _same(a, b):
+    """Equal, counting NaN equal to NaN."""
+    return (a == b) or (isinstance(a, float) and isinstance(b, float) and math.isnan(a) and math.isnan(b))
+
+
+def test_noalloc_reduce_matches_the_oracle(m, torch):
+    """Against the FP64 CPU reduction on the same inputs; a large call first, then a
+    smaller one whose grid leaves most of the first call's partials in the array."""
+    import oracle
+    for seed, n in [(5, 1 << 22), (6, 3001), (7, 1)]:
+        ll, lp, lq = _inputs(torch, seed, n)
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        got = m.mbis_reduce_noalloc(n, ll, lp, lq, w)
+        ref = oracle.reduce(ll.cpu().numpy(), lp.cpu().numpy(), lq.cpu().numpy(), want_weights=True)
+        assert got["n"] == ref["n"] == n and got["max_logw"] == ref["max_logw"]
+        assert abs(got["ess"] / ref["ess"] - 1) < TOL
+        assert abs(got["log_z"] - ref["log_z"]) < TOL * max(1.0, abs(ref["log_z"]))
+        np.testing.assert_allclose(w.cpu().numpy(), ref["weights"], rtol=TOL, atol=1e-300)
+
+
+def test_noalloc_reduce_treats_nan_and_inf_like_the_context_reduce(m, torch):
+    """A NaN log-weight and -inf weights placed at and around the maximum: whatever the
+    context reduction makes of them, the allocation-free one makes the same."""
+    ctx = _context(m)
+    try:
+        n = 70_000
+        ll, lp, lq = _inputs(torch, 11, n)
+        k = int(torch.argmax(ll + lp - lq))
+        lp[k + 1] = -math.inf               # next to the maximum
+        lp[min(n - 1, k + 2048)] = -math.inf
+        for poison in (None, float("nan")):
+            if poison is not None:
+                ll[n // 3] = poison
+            w_ref = torch.empty(n, dtype=torch.float64, device="cuda")
+            w_new = torch.empty(n, dtype=torch.float64, device="cuda")
+            ref = m.mbis_reduce(ctx, n, ll, lp, lq, w_ref)
+            got = m.mbis_reduce_noalloc(n, ll, lp, lq, w_new)
+            for key in ("n", "max_logw", "all_zero"):
+                assert _same(got[key], ref[key]), (poison, key, got[key], ref[key])
+            for key in ("ess", "log_z", "s1", "s2"):
+                a, b = got[key], ref[key]
+                assert _same(a, b) or abs(a - b) <= TOL * max(1.0, abs(b)), (poison, key, a, b)
+            a, b = w_new.cpu().numpy(), w_ref.cpu().numpy()
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            np.testing.assert_allclose(a[~np.isnan(a)], b[~np.isnan(b)], rtol=TOL, atol=1e-300)
     finally:
         m.mbis_destroy(ctx)
 
