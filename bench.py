@@ -43,8 +43,13 @@ SFU_PER_SM_PER_CLK = 16        # MUFU results per SM per clock (Blackwell)
 SFU_PER_BIN = 2                # one sine and one cosine per (sample, bin)
 N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one loglike_mixed_fold_kernel launch at this
-# workload (2^20 samples), from the full ncu capture in profiles/loglike_mixed_fold_kernel_bns.md
+# workload (2^20 samples), from a full ncu capture of the current kernel version (bench leg
+# `--steps 1 --warmup 3`); not measured inside this run
 FOLD_TRAFFIC_BYTES = 44_097_792 + 264_192
+FOLD_TRAFFIC_SOURCE = ("ncu --set full capture of one launch of this kernel version at this workload "
+                       "(dram__bytes_read.sum + dram__bytes_write.sum); not measured in this run")
+SFU_PEAK_NOTE = ("peak = 152 SM x 16 MUFU results/clk (nominal; sine/cosine measured at 15.1 per SM per clock "
+                 "on this part) x sm_max_mhz / 2 MUFU per (sample, bin)")
 
 
 def peaks():
@@ -141,7 +146,7 @@ class OracleLeg:
     """The FP64 oracle on the host cores, on events of the same workload that the oracle
     builds itself (injection, noise, Fisher proposal): no input comes from the GPU path."""
 
-    def __init__(self, w, specs):
+    def __init__(self, w, specs, threads=None):
         import oracle
         from oracle import events as oev
         oracle.build()
@@ -152,7 +157,7 @@ class OracleLeg:
             s = (ev.strain[..., 0] + 1j * ev.strain[..., 1]).astype(np.complex64)   # the data the GPU holds
             ev.set_strain(np.stack([s.real.astype(np.float64), s.imag.astype(np.float64)], axis=-1))
             self.events.append((spec, ev, th, oev.make_proposal(ev, w, th)))
-        self.cores = os.cpu_count() or 1
+        self.cores = threads or os.cpu_count() or 1
 
     def batch(self, i, n):
         """draw -> likelihood -> weights for n samples of event i; returns seconds."""
@@ -174,6 +179,22 @@ class OracleLeg:
             evals += n
             i += 1
         return evals / used, evals, used
+
+
+def oracle_one_core_rate(n_samples, budget_s):
+    """The same oracle leg on one host core: a child process limited to one OpenMP thread
+    (likelihoods / s of the first event of the workload)."""
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench, workloads; "
+            f"w = workloads.bns_population(n_events=1, n_samples={int(n_samples)}); "
+            f"leg = bench.OracleLeg(w, w.events[:1], threads=1); "
+            f"print(json.dumps(leg.rate({float(budget_s)})))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+        rate, evals, used = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": rate, "unit": UNIT, "cores": 1, "sample": f"{evals} likelihoods ({used:.1f} s)"}
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
+        return {"value": None, "error": str(e)[:200]}
 
 
 # ------------------------------------------------------------------------- GPU arm
@@ -284,8 +305,9 @@ def run_gpu(args, rank, world):
                                            "seconds_to_1e4_at_this_efficiency_median": statistics.median(per_event_s)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbin/s",
                          "frac": achieved / peak, "traffic": FOLD_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
+                         "traffic_source": FOLD_TRAFFIC_SOURCE,
                          "kernel": "loglike_mixed_fold_kernel", "launch_ms": statistics.mean(like_ms),
-                         "note": "peak = 152 SM x 16 MUFU/clk x sm_max_mhz / 2 MUFU per (sample, bin)"},
+                         "note": SFU_PEAK_NOTE},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
@@ -835,14 +857,14 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--events", type=int, default=4, help="resident events per rank")
     ap.add_argument("--samples", type=int, default=1 << 20)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--extras", default="ess,bbh,batch,serve,tiled,pp,rb",
                     help="comma list of further measurements at N=1 (ess, bbh, batch, serve, tiled, pp, rb) or "
                          "'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-compare", type=int, default=0,
-                    help="also process the stream's first K requests serially in FP64 (slow)")
+    ap.add_argument("--serve-compare", type=int, default=3,
+                    help="also process the stream's first K requests serially in FP64 (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -908,7 +930,8 @@ def main():
             rate, evals, secs = leg.rate(args.cpu_budget)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": leg.cores, "kind": "oracle",
                                    "sample": f"{evals} likelihoods of the first event ({secs:.1f} s of FP64 oracle "
-                                             f"work, OpenMP over samples)"}
+                                             f"work, OpenMP over samples)",
+                                   "one_core": oracle_one_core_rate(w.n_samples, max(2.0, args.cpu_budget / 4))}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as tdist

@@ -5,22 +5,28 @@
 //   Re z_j = sum_k Re(a_k) cos(2 pi f_k tau_j) + Im(a_k) sin(2 pi f_k tau_j),  j = 0..127
 //   ln L = ln[(1/128) sum_j exp(Re z_j - H/2)]
 //
-// The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA of 256
-// threads owns two tiles of 128 samples.  Per K-block of 16 bins:
-//   * every thread computes its sample's a_k for the 16 bins, two bins at a time in f32x2
-//     (mixed-precision phase as in the folded kernel: anchors entered in float-float when
-//     the event's phase terms allow it, FP64 otherwise; 32-bit fixed-point turns; FP32
-//     remainder; MUFU sin/cos per detector; each detector's delay and response argument as
-//     one 64-bit fixed-point turn counter) and writes them, split into a TF32 head and an
-//     FP32 tail, into its row of a 128-byte-swizzled K-major shared-memory tile;
+// The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA owns two
+// tiles of 128 samples and runs two threads per sample (512 threads, 16 warps per SM).  Per
+// K-block of 16 bins:
+//   * each thread computes its sample's a_k for one half of the block (8 bins), two bins at
+//     a time in f32x2 (mixed-precision phase as in the folded kernel: anchors entered in
+//     float-float when the event's phase terms allow it, FP64 otherwise; 32-bit fixed-point
+//     turns positioned directly at the thread's first bin; FP32 remainder; MUFU sin/cos per
+//     detector; each detector's delay and response argument as one 64-bit fixed-point turn
+//     counter) and writes them, split into a TF32 head and an FP32 tail, into its sample's
+//     row of a 128-byte-swizzled K-major shared-memory tile;
 //   * the pre-swizzled twiddle tiles (head, tail) of the block arrive by cp.async.bulk;
-//   * one thread issues 3 x 4 tcgen05.mma.kind::tf32 of 128 shifts (M, the twiddle tile) by
-//     256 samples (N, both sample tiles at once) -- head.head + head.tail + tail.head for
-//     each 8-wide K step -- accumulating in TMEM, and commits to an mbarrier that frees the
-//     double buffer two blocks later.
-// The A operand never touches global memory.  After every block each thread reads its own
-// row (its 128 shifts) back from TMEM into FP32 registers; after the last block it applies
-// the log-mean-exp.
+//   * the last warp done issues 3 x 4 tcgen05.mma.kind::tf32 of 128 shifts (M, the twiddle
+//     tile) by 256 samples (N, both sample tiles at once) -- head.head + head.tail +
+//     tail.head for each 8-wide K step -- into a fresh TMEM accumulator, and commits to an
+//     mbarrier.
+// While the tensor core runs block kb the threads compute block kb + 1's rows; then they add
+// block kb's accumulator into running sums kept in the other half of TMEM (FP32,
+// round-to-nearest), which frees the accumulator for block kb + 1.  The per-sample set-up
+// is split between the two threads of a sample (phase coefficients and cut on one, the
+// detector responses and delays on the other) and exchanged through shared memory.  The A
+// operand never touches global memory; after the last block the running sums go through
+// shared memory (transposed) to the log-mean-exp.
 #include "internal.h"
 #include "marg.cuh"
 #include "ffloat.cuh"
@@ -29,25 +35,27 @@
 namespace mbis {
 namespace {
 
-constexpr int kCompute = 256;  // two tiles of 128 samples, one per thread
-constexpr int kTT = kCompute;
+constexpr int kSamples = 256;           // samples per CTA: two tiles of 128, one N = 256 MMA
+constexpr int kTT = 2 * kSamples;       // two threads per sample
 constexpr int kTilesPerCta = 2;
+constexpr int kSegBins = kKBlockBins / 2;  // bins of a K-block per thread
 constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
-constexpr uint32_t kOffA = 0;           // [2 buf][2 tile][2 head/tail][tile]
+constexpr uint32_t kOffA = 0;           // [2 buf][2 head/tail][2 tile][tile]
 constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [2 buf][2 head/tail][tile]
-constexpr uint32_t kSmemBytes = kOffB + 2 * 2 * kTileBytes + 1024;
-static_assert(kTimeShifts * (kCompute + 1) * 4 <= kSmemBytes - 1024, "the final transpose fits the tiles' memory");
+constexpr uint32_t kOffC = kOffB + 2 * 2 * kTileBytes;                 // per-sample phase coefficients
+constexpr int kPhaseFF = 2 * kNumBasis + 2;                            // 32-bit words per sample
+constexpr uint32_t kSmemBytes = kOffC + (uint32_t)kPhaseFF * 4u * kSamples + 1024;
+static_assert(kTimeShifts * (kSamples + 1) * 4 <= kOffC, "the final transpose fits the tiles' memory");
 // D[shift][sample] = twiddle tile (M = 128 shifts) x sample tile (N = 256 samples, both
 // tiles of the CTA in one MMA)
-constexpr uint32_t kIdesc = tc::idesc_tf32(kTimeShifts, kCompute);
+constexpr uint32_t kIdesc = tc::idesc_tf32(kTimeShifts, kSamples);
 // The tensor core aligns and truncates when it accumulates, which biases a long FP32
 // accumulation toward zero by a fraction of an ulp per step.  Each K-block therefore
 // accumulates in TMEM on its own: its two split corrections (head.tail, tail.head, ~2^-11
 // smaller) first, into a fresh accumulator, then its four head.head products; the threads
-// add the block's result into FP32 registers with round-to-nearest adds.  Two accumulators
-// per tile alternate by block, so the drain of block kb - 1 runs while the tensor core works
-// on block kb, and block kb + 1's MMAs wait only for that drain, not for the tensor core.
-// TMEM: per tile [block kb even | block kb odd], 128 columns each.
+// add the block's result into the running sums with round-to-nearest adds.
+// TMEM: [accumulator: columns 0..255 | running sums: columns 256..511], lanes = shifts.
+constexpr uint32_t kRunCol = kSamples;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 // Added to the 32-bit turn count: 256 rounds (rather than truncates) when its top 23 bits
 // become a float mantissa f1 in [1, 2); 2^31 (half a turn) with the -3 pi in the remainder's
@@ -61,14 +69,20 @@ struct State {
   float w;
 };
 
-__device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan, int blk, const PhaseCoeffs& pc,
-                                            const float* cf, State& st) {
+// Per-sample phase coefficients in shared memory, one column per sample (stride kSamples):
+// float-float block entry: pf[j] = hi of C_j, pf[kNumBasis + j] = lo, then cst hi, lo;
+// FP64 block entry: pd[j] = C_j, pd[kNumBasis] = cst.
+__device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan, int blk, const double* pd,
+                                            State& st) {
   const AnchorBlock& B = plan[blk];
-  double x = pc.cst, y = 0.0;
+  double x = pd[kNumBasis * kSamples], y = 0.0;
+  float cf[kNumBasis - 1];
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
-    x = fma(pc.C[j], B.B[j], x);
-    y = fma(pc.C[j], B.dB[j], y);
+    const double c = pd[j * kSamples];
+    if (j < kNumBasis - 1) cf[j] = (float)c;
+    x = fma(c, B.B[j], x);
+    y = fma(c, B.dB[j], y);
   }
   const double w0 = (double)(B.k0 - B.kc);
   const double ph0 = fma(w0, y, x);
@@ -94,17 +108,13 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   st.w = (float)w0;
 }
 
-// Per-sample phase coefficients as float pairs, kept in shared memory (one column per
-// thread): pf[j * kCompute] = hi of C_j, pf[(kNumBasis + j) * kCompute] = lo, then cst hi, lo.
-constexpr int kPhaseFF = 2 * kNumBasis + 2;
-
 __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ plan, int blk, const float* pf,
                                                State& st) {
   const AnchorBlock& B = plan[blk];
-  float xh = pf[2 * kNumBasis * kCompute], xl = pf[(2 * kNumBasis + 1) * kCompute], yh = 0.f, yl = 0.f;
+  float xh = pf[2 * kNumBasis * kSamples], xl = pf[(2 * kNumBasis + 1) * kSamples], yh = 0.f, yl = 0.f;
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
-    const float ch = pf[j * kCompute], cl = pf[(kNumBasis + j) * kCompute];
+    const float ch = pf[j * kSamples], cl = pf[(kNumBasis + j) * kSamples];
     ff_mac(ch, cl, B.Bh[j], B.Bl[j], xh, xl);
     ff_mac(ch, cl, B.dBh[j], B.dBl[j], yh, yl);
   }
@@ -119,7 +129,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   for (int m = 0; m <= kTimeRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * kCompute], B.E[j][m], s);
+    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * kSamples], B.E[j][m], s);
     st.c[m] = s;
   }
   st.c[0] += r0 - w0 * r1;
@@ -133,7 +143,6 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
 
 // turns t -> 64-bit fixed point of frac(t)
 __device__ __forceinline__ uint64_t frac64(double t) {
@@ -151,23 +160,25 @@ template <bool kFF, int kRows>
 __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // bbar[b]: twiddle tiles of buffer b landed; full[b]: the 256 threads wrote A[b]; mbar[b]:
-  // the MMAs reading buffer b completed.  The last thread to finish a block's A rows issues
-  // its MMAs (and the next block's twiddle copies), so the other warps run on while the
-  // tensor core works.  Decisions taken on a wait's outcome are warp-uniform, since TMEM
-  // loads are warp-collective.
+  // bbar[b]: twiddle tiles of buffer b landed; full[b]: every warp wrote its halves of the
+  // rows of A[b] and added the previous block's accumulator into the running sums (one
+  // arrival per warp); mbar[b]: the MMAs reading buffer b completed.  The last warp to arrive
+  // for a block issues its MMAs (and the next block's twiddle copies) from its first lane.  Decisions taken on a wait's outcome are
+  // warp-uniform, since TMEM loads and stores are warp-collective.
   __shared__ __align__(8) uint64_t bbar[2], full[2], mbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_kmax, s_done[2];
   __shared__ int s_issued_b[2], s_issued_m[2];
   __shared__ volatile int s_bad;
-  const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
+  __shared__ int32_t s_kcut[kSamples];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = tid / kSamples, si = tid % kSamples;
+  const int tile = si >> 7, row = si & 127;
   constexpr int nrow = kRows;
-  const int64_t slot = (int64_t)blockIdx.x * kCompute + tid;
+  const int64_t slot = (int64_t)blockIdx.x * kSamples + si;
   const bool active = slot < a.n;
   const int64_t s = active && a.perm != nullptr ? (int64_t)a.perm[slot] : slot;
 
-  // ---- per-sample set-up (FP64)
+  // ---- per-sample set-up (FP64), shared by the sample's two threads
   double par[kNumSlots];
 #pragma unroll
   for (int i = 0; i < kNumSlots; ++i)
@@ -175,79 +186,85 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   const bool valid = active && par[kMc] > 0.0 && par[kQ] > 0.0 && fabs(par[kChi1]) < 1.0 &&
                      fabs(par[kChi2]) < 1.0 && par[kDl] > 0.0 && isfinite(par[kTc]) && isfinite(par[kPhic]) &&
                      isfinite(par[kRa]) && isfinite(par[kDec]) && isfinite(par[kPsi]) && isfinite(par[kIota]);
-  PhaseCoeffs pc;
-  int32_t kcut = 0;
-  double amp = 0.0, H = 0.0;
-  // Detector d enters as |P_d| c_dk e^{-i (Psi_k + 2 pi f_k dt_d - arg P_d)}: the argument of
-  // the response and the delay share one 64-bit fixed-point turn counter (off, stp per bin).
-  float pmag[nrow];
-  uint64_t off[nrow], stp[nrow];
-#pragma unroll
-  for (int d = 0; d < nrow; ++d) {
-    pmag[d] = 0.f;
-    off[d] = 0;
-    stp[d] = 0;
-  }
-  if (valid) {
-    const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], par[kDl],
-                                        a.f_lo, a.df, a.n_bins);
-    pc = ss.pc;
-    kcut = ss.kcut;
-    amp = ss.amp;
-    if (a.fold) {
-      pmag[0] = 1.f;
-      H = amp * amp * a.tfold[kcut];
-    } else {
-      // FP64 for the delays (2 pi f dt to ~1e-7 rad) and for |P|^2 (H scales with it); the
-      // response argument enters the phase at FP32 accuracy
-      double sp, cp, sd, cd, ss, cs;
-      sincos(par[kRa] - a.gmst, &sp, &cp);
-      sincos(par[kDec], &sd, &cd);
-      sincos(par[kPsi], &ss, &cs);
-      const double ci = cos(par[kIota]);
-#pragma unroll
-      for (int d = 0; d < nrow; ++d) {
-        double fp, fc;
-        antenna_trig(a.det_x[d], a.det_y[d], sp, cp, sd, cd, ss, cs, &fp, &fc);
-        const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
-        const double p2 = p_re * p_re + p_im * p_im;
-        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
-        pmag[d] = (float)sqrt(p2);
-        const double arg_turns = (double)atan2f((float)p_im, (float)p_re) * (1.0 / kTwoPi);
-        off[d] = frac64(a.f_lo * dt - arg_turns);
-        stp[d] = frac64(a.df * dt);
-        H += amp * amp * p2 * a.tdet[(int64_t)d * (a.n_bins + 1) + kcut];
-      }
-    }
-  } else {
+  // exchange area in the A tiles' memory (free until the first rows are written):
+  // [detector][sample] |P_d|, delay counter offset and step, |P_d|^2
+  float* x_pm = reinterpret_cast<float*>(sm + kOffA);
+  uint64_t* x_off = reinterpret_cast<uint64_t*>(sm + kOffA + 4 * kMaxDet * kSamples);
+  uint64_t* x_stp = x_off + kMaxDet * kSamples;
+  double* x_p2 = reinterpret_cast<double*>(x_stp + kMaxDet * kSamples);
+  double amp = 0.0;
+  if (half == 0) {
+    // phase coefficients, amplitude and cut
+    PhaseCoeffs pc;
 #pragma unroll
     for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
     pc.cst = 0.0;
-  }
-  float cf[kNumBasis - 1];
-  __shared__ float s_pf[kFF ? kPhaseFF * kCompute : 1];
-  float* pf = s_pf + tid;
-  if constexpr (kFF) {
-#pragma unroll
-    for (int j = 0; j < kNumBasis; ++j) {
-      const float h = (float)pc.C[j];
-      pf[j * kCompute] = h;
-      pf[(kNumBasis + j) * kCompute] = (float)(pc.C[j] - (double)h);
+    int32_t kcut = 0;
+    if (valid) {
+      const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic],
+                                          par[kDl], a.f_lo, a.df, a.n_bins);
+      pc = ss.pc;
+      kcut = ss.kcut;
+      amp = ss.amp;
     }
-    const float h = (float)pc.cst;
-    pf[2 * kNumBasis * kCompute] = h;
-    pf[(2 * kNumBasis + 1) * kCompute] = (float)(pc.cst - (double)h);
-  } else {
+    if constexpr (kFF) {
+      float* pf = reinterpret_cast<float*>(sm + kOffC) + si;
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) cf[j] = (float)pc.C[j];
+      for (int j = 0; j < kNumBasis; ++j) {
+        const float h = (float)pc.C[j];
+        pf[j * kSamples] = h;
+        pf[(kNumBasis + j) * kSamples] = (float)(pc.C[j] - (double)h);
+      }
+      const float h = (float)pc.cst;
+      pf[2 * kNumBasis * kSamples] = h;
+      pf[(2 * kNumBasis + 1) * kSamples] = (float)(pc.cst - (double)h);
+    } else {
+      double* pd = reinterpret_cast<double*>(sm + kOffC) + si;
+#pragma unroll
+      for (int j = 0; j < kNumBasis; ++j) pd[j * kSamples] = pc.C[j];
+      pd[kNumBasis * kSamples] = pc.cst;
+    }
+    s_kcut[si] = kcut;
+  } else if (!a.fold) {
+    // Detector d enters as |P_d| c_dk e^{-i (Psi_k + 2 pi f_k dt_d - arg P_d)}: the argument
+    // of the response and the delay share one 64-bit fixed-point turn counter (off, stp per
+    // bin).  FP64 for the delays (2 pi f dt to ~1e-7 rad) and for |P|^2 (H scales with it);
+    // the response argument enters the phase at FP32 accuracy.
+    double sp = 0.0, cp = 1.0, sd = 0.0, cd = 1.0, ss = 0.0, cs = 1.0, ci = 1.0;
+    if (valid) {
+      sincos(par[kRa] - a.gmst, &sp, &cp);
+      sincos(par[kDec], &sd, &cd);
+      sincos(par[kPsi], &ss, &cs);
+      ci = cos(par[kIota]);
+    }
+#pragma unroll
+    for (int d = 0; d < nrow; ++d) {
+      float pm = 0.f;
+      uint64_t off = 0, stp = 0;
+      double p2 = 0.0;
+      if (valid) {
+        double fp, fc;
+        antenna_trig(a.det_x[d], a.det_y[d], sp, cp, sd, cd, ss, cs, &fp, &fc);
+        const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
+        p2 = p_re * p_re + p_im * p_im;
+        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
+        pm = (float)sqrt(p2);
+        const double arg_turns = (double)atan2f((float)p_im, (float)p_re) * (1.0 / kTwoPi);
+        off = frac64(a.f_lo * dt - arg_turns);
+        stp = frac64(a.df * dt);
+      }
+      x_pm[d * kSamples + si] = pm;
+      x_off[d * kSamples + si] = off;
+      x_stp[d * kSamples + si] = stp;
+      x_p2[d * kSamples + si] = p2;
+    }
   }
-
   if (tid == 0) {
     s_kmax = 0;
     s_bad = 0;
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&bbar[b], 1);
-      tc::mbar_init(&full[b], kCompute);
+      tc::mbar_init(&full[b], kTT / 32);
       tc::mbar_init(&mbar[b], 1);
       s_done[b] = 0;
       s_issued_b[b] = 0;
@@ -259,10 +276,33 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  atomicMax(&s_kmax, kcut);
-  __syncthreads();
+  const int32_t kcut = s_kcut[si];
+  float pmag[nrow];
+  uint64_t off[nrow], stp[nrow];
+  double H = 0.0;
+  if (a.fold) {
+#pragma unroll
+    for (int d = 0; d < nrow; ++d) {
+      pmag[d] = d == 0 ? 1.f : 0.f;
+      off[d] = 0;
+      stp[d] = 0;
+    }
+    if (half == 0 && valid) H = amp * amp * a.tfold[kcut];
+  } else {
+#pragma unroll
+    for (int d = 0; d < nrow; ++d) {
+      pmag[d] = x_pm[d * kSamples + si];
+      off[d] = x_off[d * kSamples + si];
+      stp[d] = x_stp[d * kSamples + si];
+      if (half == 0 && valid) H += amp * amp * x_p2[d * kSamples + si] * a.tdet[(int64_t)d * (a.n_bins + 1) + kcut];
+    }
+  }
+  if (half == 0) atomicMax(&s_kmax, kcut);
+  __syncthreads();  // the exchange area is read before the first rows overwrite it
   const uint32_t tmem = s_tmem;
   const int32_t nkb = (s_kmax + kKBlockBins - 1) / kKBlockBins;
+  const float* pf = reinterpret_cast<const float*>(sm + kOffC) + si;
+  const double* pd = reinterpret_cast<const double*>(sm + kOffC) + si;
 
   unsigned char* sA = sm + kOffA;
   unsigned char* sB = sm + kOffB;
@@ -277,23 +317,26 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   };
   if (tid == 0 && nkb > 0) load_b(0);
   bool bad = false;
-  float zacc[kTimeShifts];  // this sample's Re z_j, summed over drained segments (round to nearest)
+  // TMEM lanes are the shifts, columns the samples.  This warp adds the accumulator into the
+  // running sums for its lane quarter (shifts 32 (warp % 4) + lane) over the 64 samples of
+  // column group warp / 4, with round-to-nearest FP32 adds in block order.
+  const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  auto drain = [&](bool first) {
 #pragma unroll
-  for (int j = 0; j < kTimeShifts; ++j) zacc[j] = 0.f;
-  // TMEM lanes are the shifts, columns the samples: the even blocks' accumulator at column 0,
-  // the odd blocks' at 256.  This thread drains lane 32 (warp % 4) + lane (its warp's lane
-  // quarter) over the 128 samples of half warp / 4: zacc[c] is shift (32 (warp % 4) + lane)
-  // of sample 128 (warp / 4) + c, transposed through shared memory at the end.
-  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kTimeShifts);
-  auto drain = [&](int which) {
-    const uint32_t base = tbase + (uint32_t)(which * kCompute);
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t r[16], q[16];
+      tc::tmem_ld16(tq + c0, r);
+      if (first) {
 #pragma unroll
-    for (int c0 = 0; c0 < kTimeShifts; c0 += 32) {
-      uint32_t r[32];
-      tc::tmem_ld32(base + c0, r);
+        for (int i = 0; i < 16; ++i) q[i] = 0u;
+      } else {
+        tc::tmem_ld16(tq + kRunCol + c0, q);
+      }
 #pragma unroll
-      for (int i = 0; i < 32; ++i) zacc[c0 + i] += __uint_as_float(r[i]);
+      for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(__fadd_rn(__uint_as_float(q[i]), __uint_as_float(r[i])));
+      tc::tmem_st16(tq + kRunCol + c0, r);
     }
+    tc::tmem_wait_st();
   };
 
   State st;
@@ -304,101 +347,135 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   for (int m = 0; m <= kTimeRemDeg; ++m) st.c[m] = 0.f;
   int blk = -1;
   int32_t blk_end = 0;
-  uint32_t cnt[nrow], stepd[nrow];
+  uint32_t base[nrow], stepd[nrow];
   float epsd[nrow];
-  float2 u2 = make_float2(0.f, 1.f);
 #pragma unroll
   for (int d = 0; d < nrow; ++d) {
-    cnt[d] = 0;
+    base[d] = 0;
     stepd[d] = 0;
     epsd[d] = 0.f;
   }
+  // enter plan block blk at its first bin k0: the phase state, and per detector the 32-bit
+  // turn counter at k0, its step per bin, and the fraction of a counter unit the step drops
+  // per bin (as an FP32 slope)
+  auto enter = [&](int32_t k0) {
+    if constexpr (kFF)
+      enter_block_ff(a.plan, blk, pf, st);
+    else
+      enter_block(a.plan, blk, pd, st);
+    blk_end = a.plan[blk].k1;
+#pragma unroll
+    for (int d = 0; d < nrow; ++d) {
+      const uint64_t od = off[d] + (uint64_t)(uint32_t)k0 * stp[d];
+      base[d] = st.acc + (uint32_t)(od >> 32);
+      stepd[d] = st.step + (uint32_t)(stp[d] >> 32);
+      epsd[d] = (float)(uint32_t)stp[d] * (kTwoPiF * 5.421010862427522e-20f);  // 2 pi 2^-64
+    }
+  };
+  int32_t blk_k0 = 0;
   for (int32_t kb = 0; kb < nkb; ++kb) {
     const int b = kb & 1;
-    if (kb >= 2) {
-      // A[b] is free once the MMAs of block kb - 2 completed
-      const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)(((kb - 2) >> 1) & 1));
+    // this thread's half of the block: bins k_seg .. k_seg + 7 -> K values 16 half .. +15 of
+    // its sample's row, 16-byte chunks 4 half .. 4 half + 3.  Buffer b is free: this thread
+    // saw the MMAs of block kb - 2 complete before it drained them.
+    const int32_t k_seg = kb * kKBlockBins + half * kSegBins;
+    const float4* tab = reinterpret_cast<const float4*>(a.cdet32) + (int64_t)(k_seg >> 1);
+    unsigned char* rowA = sA + ((b * 2) * kTilesPerCta + tile) * kTileBytes + row * 128;
+    uint32_t cnt[nrow];
+    float2 wv = f2(0.f), u2 = f2(0.f);  // bin - kc (remainder) and bin - k0 (counter slope)
+#pragma unroll
+    for (int d = 0; d < nrow; ++d) cnt[d] = 0;
+    if (k_seg < kcut) {
+      if (k_seg >= blk_end) {
+        // the plan block holding the first bin (blocks may have begun in the other half)
+        do {
+          ++blk;
+        } while (a.plan[blk].k1 <= k_seg);
+        blk_k0 = a.plan[blk].k0;
+        enter(blk_k0);
+      }
+      const uint32_t u = (uint32_t)(k_seg - blk_k0);
+#pragma unroll
+      for (int d = 0; d < nrow; ++d) cnt[d] = base[d] + u * stepd[d];
+      wv = make_float2(st.w + (float)u, st.w + (float)u + 1.0f);
+      u2 = make_float2((float)u, (float)u + 1.0f);
+    }
+#pragma unroll 1
+    for (int kk = 0; kk < kSegBins; kk += 2) {
+      const int32_t k = k_seg + kk;
+      if (k < kcut && k == blk_end) {  // a plan block begins inside the half (plan blocks start on even bins)
+        ++blk;
+        blk_k0 = k;
+        enter(k);
+#pragma unroll
+        for (int d = 0; d < nrow; ++d) cnt[d] = base[d];
+        wv = make_float2(st.w, st.w + 1.0f);
+        u2 = make_float2(0.f, 1.f);
+      }
+      float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
+      if (k < kcut) {
+        float2 R = f2(st.c[kTimeRemDeg]);
+#pragma unroll
+        for (int m = kTimeRemDeg - 1; m >= 0; --m) R = __ffma2_rn(R, wv, f2(st.c[m]));
+#pragma unroll
+        for (int d = 0; d < nrow; ++d) {
+          const float2 f1 = make_float2(mantissa_turn(cnt[d]), mantissa_turn(cnt[d] + stepd[d]));
+          const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), __ffma2_rn(f2(epsd[d]), u2, R));
+          cnt[d] += 2u * stepd[d];
+          float2 sn, cs;
+          __sincosf(ang.x, &sn.x, &cs.x);
+          __sincosf(ang.y, &sn.y, &cs.y);
+          const float4 c = __ldg(tab + (int64_t)d * (a.n_pad16 / 2) + (kk >> 1));  // re_k, re_k+1, im_k, im_k+1
+          const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
+          const float2 q = __fmul2_rn(f2(pmag[d]), cs), r = __fmul2_rn(f2(pmag[d]), sn);
+          re = __ffma2_rn(cx, q, __ffma2_rn(cy, r, re));
+          imc = __ffma2_rn(cy, q, imc);
+          ims = __ffma2_rn(cx, r, ims);
+        }
+        if (k + 1 >= kcut) {  // odd cut: the second bin of the pair is beyond the ISCO
+          re.y = 0.f;
+          imc.y = 0.f;
+          ims.y = 0.f;
+        }
+      }
+      wv = __fadd2_rn(wv, f2(2.0f));
+      u2 = __fadd2_rn(u2, f2(2.0f));
+      const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
+      float4 hi, lo;
+      // head and tail both rounded to TF32: the tensor core reads a TF32 operand by
+      // truncating an FP32 one, which would bias the tails toward zero
+      hi.x = tc::tf32_round(re.x); lo.x = tc::tf32_round(re.x - hi.x);
+      hi.y = tc::tf32_round(im.x); lo.y = tc::tf32_round(im.x - hi.y);
+      hi.z = tc::tf32_round(re.y); lo.z = tc::tf32_round(re.y - hi.z);
+      hi.w = tc::tf32_round(im.y); lo.w = tc::tf32_round(im.y - hi.w);
+      const int chunk = (half * (kSegBins / 2) + (kk >> 1)) ^ (row & 7);
+      *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
+      *reinterpret_cast<float4*>(rowA + kTilesPerCta * kTileBytes + (chunk << 4)) = lo;
+    }
+    tc::fence_proxy_async();
+    if (kb >= 1) {
+      // block kb - 1's accumulator into the running sums, once its MMAs completed (they ran
+      // while this block's rows were computed); the accumulator is then free for block kb
+      const bool ok = tc::mbar_wait(&mbar[(kb - 1) & 1], (uint32_t)(((kb - 1) >> 1) & 1));
       if (__any_sync(0xffffffffu, !ok || s_bad)) {
         bad = true;
         break;
       }
+      tc::fence_after_sync();
+      drain(kb == 1);
     }
-    const float4* tab = reinterpret_cast<const float4*>(a.cdet32) + (int64_t)kb * (kKBlockBins / 2);
-      // this thread's row of the A operand: 16 bins -> 32 K values -> 8 chunks of 16 bytes.
-      // Bins go in pairs (plan blocks have even starts), two lanes of f32x2 arithmetic.
-      // [buffer][head, tail][tile]: the heads (and tails) of both tiles are one 256-row operand
-      unsigned char* rowA = sA + ((b * 2) * kTilesPerCta + tile) * kTileBytes + row * 128;
-#pragma unroll 1
-      for (int kk = 0; kk < kKBlockBins; kk += 2) {
-        const int32_t k = kb * kKBlockBins + kk;
-        if (k < kcut && k == blk_end) {
-          ++blk;
-          if constexpr (kFF)
-            enter_block_ff(a.plan, blk, pf, st);
-          else
-            enter_block(a.plan, blk, pc, cf, st);
-          blk_end = a.plan[blk].k1;
-          // per-detector 32-bit turn counters from the block's first bin; the fraction of a
-          // counter unit they drop per bin enters the angle as a small FP32 slope
-#pragma unroll
-          for (int d = 0; d < nrow; ++d) {
-            const uint64_t od = off[d] + (uint64_t)(uint32_t)k * stp[d];
-            cnt[d] = st.acc + (uint32_t)(od >> 32);
-            stepd[d] = st.step + (uint32_t)(stp[d] >> 32);
-            epsd[d] = (float)(uint32_t)stp[d] * (kTwoPiF * 5.421010862427522e-20f);  // 2 pi 2^-64
-          }
-          u2 = make_float2(0.f, 1.f);
-        }
-        float2 re = f2(0.f), imc = f2(0.f), ims = f2(0.f);  // im = imc - ims
-        if (k < kcut) {
-          const float2 w = make_float2(st.w, st.w + 1.0f);
-          float2 R = f2(st.c[kTimeRemDeg]);
-#pragma unroll
-          for (int m = kTimeRemDeg - 1; m >= 0; --m) R = __ffma2_rn(R, w, f2(st.c[m]));
-#pragma unroll
-          for (int d = 0; d < nrow; ++d) {
-            {
-              const float2 f1 = make_float2(mantissa_turn(cnt[d]), mantissa_turn(cnt[d] + stepd[d]));
-              const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), __ffma2_rn(f2(epsd[d]), u2, R));
-              cnt[d] += 2u * stepd[d];
-              float2 sn, cs;
-              __sincosf(ang.x, &sn.x, &cs.x);
-              __sincosf(ang.y, &sn.y, &cs.y);
-              const float4 c = __ldg(tab + (int64_t)d * (a.n_pad16 / 2) + (kk >> 1));  // re_k, re_k+1, im_k, im_k+1
-              const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
-              const float2 q = __fmul2_rn(f2(pmag[d]), cs), r = __fmul2_rn(f2(pmag[d]), sn);
-              re = __ffma2_rn(cx, q, __ffma2_rn(cy, r, re));
-              imc = __ffma2_rn(cy, q, imc);
-              ims = __ffma2_rn(cx, r, ims);
-            }
-          }
-          if (k + 1 >= kcut) {  // odd cut: the second bin of the pair is beyond the ISCO
-            re.y = 0.f;
-            imc.y = 0.f;
-            ims.y = 0.f;
-          }
-        }
-        st.w += 2.0f;
-        u2 = __fadd2_rn(u2, f2(2.0f));
-        const float2 im = __fadd2_rn(imc, make_float2(-ims.x, -ims.y));
-        float4 hi, lo;
-        // head and tail both rounded to TF32: the tensor core reads a TF32 operand by
-        // truncating an FP32 one, which would bias the tails toward zero
-        hi.x = tc::tf32_round(re.x); lo.x = tc::tf32_round(re.x - hi.x);
-        hi.y = tc::tf32_round(im.x); lo.y = tc::tf32_round(im.x - hi.y);
-        hi.z = tc::tf32_round(re.y); lo.z = tc::tf32_round(re.y - hi.z);
-        hi.w = tc::tf32_round(im.y); lo.w = tc::tf32_round(im.y - hi.w);
-        const int chunk = (kk >> 1) ^ (row & 7);
-        *reinterpret_cast<float4*>(rowA + (chunk << 4)) = hi;
-        *reinterpret_cast<float4*>(rowA + kTilesPerCta * kTileBytes + (chunk << 4)) = lo;
-      }
-    tc::fence_proxy_async();
-    tc::mbar_arrive(&full[b]);
-    if (atomicAdd(&s_done[b], 1) == kCompute - 1) {
-      // The last thread done with this block issues its MMAs (issuing blocks the thread for
-      // about as long as the tensor core works on them, ~1.6k cycles; a first-finisher
-      // issuer, which has to wait for the others, measured slower), then the next block's
-      // twiddle copies.
+    tc::fence_before_sync();
+    // one arrival per warp, once all its lanes wrote their rows and drained
+    __syncwarp();
+    int done = 0;
+    if (lane == 0) {
+      tc::mbar_arrive(&full[b]);
+      done = atomicAdd(&s_done[b], 1);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (lane == 0 && done == kTT / 32 - 1) {
+      // The last warp done with this block issues its MMAs, then the next block's twiddle
+      // copies (buffer b ^ 1 was read by block kb - 1, whose MMAs this warp saw complete).
       atomicExch(&s_done[b], 0);
       __threadfence_block();
       const uint32_t par = (uint32_t)((kb >> 1) & 1);
@@ -407,24 +484,20 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         tc::fence_after_sync();
         const uint32_t s_base = tc::smem_addr(sA + b * 2 * kTilesPerCta * kTileBytes);  // samples (N)
         const uint32_t w_base = tc::smem_addr(sB + b * 2 * kTileBytes);                 // twiddles (M)
-        {
-          // block kb's accumulator: the two split corrections (twiddle tail x sample head,
-          // twiddle head x sample tail) first, started afresh, then the head x head products
-          const uint32_t d = tmem + (uint32_t)(b * kCompute);
+        // the two split corrections (twiddle tail x sample head, twiddle head x sample tail)
+        // first, started afresh, then the head x head products
 #pragma unroll
-          for (int term = 1; term <= 3; ++term)
+        for (int term = 1; term <= 3; ++term)
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const int tt = term % 3;  // 1: twiddle tail, 2: sample tail, 0: head x head
-              const uint32_t ww = w_base + (tt == 1 ? kTileBytes : 0) + ks * 32;
-              const uint32_t ss = s_base + (tt == 2 ? kTilesPerCta * kTileBytes : 0) + ks * 32;
-              const bool fresh = term == 1 && ks == 0;
-              tc::mma_tf32(d, tc::desc_k_sw128(ww), tc::desc_k_sw128(ss), kIdesc, fresh ? 0u : 1u);
-            }
-        }
+          for (int ks = 0; ks < 4; ++ks) {
+            const int tt = term % 3;  // 1: twiddle tail, 2: sample tail, 0: head x head
+            const uint32_t ww = w_base + (tt == 1 ? kTileBytes : 0) + ks * 32;
+            const uint32_t ss = s_base + (tt == 2 ? kTilesPerCta * kTileBytes : 0) + ks * 32;
+            const bool fresh = term == 1 && ks == 0;
+            tc::mma_tf32(tmem, tc::desc_k_sw128(ww), tc::desc_k_sw128(ss), kIdesc, fresh ? 0u : 1u);
+          }
         tc::commit(&mbar[b]);
         ++s_issued_m[b];
-        // buffer b ^ 1 is free once the MMAs of block kb - 1 completed
         if (kb + 1 < nkb) {
           ok = kb < 1 || tc::mbar_wait(&mbar[b ^ 1], (uint32_t)(((kb - 1) >> 1) & 1));
           if (ok) load_b(kb + 1);
@@ -435,18 +508,6 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
       }
     }
-    if (kb >= 1) {
-      // block kb - 1's accumulator, while the tensor core runs block kb into the other one;
-      // every thread drains it before it arrives for block kb + 1, whose MMAs reuse it
-      const bool ok = tc::mbar_wait(&mbar[(kb - 1) & 1], (uint32_t)(((kb - 1) >> 1) & 1));
-      if (__any_sync(0xffffffffu, !ok || s_bad)) {
-        bad = true;
-        break;
-      }
-      tc::fence_after_sync();
-      drain((kb - 1) & 1);
-      tc::fence_before_sync();
-    }
   }
   if (!bad && nkb > 0) {
     // the last block's accumulator, once its MMAs (and so all) completed
@@ -455,14 +516,14 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
       bad = true;
     } else {
       tc::fence_after_sync();
-      drain((nkb - 1) & 1);
-      tc::fence_before_sync();
+      drain(nkb == 1);
     }
   }
   if (bad) {
     s_bad = 1;
     atomicExch(a.err, (int32_t)MBIS_E_TIMEOUT);
   }
+  tc::fence_before_sync();
   __syncthreads();
   if (tid == 0 && s_bad) {
     // let every copy and MMA issued land (bounded) before the CTA releases its memory
@@ -473,28 +534,37 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   }
   double ll = 0.0;
   if (nkb > 0 && !s_bad) {
-    // every MMA and copy completed: the tiles' shared memory takes the transpose
-    // [shift][sample] (rows padded to 257 floats, conflict-free both ways)
-    constexpr int kT = kCompute + 1;
+    // every MMA and copy completed: the tiles' shared memory takes the running sums,
+    // transposed to [shift][sample] (rows padded to 257 floats, conflict-free both ways)
+    tc::fence_after_sync();
+    constexpr int kT = kSamples + 1;
     float* zt = reinterpret_cast<float*>(sm);
-    const int shift = 32 * (warp & 3) + (tid & 31), col0 = (warp >> 2) * kTimeShifts;
+    const int shift = 32 * (warp & 3) + (tid & 31), col0 = 64 * (warp >> 2);
 #pragma unroll
-    for (int c = 0; c < kTimeShifts; ++c) zt[shift * kT + col0 + c] = zacc[c];
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t r[16];
+      tc::tmem_ld16(tq + kRunCol + c0, r);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) zt[shift * kT + col0 + c0 + i] = __uint_as_float(r[i]);
+    }
     __syncthreads();
-    float m = -INFINITY;
-    for (int j = 0; j < kTimeShifts; ++j) m = fmaxf(m, zt[j * kT + tid]);
-    const double g = amp * a.cscale;  // Re z_j = g * accumulator_j
-    const float gf = (float)g;
-    float sum = 0.f;
-    for (int j = 0; j < kTimeShifts; ++j) sum += __expf(gf * (zt[j * kT + tid] - m));
-    ll = g * (double)m + log((double)sum / kTimeShifts) - 0.5 * H;
+    if (half == 0) {
+      float m = -INFINITY;
+      for (int j = 0; j < kTimeShifts; ++j) m = fmaxf(m, zt[j * kT + si]);
+      const double g = amp * a.cscale;  // Re z_j = g * running sum_j
+      const float gf = (float)g;
+      float sum = 0.f;
+      for (int j = 0; j < kTimeShifts; ++j) sum += __expf(gf * (zt[j * kT + si] - m));
+      // ln of a sum in [1, 128]: FP32 is exact to ~5e-7 absolute
+      ll = g * (double)m + (double)logf(sum * (1.0f / kTimeShifts)) - 0.5 * H;
+    }
   } else if (!s_bad) {
     ll = -0.5 * H;
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc<512>(tmem);
-  if (active) a.out[s] = (bad || s_bad) ? NAN : (valid ? ll : -INFINITY);
+  if (half == 0 && active) a.out[s] = (bad || s_bad) ? NAN : (valid ? ll : -INFINITY);
 }
 
 template <bool kFF, int kRows>
@@ -506,7 +576,7 @@ cudaError_t launch_time(const LikeArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int64_t blocks = (a.n + kCompute - 1) / kCompute;
+  const int64_t blocks = (a.n + kSamples - 1) / kSamples;
   loglike_mixed_time_kernel<kFF, kRows><<<(unsigned)blocks, kTT, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
