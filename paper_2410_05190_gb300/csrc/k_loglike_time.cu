@@ -5,9 +5,9 @@
 //   Re z_j = sum_k Re(a_k) cos(2 pi f_k tau_j) + Im(a_k) sin(2 pi f_k tau_j),  j = 0..127
 //   ln L = ln[(1/128) sum_j exp(Re z_j - H/2)]
 //
-// The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA owns two
-// tiles of 128 samples and runs two threads per sample (512 threads, 16 warps per SM).  Per
-// K-block of 16 bins:
+// The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA owns a
+// tile of 128 samples and runs two threads per sample (256 threads); two CTAs share an SM,
+// so that one's FP64 set-up overlaps the other's blocks.  Per K-block of 16 bins:
 //   * each thread computes its sample's a_k for one half of the block (8 bins), two bins at
 //     a time in f32x2 (mixed-precision phase as in the folded kernel: anchors entered in
 //     float-float when the event's phase terms allow it, FP64 otherwise; 32-bit fixed-point
@@ -15,9 +15,10 @@
 //     detector; each detector's delay and response argument as one 64-bit fixed-point turn
 //     counter) and writes them, split into a TF32 head and an FP32 tail, into its sample's
 //     row of a 128-byte-swizzled K-major shared-memory tile;
-//   * the pre-swizzled twiddle tiles (head, tail) of the block arrive by cp.async.bulk;
+//   * the pre-swizzled twiddle tiles (head, tail) of the block arrive by cp.async.bulk, one
+//     block ahead (the first warp to see a block's MMAs complete requests the next block's);
 //   * the last warp done issues 3 x 4 tcgen05.mma.kind::tf32 of 128 shifts (M, the twiddle
-//     tile) by 256 samples (N, both sample tiles at once) -- head.head + head.tail +
+//     tile) by 128 samples (N, the sample tile) -- head.head + head.tail +
 //     tail.head for each 8-wide K step -- into a fresh TMEM accumulator, and commits to an
 //     mbarrier.
 // While the tensor core runs block kb the threads compute block kb + 1's rows; then they add
@@ -35,26 +36,29 @@
 namespace mbis {
 namespace {
 
-constexpr int kSamples = 256;           // samples per CTA: two tiles of 128, one N = 256 MMA
+constexpr int kSamples = 128;           // samples per CTA: one tile of 128, one N = 128 MMA
 constexpr int kTT = 2 * kSamples;       // two threads per sample
-constexpr int kTilesPerCta = 2;
+constexpr int kCtasPerSm = 2;
+constexpr int kTilesPerCta = 1;
 constexpr int kSegBins = kKBlockBins / 2;  // bins of a K-block per thread
 constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
-constexpr uint32_t kOffA = 0;           // [2 buf][2 head/tail][2 tile][tile]
-constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [2 buf][2 head/tail][tile]
-constexpr uint32_t kOffC = kOffB + 2 * 2 * kTileBytes;                 // per-sample phase coefficients
+constexpr uint32_t kOffA = 0;           // [2 buf][2 head/tail][tile]
+constexpr uint32_t kOffB = kOffA + 2 * kTilesPerCta * 2 * kTileBytes;  // [head/tail][tile], one buffer
+constexpr uint32_t kOffC = kOffB + 2 * kTileBytes;                     // per-sample phase coefficients
 constexpr int kPhaseFF = 2 * kNumBasis + 2;                            // 32-bit words per sample
 constexpr uint32_t kSmemBytes = kOffC + (uint32_t)kPhaseFF * 4u * kSamples + 1024;
 static_assert(kTimeShifts * (kSamples + 1) * 4 <= kOffC, "the final transpose fits the tiles' memory");
-// D[shift][sample] = twiddle tile (M = 128 shifts) x sample tile (N = 256 samples, both
-// tiles of the CTA in one MMA)
+// D[shift][sample] = twiddle tile (M = 128 shifts) x sample tile (N = 128 samples, the CTA's
+// tile)
 constexpr uint32_t kIdesc = tc::idesc_tf32(kTimeShifts, kSamples);
 // The tensor core aligns and truncates when it accumulates, which biases a long FP32
 // accumulation toward zero by a fraction of an ulp per step.  Each K-block therefore
 // accumulates in TMEM on its own: its two split corrections (head.tail, tail.head, ~2^-11
 // smaller) first, into a fresh accumulator, then its four head.head products; the threads
 // add the block's result into the running sums with round-to-nearest adds.
-// TMEM: [accumulator: columns 0..255 | running sums: columns 256..511], lanes = shifts.
+// TMEM (256 columns per CTA): [accumulator: columns 0..127 | running sums: 128..255],
+// lanes = shifts.
+constexpr uint32_t kTmemCols = 2 * kSamples;
 constexpr uint32_t kRunCol = kSamples;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 // Added to the 32-bit turn count: 256 rounds (rather than truncates) when its top 23 bits
@@ -157,18 +161,19 @@ __device__ __forceinline__ uint64_t frac64(double t) {
 // kFloatFloatMaxTurns), otherwise in FP64.  kRows: detector rows of the table (1 when the
 // detectors are folded), a compile-time count so the detectors' chains interleave.
 template <bool kFF, int kRows>
-__global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) {
+__global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(LikeArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // bbar[b]: twiddle tiles of buffer b landed; full[b]: every warp wrote its halves of the
+  // bbar: the twiddle tiles of the current block landed; full[b]: every warp wrote its halves of the
   // rows of A[b] and added the previous block's accumulator into the running sums (one
   // arrival per warp); mbar[b]: the MMAs reading buffer b completed.  The last warp to arrive
-  // for a block issues its MMAs (and the next block's twiddle copies) from its first lane.  Decisions taken on a wait's outcome are
+  // for a block issues its MMAs from its first lane; the first warp to see them complete
+  // requests the next block's twiddle tiles.  Decisions taken on a wait's outcome are
   // warp-uniform, since TMEM loads and stores are warp-collective.
-  __shared__ __align__(8) uint64_t bbar[2], full[2], mbar[2];
+  __shared__ __align__(8) uint64_t bbar, full[2], mbar[2];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_kmax, s_done[2];
-  __shared__ int s_issued_b[2], s_issued_m[2];
+  __shared__ int s_kmax, s_done[2], s_bnext;
+  __shared__ int s_issued_b, s_issued_m[2];
   __shared__ volatile int s_bad;
   __shared__ int32_t s_kcut[kSamples];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = tid / kSamples, si = tid % kSamples;
@@ -262,17 +267,18 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   if (tid == 0) {
     s_kmax = 0;
     s_bad = 0;
+    s_bnext = 0;
+    s_issued_b = 0;
+    tc::mbar_init(&bbar, 1);
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&bbar[b], 1);
       tc::mbar_init(&full[b], kTT / 32);
       tc::mbar_init(&mbar[b], 1);
       s_done[b] = 0;
-      s_issued_b[b] = 0;
       s_issued_m[b] = 0;
     }
     tc::mbar_fence_init();
   }
-  if (warp == 0) tc::tmem_alloc<512>(&s_tmem);
+  if (warp == 0) tc::tmem_alloc<kTmemCols>(&s_tmem);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -307,13 +313,12 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   unsigned char* sA = sm + kOffA;
   unsigned char* sB = sm + kOffB;
   const float* tiles = a.ttiles;
-  // twiddle tiles of block kb into buffer kb & 1 (one thread)
+  // twiddle tiles of block kb into the buffer (one thread; the MMAs of block kb - 1 completed)
   auto load_b = [&](int kb) {
-    const int b = kb & 1;
-    tc::mbar_expect_tx(&bbar[b], 2 * kTileBytes);
-    tc::bulk_g2s(sB + b * 2 * kTileBytes, tiles + (int64_t)kb * 2 * 4096, kTileBytes, &bbar[b]);
-    tc::bulk_g2s(sB + b * 2 * kTileBytes + kTileBytes, tiles + (int64_t)kb * 2 * 4096 + 4096, kTileBytes, &bbar[b]);
-    ++s_issued_b[b];
+    tc::mbar_expect_tx(&bbar, 2 * kTileBytes);
+    tc::bulk_g2s(sB, tiles + (int64_t)kb * 2 * 4096, kTileBytes, &bbar);
+    tc::bulk_g2s(sB + kTileBytes, tiles + (int64_t)kb * 2 * 4096 + 4096, kTileBytes, &bbar);
+    ++s_issued_b;
   };
   if (tid == 0 && nkb > 0) load_b(0);
   bool bad = false;
@@ -461,6 +466,8 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
         bad = true;
         break;
       }
+      // the first warp to see them complete requests this block's twiddle tiles
+      if (lane == 0 && atomicCAS(&s_bnext, kb - 1, kb) == kb - 1) load_b(kb);
       tc::fence_after_sync();
       drain(kb == 1);
     }
@@ -474,16 +481,15 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
     }
     done = __shfl_sync(0xffffffffu, done, 0);
     if (lane == 0 && done == kTT / 32 - 1) {
-      // The last warp done with this block issues its MMAs, then the next block's twiddle
-      // copies (buffer b ^ 1 was read by block kb - 1, whose MMAs this warp saw complete).
+      // The last warp done with this block issues its MMAs.
       atomicExch(&s_done[b], 0);
       __threadfence_block();
       const uint32_t par = (uint32_t)((kb >> 1) & 1);
-      bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar[b], par);
+      bool ok = tc::mbar_wait(&full[b], par) && tc::mbar_wait(&bbar, (uint32_t)(kb & 1));
       if (ok) {
         tc::fence_after_sync();
         const uint32_t s_base = tc::smem_addr(sA + b * 2 * kTilesPerCta * kTileBytes);  // samples (N)
-        const uint32_t w_base = tc::smem_addr(sB + b * 2 * kTileBytes);                 // twiddles (M)
+        const uint32_t w_base = tc::smem_addr(sB);                                      // twiddles (M)
         // the two split corrections (twiddle tail x sample head, twiddle head x sample tail)
         // first, started afresh, then the head x head products
 #pragma unroll
@@ -498,10 +504,6 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
           }
         tc::commit(&mbar[b]);
         ++s_issued_m[b];
-        if (kb + 1 < nkb) {
-          ok = kb < 1 || tc::mbar_wait(&mbar[b ^ 1], (uint32_t)(((kb - 1) >> 1) & 1));
-          if (ok) load_b(kb + 1);
-        }
       }
       if (!ok) {
         s_bad = 1;
@@ -527,10 +529,9 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   __syncthreads();
   if (tid == 0 && s_bad) {
     // let every copy and MMA issued land (bounded) before the CTA releases its memory
-    for (int b = 0; b < 2; ++b) {
-      if (s_issued_b[b] > 0) (void)tc::mbar_wait(&bbar[b], (uint32_t)((s_issued_b[b] - 1) & 1), 1000000000ull);
+    if (s_issued_b > 0) (void)tc::mbar_wait(&bbar, (uint32_t)((s_issued_b - 1) & 1), 1000000000ull);
+    for (int b = 0; b < 2; ++b)
       if (s_issued_m[b] > 0) (void)tc::mbar_wait(&mbar[b], (uint32_t)((s_issued_m[b] - 1) & 1), 1000000000ull);
-    }
   }
   double ll = 0.0;
   if (nkb > 0 && !s_bad) {
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(kTT, 1) loglike_mixed_time_kernel(LikeArgs a) 
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc<512>(tmem);
+  if (warp == 0) tc::tmem_dealloc<kTmemCols>(tmem);
   if (half == 0 && active) a.out[s] = (bad || s_bad) ? NAN : (valid ? ll : -INFINITY);
 }
 
