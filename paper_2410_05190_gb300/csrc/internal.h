@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -41,9 +42,13 @@ struct AnchorBlock {
   double B[kNumBasis];     // basis_j(f_kc)
   double dB[kNumBasis];    // basis_j'(f_kc) * df
   float E[kNumBasis - 1][kRemDegMax + 1];  // basis 8 (f) is linear: no remainder; degree of the plan
-  // B and dB as unevaluated float pairs (hi + lo) for the float-float block entry
-  float Bh[kNumBasis], Bl[kNumBasis], dBh[kNumBasis], dBl[kNumBasis];
+  // B and dB as unevaluated float pairs for the float-float block entry, one 16-byte vector
+  // per basis function: (hi of B_j, lo of B_j, hi of dB_j, lo of dB_j)
+  float4 Bq[kNumBasis];
 };
+static_assert(offsetof(AnchorBlock, E) % 16 == 0 && offsetof(AnchorBlock, Bq) % 16 == 0 &&
+                  sizeof(AnchorBlock) % 16 == 0,
+              "anchor-block vectors are 16-byte aligned");
 
 // Events whose phase terms stay below this many turns may enter anchor blocks in float-float
 // arithmetic (~2^-44 relative) instead of FP64.

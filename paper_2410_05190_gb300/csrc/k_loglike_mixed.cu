@@ -91,8 +91,8 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
     const float ch = pf[j * S], cl = pf[(L + j) * S];
-    ff_mac(ch, cl, B.Bh[j], B.Bl[j], xh, xl);
-    ff_mac(ch, cl, B.dBh[j], B.dBl[j], yh, yl);
+    ff_mac(ch, cl, B.Bq[j].x, B.Bq[j].y, xh, xl);
+    ff_mac(ch, cl, B.Bq[j].z, B.Bq[j].w, yh, yl);
   }
   two_sum(yh, yl, yh, yl);
   const float w0 = (float)(B.k0 - B.kc);

@@ -30,6 +30,7 @@
 // shared memory (transposed) to the log-mean-exp.
 #include "internal.h"
 #include "marg.cuh"
+#include "anchor.cuh"
 #include "ffloat.cuh"
 #include "tc.cuh"
 
@@ -97,13 +98,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   const double r1 = fy - (double)p1 * 2.3283064365386963e-10;
   st.acc = (uint32_t)p0 + kTurnOffset;
   st.step = (uint32_t)p1;
-#pragma unroll
-  for (int m = 0; m <= kTimeRemDeg; ++m) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j], B.E[j][m], s);
-    st.c[m] = s;
-  }
+  remainder_coeffs<kTimeRemDeg>(B, [&](int j) { return cf[j]; }, st.c);
   st.c[0] += (float)(r0 - w0 * r1);
   st.c[1] += (float)r1;
 #pragma unroll
@@ -119,8 +114,9 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
     const float ch = pf[j * kSamples], cl = pf[(kNumBasis + j) * kSamples];
-    ff_mac(ch, cl, B.Bh[j], B.Bl[j], xh, xl);
-    ff_mac(ch, cl, B.dBh[j], B.dBl[j], yh, yl);
+    const float4 q = __ldg(&B.Bq[j]);
+    ff_mac(ch, cl, q.x, q.y, xh, xl);
+    ff_mac(ch, cl, q.z, q.w, yh, yl);
   }
   two_sum(yh, yl, yh, yl);
   const float w0 = (float)(B.k0 - B.kc);
@@ -129,13 +125,7 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
   float r0, r1;
   st.acc = ff_frac32(xh, xl, r0) + kTurnOffset;
   st.step = ff_frac32(yh, yl, r1);
-#pragma unroll
-  for (int m = 0; m <= kTimeRemDeg; ++m) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(pf[j * kSamples], B.E[j][m], s);
-    st.c[m] = s;
-  }
+  remainder_coeffs<kTimeRemDeg>(B, [&](int j) { return pf[j * kSamples]; }, st.c);
   st.c[0] += r0 - w0 * r1;
   st.c[1] += r1;
 #pragma unroll
@@ -338,7 +328,12 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
         tc::tmem_ld16(tq + kRunCol + c0, q);
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(__fadd_rn(__uint_as_float(q[i]), __uint_as_float(r[i])));
+      for (int i = 0; i < 16; i += 2) {  // running sum + block sum, two lanes of f32x2
+        const float2 u = __fadd2_rn(make_float2(__uint_as_float(q[i]), __uint_as_float(q[i + 1])),
+                                    make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])));
+        r[i] = __float_as_uint(u.x);
+        r[i + 1] = __float_as_uint(u.y);
+      }
       tc::tmem_st16(tq + kRunCol + c0, r);
     }
     tc::tmem_wait_st();
@@ -352,12 +347,13 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
   for (int m = 0; m <= kTimeRemDeg; ++m) st.c[m] = 0.f;
   int blk = -1;
   int32_t blk_end = 0;
-  uint32_t base[nrow], stepd[nrow];
+  uint32_t base[nrow], stepd[nrow], step2[nrow];
   float epsd[nrow];
 #pragma unroll
   for (int d = 0; d < nrow; ++d) {
     base[d] = 0;
     stepd[d] = 0;
+    step2[d] = 0;
     epsd[d] = 0.f;
   }
   // enter plan block blk at its first bin k0: the phase state, and per detector the 32-bit
@@ -374,6 +370,7 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
       const uint64_t od = off[d] + (uint64_t)(uint32_t)k0 * stp[d];
       base[d] = st.acc + (uint32_t)(od >> 32);
       stepd[d] = st.step + (uint32_t)(stp[d] >> 32);
+      step2[d] = 2u * stepd[d];
       epsd[d] = (float)(uint32_t)stp[d] * (kTwoPiF * 5.421010862427522e-20f);  // 2 pi 2^-64
     }
   };
@@ -426,7 +423,7 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
         for (int d = 0; d < nrow; ++d) {
           const float2 f1 = make_float2(mantissa_turn(cnt[d]), mantissa_turn(cnt[d] + stepd[d]));
           const float2 ang = __ffma2_rn(f1, f2(kTwoPiF), __ffma2_rn(f2(epsd[d]), u2, R));
-          cnt[d] += 2u * stepd[d];
+          cnt[d] += step2[d];
           float2 sn, cs;
           __sincosf(ang.x, &sn.x, &cs.x);
           __sincosf(ang.y, &sn.y, &cs.y);

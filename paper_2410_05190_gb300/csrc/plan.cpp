@@ -74,10 +74,8 @@ Fit fit_block(const PlanInput& in, int32_t k0, int32_t S, int32_t max_pts) {
   basis_all(fc, b.B);
   for (int j = 0; j < kNumBasis; ++j) {
     b.dB[j] = basis_deriv(j, fc) * in.df;
-    b.Bh[j] = (float)b.B[j];
-    b.Bl[j] = (float)(b.B[j] - (double)b.Bh[j]);
-    b.dBh[j] = (float)b.dB[j];
-    b.dBl[j] = (float)(b.dB[j] - (double)b.dBh[j]);
+    const float bh = (float)b.B[j], dbh = (float)b.dB[j];
+    b.Bq[j] = make_float4(bh, (float)(b.B[j] - (double)bh), dbh, (float)(b.dB[j] - (double)dbh));
   }
   // remainders of every basis function beyond its tangent at fc, at offset w
   auto rem_all = [&](double w, double* r) {
