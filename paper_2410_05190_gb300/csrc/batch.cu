@@ -26,6 +26,10 @@ struct mbis_batch {
   std::vector<int64_t> ns;
   std::vector<uint64_t> seeds;
   std::vector<double*> theta, logq, logp, ll;
+  // per event: the order in which the tiles take its samples (longest band first; null when
+  // its prior box cannot end inside the grid or it has few samples) and its key counts
+  std::vector<int32_t*> perm, hist;
+  std::vector<LikeArgs> hargs;  // host copies of the launch arguments
   LikeArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;  // float-float-entry events' tiles first, then FP64-entry ones
   int32_t n_items = 0, n_ff = 0;
@@ -56,7 +60,9 @@ mbis_status berr(mbis_status st, const std::string& m) {
 
 // The work list: every event's 128-sample tiles, longest first (live bins at the proposal
 // mean), in two groups by block-entry arithmetic -- each group runs in its own persistent
-// launch.  Rebuilt when a context is re-targeted.
+// launch.  Within an event whose prior box reaches cuts inside the grid the tiles take the
+// samples longest band first (a permutation made after the draws of each step).  Rebuilt
+// when a context is re-targeted.
 mbis_status build_items(mbis_batch* b) {
   struct Cost {
     double cost;
@@ -93,6 +99,13 @@ cudaError_t launch_items(mbis_batch* b, cudaStream_t s) {
   return e;
 }
 
+// launch arguments of event i, with its sample order when it has one
+LikeArgs batch_args(const mbis_batch* b, int i) {
+  LikeArgs a = make_like_args(b->ctx[i], b->ns[i], b->theta[i], b->ll[i]);
+  a.perm = b->perm[i];
+  return a;
+}
+
 // enqueue one step on b->stream (also used inside stream capture)
 mbis_status enqueue_step(mbis_batch* b) {
   B_TRY(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(uint64_t) * b->n, cudaMemcpyHostToDevice, b->stream));
@@ -100,6 +113,7 @@ mbis_status enqueue_step(mbis_batch* b) {
     DrawArgs da = make_draw_args(b->ctx[i], b->seeds[i], 0, b->ns[i], b->theta[i], b->logq[i], b->logp[i]);
     da.d_ctr0 = b->d_ctr + i;
     B_TRY(launch_draw(da, b->stream));
+    if (b->perm[i]) B_TRY(launch_sample_order(b->hargs[i], kFoldOrderGran, b->hist[i], b->perm[i], b->stream));
   }
   B_TRY(launch_items(b, b->stream));
   for (int i = 0; i < b->n; ++i) {
@@ -145,13 +159,23 @@ mbis_status refresh(mbis_batch* b) {
   bool stale = false;
   for (int i = 0; i < b->n; ++i) stale |= b->ctx[i]->gen != b->gen[i];
   if (!stale) return MBIS_OK;
-  std::vector<LikeArgs> args(b->n);
-  for (int i = 0; i < b->n; ++i) {
+  for (int i = 0; i < b->n; ++i)
     if (const mbis_status st = check_ctx(b->ctx[i]); st != MBIS_OK) return st;
-    args[i] = make_like_args(b->ctx[i], b->ns[i], b->theta[i], b->ll[i]);
-  }
   B_TRY(cudaStreamSynchronize(b->stream));
-  B_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * b->n, cudaMemcpyHostToDevice));
+  for (int i = 0; i < b->n; ++i) {
+    // a re-targeted prior box may begin or stop reaching cuts inside the grid
+    const bool want = b->ctx[i]->may_cut && b->ns[i] >= kOrderMinSamples;
+    if (want && !b->perm[i]) {
+      B_TRY(cudaMalloc(&b->perm[i], sizeof(int32_t) * b->ns[i]));
+      B_TRY(cudaMalloc(&b->hist[i], sizeof(int32_t) * order_keys(b->ctx[i]->n_bins, kFoldOrderGran)));
+    } else if (!want && b->perm[i]) {
+      cudaFree(b->perm[i]);
+      cudaFree(b->hist[i]);
+      b->perm[i] = b->hist[i] = nullptr;
+    }
+    b->hargs[i] = batch_args(b, i);
+  }
+  B_TRY(cudaMemcpy(b->d_args, b->hargs.data(), sizeof(LikeArgs) * b->n, cudaMemcpyHostToDevice));
   for (int i = 0; i < b->n; ++i) b->gen[i] = b->ctx[i]->gen;
   if (const mbis_status st = build_items(b); st != MBIS_OK) return st;
   return capture(b);
@@ -181,6 +205,9 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
   b->logq.assign(n_ctx, nullptr);
   b->logp.assign(n_ctx, nullptr);
   b->ll.assign(n_ctx, nullptr);
+  b->perm.assign(n_ctx, nullptr);
+  b->hist.assign(n_ctx, nullptr);
+  b->hargs.assign(n_ctx, LikeArgs{});
   auto fail = [&](mbis_status st) {
     mbis_batch_destroy(b);
     return st;
@@ -195,7 +222,6 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
     }                                                                                             \
   } while (0)
   C_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
-  std::vector<LikeArgs> args(n_ctx);
   int64_t total_tiles = 0;
   for (int i = 0; i < n_ctx; ++i) {
     const mbis_ctx* c = ctxs[i];
@@ -204,7 +230,11 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
     C_TRY(cudaMalloc(&b->logq[i], sizeof(double) * n));
     C_TRY(cudaMalloc(&b->logp[i], sizeof(double) * n));
     C_TRY(cudaMalloc(&b->ll[i], sizeof(double) * n));
-    args[i] = make_like_args(c, n, b->theta[i], b->ll[i]);
+    if (c->may_cut && n >= kOrderMinSamples) {
+      C_TRY(cudaMalloc(&b->perm[i], sizeof(int32_t) * n));
+      C_TRY(cudaMalloc(&b->hist[i], sizeof(int32_t) * order_keys(c->n_bins, kFoldOrderGran)));
+    }
+    b->hargs[i] = batch_args(b, i);
     total_tiles += (n + kMixedThreads - 1) / kMixedThreads;
   }
   if (total_tiles > INT32_MAX) {
@@ -213,7 +243,7 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
   }
   b->n_items = (int32_t)total_tiles;
   C_TRY(cudaMalloc(&b->d_args, sizeof(LikeArgs) * n_ctx));
-  C_TRY(cudaMemcpy(b->d_args, args.data(), sizeof(LikeArgs) * n_ctx, cudaMemcpyHostToDevice));
+  C_TRY(cudaMemcpy(b->d_args, b->hargs.data(), sizeof(LikeArgs) * n_ctx, cudaMemcpyHostToDevice));
   C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)b->n_items));
   C_TRY(cudaMalloc(&b->d_next, 2 * sizeof(int32_t)));
   C_TRY(cudaMalloc(&b->d_ctr, sizeof(uint64_t) * n_ctx));
@@ -239,6 +269,8 @@ void mbis_batch_destroy(mbis_batch* b) {
     if (b->logq[i]) cudaFree(b->logq[i]);
     if (b->logp[i]) cudaFree(b->logp[i]);
     if (b->ll[i]) cudaFree(b->ll[i]);
+    if (b->perm[i]) cudaFree(b->perm[i]);
+    if (b->hist[i]) cudaFree(b->hist[i]);
   }
   if (b->d_args) cudaFree(b->d_args);
   if (b->d_items) cudaFree(b->d_items);

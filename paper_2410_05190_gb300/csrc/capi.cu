@@ -217,6 +217,24 @@ namespace mbis {
 // message for mbis_last_error(NULL) from entry points defined in other files
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+// The order in which the CTAs of a likelihood launch take its samples: longest band first
+// (a permutation in scratch the context owns), for launches of kOrderMinSamples or more whose
+// prior box reaches total masses with the ISCO inside the grid; *perm = null otherwise.
+mbis_status sample_order(mbis_ctx* c, const LikeArgs& a, int32_t gran, cudaStream_t s, const int32_t** perm) {
+  *perm = nullptr;
+  if (a.n < kOrderMinSamples || !c->may_cut) return MBIS_OK;
+  if (c->tperm_cap < a.n) {
+    dfree(c, c->d_tperm);
+    c->tperm_cap = 0;
+    CU_TRY(c, dalloc(c, &c->d_tperm, sizeof(int32_t) * (size_t)a.n));
+    c->tperm_cap = a.n;
+  }
+  if (!c->d_thist) CU_TRY(c, dalloc(c, &c->d_thist, sizeof(int32_t) * (size_t)order_keys(c->n_bins, kFoldOrderGran)));
+  CU_TRY(c, launch_sample_order(a, gran, c->d_thist, c->d_tperm, s));
+  *perm = c->d_tperm;
+  return MBIS_OK;
+}
+
 DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
                         double* log_prior) {
   DrawArgs a = {};
@@ -669,6 +687,22 @@ mbis_status mbis_set_metric(mbis_ctx* c, int32_t P, const int32_t* ids, const do
     }
     c->log_mass_norm = log(0.5 * (mhi * mhi - mlo * mlo) * q_integral(qlo, qhi));
   }
+  {
+    // whether samples inside the prior box can end (ISCO) inside the grid: then a launch
+    // orders its samples by their live bins
+    double mc_hi = c->fixed[kMc], q_lo = c->fixed[kQ], q_hi = c->fixed[kQ];
+    for (int p = 0; p < P; ++p) {
+      if (ids[p] == kMc) mc_hi = hi[p];
+      if (ids[p] == kQ) {
+        q_lo = lo[p];
+        q_hi = hi[p];
+      }
+    }
+    double m_max = 0.0;
+    for (const double q : {q_lo, q_hi})
+      if (q > 0.0 && mc_hi > 0.0) m_max = std::max(m_max, total_mass_seconds(mc_hi, q));
+    c->may_cut = m_max > 0.0 && f_isco_m(m_max) <= c->f_lo + c->df * (c->n_bins - 1);
+  }
   const mbis_status st = build_tables(c);
   if (st != MBIS_OK) return st;
   c->has_metric = true;
@@ -698,18 +732,7 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
     CU_TRY(c, launch_loglike_fp64(a, s));
   } else if (c->opts.marg & MBIS_MARG_TIME) {
     LikeArgs b = a;
-    if (n >= kTimeSortMinSamples) {
-      // CTAs take the samples in order of their live K-blocks, longest first
-      if (c->tperm_cap < n) {
-        dfree(c, c->d_tperm);
-        c->tperm_cap = 0;
-        CU_TRY(c, dalloc(c, &c->d_tperm, sizeof(int32_t) * (size_t)n));
-        c->tperm_cap = n;
-      }
-      if (!c->d_thist) CU_TRY(c, dalloc(c, &c->d_thist, sizeof(int32_t) * (size_t)(c->n_kb + 1)));
-      CU_TRY(c, launch_time_order(a, c->d_thist, c->d_tperm, s));
-      b.perm = c->d_tperm;
-    }
+    if (const mbis_status r = sample_order(c, a, kKBlockBins, s, &b.perm); r != MBIS_OK) return r;
     CU_TRY(c, launch_loglike_mixed_time(b, s));
   } else {
     if (!a.fold)
@@ -735,6 +758,7 @@ mbis_status mbis_loglike(mbis_ctx* c, int64_t n, const double* theta, double* lo
         }
       }
     }
+    if (const mbis_status r = sample_order(c, a, kFoldOrderGran, s, &b.perm); r != MBIS_OK) return r;
     if (b.split > 1) {
       if (c->split_cap < n) {
         dfree(c, c->d_zpart);

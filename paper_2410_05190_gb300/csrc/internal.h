@@ -105,8 +105,8 @@ struct LikeArgs {
   double2* zpart;             // [n_parts][n]
   double* amp_out;            // [n]
   int32_t* kcut_out;          // [n]
-  // TIME, mixed: the order in which CTAs take the samples (slot i evaluates sample perm[i]),
-  // most live K-blocks first; null: sample i in slot i
+  // mixed: the order in which CTAs take the samples (slot i evaluates sample perm[i]), most
+  // live bins first; null: sample i in slot i
   const int32_t* perm;
 };
 
@@ -135,11 +135,14 @@ struct BatchItem {
 
 // kernel launchers (each returns cudaGetLastError() of its launch)
 cudaError_t launch_basis_table(double f_lo, double df, int32_t n, double* out, cudaStream_t s);
-// TIME, mixed: samples per launch from which the time-marginalised kernel takes its samples
-// in order of their live K-blocks
-constexpr int64_t kTimeSortMinSamples = 4096;
-// the order: hist (n_kb + 1 ints) and perm (n ints) are scratch of the caller
-cudaError_t launch_time_order(const LikeArgs& a, int32_t* hist, int32_t* perm, cudaStream_t s);
+// Samples per launch from which the mixed likelihood kernels take the samples in order of
+// their live bins (longest band first); gran: the bins of one key (16 for the K-blocks of
+// the time-marginalised kernel, a bin pair for the folded kernel).  hist (order_keys ints)
+// and perm (n ints) are scratch of the caller; slot i of the launch evaluates perm[i].
+constexpr int64_t kOrderMinSamples = 4096;
+constexpr int32_t kFoldOrderGran = 2;
+int32_t order_keys(int32_t n_bins, int32_t gran);
+cudaError_t launch_sample_order(const LikeArgs& a, int32_t gran, int32_t* hist, int32_t* perm, cudaStream_t s);
 cudaError_t launch_twiddles(int32_t n, double f_lo, double df, int32_t J, double dt, double2* out, cudaStream_t s);
 cudaError_t launch_rows_to_f32(const double2* c, int32_t rows, int32_t n, int32_t n_pad, double inv_scale,
                                float2* out, cudaStream_t s);
@@ -251,6 +254,7 @@ void ess_result(const EssState& st, mbis_summary* out, int64_t* n_drawn, int64_t
 DrawArgs make_draw_args(const mbis_ctx* c, uint64_t seed, uint64_t ctr0, int64_t n, double* theta, double* log_q,
                         double* log_prior);
 LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, double* loglike);
+mbis_status sample_order(mbis_ctx* c, const LikeArgs& a, int32_t gran, cudaStream_t s, const int32_t** perm);
 void rb_free(mbis_ctx* c);
 }  // namespace mbis
 
@@ -290,10 +294,11 @@ struct mbis_ctx {
   double* d_amp = nullptr;
   int32_t* d_kcut = nullptr;
   int64_t split_cap = 0;     // samples x parts the scratch holds
-  // scratch of the time-marginalised launch's sample order (grown on demand)
+  // scratch of a launch's sample order (grown on demand)
   int32_t* d_tperm = nullptr;
   int32_t* d_thist = nullptr;
   int64_t tperm_cap = 0;
+  bool may_cut = false;      // the prior box reaches total masses whose ISCO lies inside the grid
   double* d_basis = nullptr;
   double2* d_cfold64 = nullptr;
   double* d_tfold = nullptr;

@@ -151,8 +151,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   float* sCF = sm.sCF;
   int& s_kmax = sm.s_kmax;
   const int tid = threadIdx.x;
-  const int64_t s = tile * kMixedThreads + tid;
-  const bool active = s < a.n;
+  const int64_t slot = tile * kMixedThreads + tid;
+  const bool active = slot < a.n;
+  const int64_t s = active && a.perm != nullptr ? (int64_t)a.perm[slot] : slot;
 
   // ---- per-sample set-up (FP64)
   double par[kNumSlots];

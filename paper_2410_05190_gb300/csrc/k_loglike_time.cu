@@ -589,106 +589,7 @@ cudaError_t launch_time_rows(const LikeArgs& a, cudaStream_t s) {
   }
 }
 
-// ---- sample order: most live K-blocks first
-// A sample's result does not depend on the CTA it shares (its A rows beyond its own cut are
-// zeros, whose products add exact zeros), so the order only saves the blocks a CTA would
-// run for samples whose band ends earlier than its longest one's.
-
-// live K-blocks of sample i, estimated in FP32 (the estimate only steers the order; each
-// CTA runs to the exact cut of its samples)
-__device__ __forceinline__ int32_t kb_key(const LikeArgs& a, int64_t i) {
-  const double mc = a.pos[kMc] >= 0 ? a.theta[(int64_t)a.pos[kMc] * a.n + i] : a.fixed[kMc];
-  const double q = a.pos[kQ] >= 0 ? a.theta[(int64_t)a.pos[kQ] * a.n + i] : a.fixed[kQ];
-  if (!(mc > 0.0) || !(q > 0.0)) return 0;
-  const float qf = (float)q;
-  const float m_sec = (float)(mc * kTsun) * powf(1.0f + qf, 1.2f) * powf(qf, -0.6f);
-  const float fi = 1.0f / (46.172139f * m_sec);  // 6^(3/2) pi M
-  const float k = fminf(fmaxf(ceilf((fi - (float)a.f_lo) / (float)a.df), 0.0f), (float)a.n_bins);
-  return ((int32_t)k + kKBlockBins - 1) / kKBlockBins;
-}
-
-// warp-uniform loop over the samples; lanes with the same key add once per warp
-__global__ void time_order_hist_kernel(LikeArgs a, int32_t* hist) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
-    const int64_t i = base + lane;
-    const bool on = i < a.n;
-    const unsigned mask = __ballot_sync(0xffffffffu, on);
-    if (on) {
-      const int32_t key = kb_key(a, i);
-      const unsigned peers = __match_any_sync(mask, key);
-      if (lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
-    }
-  }
-}
-
-// one CTA: counts -> first slot of each key, keys in decreasing order
-__global__ void time_order_scan_kernel(int32_t n_keys, int32_t* hist) {
-  __shared__ int32_t warp_tot[32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int per = (n_keys + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int r0 = t * per, r1 = min(r0 + per, n_keys);  // ranks r: key n_keys - 1 - r
-  int32_t local = 0;
-  for (int r = r0; r < r1; ++r) local += hist[n_keys - 1 - r];
-  int32_t incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (int)blockDim.x >> 5;
-    int32_t v = lane < nw ? warp_tot[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += u;
-    }
-    if (lane < nw) warp_tot[lane] = v;  // inclusive over warps
-  }
-  __syncthreads();
-  int32_t run = incl - local + (warp > 0 ? warp_tot[warp - 1] : 0);
-  for (int r = r0; r < r1; ++r) {
-    const int32_t c = hist[n_keys - 1 - r];
-    hist[n_keys - 1 - r] = run;
-    run += c;
-  }
-}
-
-__global__ void time_order_scatter_kernel(LikeArgs a, int32_t* next, int32_t* perm) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
-    const int64_t i = base + lane;
-    const bool on = i < a.n;
-    const unsigned mask = __ballot_sync(0xffffffffu, on);
-    if (on) {
-      const int32_t key = kb_key(a, i);
-      const unsigned peers = __match_any_sync(mask, key);
-      const int leader = __ffs(peers) - 1;
-      int32_t first = 0;
-      if (lane == leader) first = atomicAdd(&next[key], __popc(peers));
-      first = __shfl_sync(peers, first, leader);
-      perm[first + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
-    }
-  }
-}
-
 }  // namespace
-
-cudaError_t launch_time_order(const LikeArgs& a, int32_t* hist, int32_t* perm, cudaStream_t s) {
-  const int32_t n_keys = a.n_kb + 1;
-  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * (size_t)n_keys, s);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)std::min<int64_t>((a.n + 255) / 256, 4 * 152);
-  time_order_hist_kernel<<<grid, 256, 0, s>>>(a, hist);
-  time_order_scan_kernel<<<1, 1024, 0, s>>>(n_keys, hist);
-  time_order_scatter_kernel<<<grid, 256, 0, s>>>(a, hist, perm);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_loglike_mixed_time(const LikeArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;

@@ -99,9 +99,9 @@ int64_t request_footprint(const Request& q) {
     const size_t parts = ((size_t)r.grid.n_bins + kPartBins - 1) / kPartBins, nb = (size_t)r.ess.batch;
     t += round_alloc(16 * parts * nb) + round_alloc(8 * nb) + round_alloc(4 * nb);
   }
-  if (r.opts.precision == MBIS_MIXED && (r.opts.marg & MBIS_MARG_TIME)) {
-    // sample order of a time-marginalised launch: the permutation and the key counts
-    t += round_alloc(4 * (size_t)r.ess.batch) + round_alloc(4 * ((size_t)r.grid.n_bins / kKBlockBins + 2));
+  if (r.opts.precision == MBIS_MIXED) {
+    // sample order of a launch: the permutation and the key counts
+    t += round_alloc(4 * (size_t)r.ess.batch) + round_alloc(4 * (size_t)order_keys(r.grid.n_bins, kFoldOrderGran));
   }
   if (r.rb_fiducial) {
     // relative binning: prefix tables, their build scratch, edge records, weights, edges
