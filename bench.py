@@ -435,6 +435,7 @@ def batch_measurement(m, torch, steps=3, warmup=2):
         b = m.mbis_batch_create(ctxs, [w.n_samples for w in ws], [w.events[0].draw_seed for w in ws])
         try:
             grid, tune_ms = m.mbis_batch_autotune(b)
+            tile, _ = m.mbis_batch_shape(b)
             for i in range(warmup):
                 m.mbis_batch_step(b, i, len(ws))
             torch.cuda.synchronize()
@@ -464,6 +465,7 @@ def batch_measurement(m, torch, steps=3, warmup=2):
     out = {"workload": "uneven batch: 64 events (heavy and BNS families), 1969-128513 bins, 2-3 detectors, "
                         "2^14-2^20 samples each, one persistent likelihood launch per step, CUDA graph replay",
             "value": n / dt, "unit": UNIT, "ms_per_step": dt * 1e3, "samples_per_step": n, "grid": grid,
+            "samples_per_cta": tile,
             "launch_ms": statistics.mean(launch) * 1e3,
             "roofline": {"bound": "alu", "achieved": units / statistics.mean(launch) / 1e9,
                          "peak": N_SM * SFU_PER_SM_PER_CLK * peaks().get("sm_max_mhz", 2070.0) * 1e6 / SFU_PER_BIN / 1e9,

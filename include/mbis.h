@@ -246,10 +246,22 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
  * summaries (this step alone).  Synchronises the batch's own stream. */
 mbis_status mbis_batch_step(mbis_batch* b, uint64_t step, mbis_summary* out);
 
-/* Times the persistent launch for 2, 4, 6 and 7 CTAs per SM (7 is the most that fit) on the
- * current samples and keeps the fastest (re-capturing the step graph).  grid_out / ms_out
- * (host, nullable). */
+/* Times the persistent launch on the current samples for every tile shape -- 64, 128 or 256
+ * samples per CTA (the work list is rebuilt for each) -- at 1/2, 3/4 and all of the CTAs per
+ * SM that the shape's registers and shared memory allow (14, 7 and 3), keeps the fastest
+ * and re-captures the step graph.  Results do not depend on the shape.  grid_out / ms_out
+ * (host, nullable): the chosen grid and its launch time; mbis_batch_shape reports both. */
 mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out);
+
+/* Sets the shape of the persistent launch instead of the autotuner: samples_per_cta (64,
+ * 128 or 256) and ctas_per_sm (1 .. 14, 7 or 3 for those tiles); rebuilds the work list and
+ * re-captures the step graph.  Results do not depend on the shape.
+ * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_batch_set_shape(mbis_batch* b, int32_t samples_per_cta, int32_t ctas_per_sm);
+
+/* The current shape of the persistent launch: samples per CTA and CTAs in the grid (host,
+ * nullable).  Errors: MBIS_E_INVALID. */
+mbis_status mbis_batch_shape(const mbis_batch* b, int32_t* samples_per_cta, int32_t* grid);
 
 /* The persistent likelihood launch alone, on the batch's current samples, on a caller
  * stream (for timing and tests). */

@@ -136,6 +136,8 @@ def _load():
         "mbis_batch_create": [i32, p, p, p, p],
         "mbis_batch_step": [p, u64, p],
         "mbis_batch_autotune": [p, p, p],
+        "mbis_batch_shape": [p, p, p],
+        "mbis_batch_set_shape": [p, i32, i32],
         "mbis_batch_loglike": [p, p],
         "mbis_batch_buffers": [p, i32, p, p],
         "mbis_batch_copy_out": [p, i32, p, p],
@@ -339,6 +341,17 @@ def mbis_batch_autotune(b):
     g, ms = C.c_int32(), C.c_float()
     _check(_lib.mbis_batch_autotune(b, C.byref(g), C.byref(ms)))
     return g.value, ms.value
+
+
+def mbis_batch_set_shape(b, samples_per_cta, ctas_per_sm):
+    _check(_lib.mbis_batch_set_shape(b, samples_per_cta, ctas_per_sm))
+
+
+def mbis_batch_shape(b):
+    """(samples per CTA, CTAs in the grid) of the batch's persistent launch."""
+    t, g = C.c_int32(), C.c_int32()
+    _check(_lib.mbis_batch_shape(b, C.byref(t), C.byref(g)))
+    return t.value, g.value
 
 
 def mbis_batch_loglike(b, stream=None):

@@ -7,7 +7,8 @@
 // device counter.  One step -- upload of the Philox counters, the draws of every
 // event, the persistent likelihood launch, the two-pass reduction of every event and the
 // copy of the summaries to pinned host memory -- is captured once in a CUDA graph and
-// replayed.  The size of the persistent grid is picked by timing candidates (autotuner).
+// replayed.  The tile shape (samples per CTA) and the size of the persistent grid are picked
+// by timing candidates (autotuner).
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -33,6 +34,8 @@ struct mbis_batch {
   LikeArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;  // float-float-entry events' tiles first, then FP64-entry ones
   int32_t n_items = 0, n_ff = 0;
+  int32_t tile = kMixedThreads;  // samples per CTA of the persistent launch (64, 128 or 256)
+  int64_t items_cap = 0;         // work items d_items holds (the count at the smallest tile)
   int32_t* d_next = nullptr;     // one work counter per group
   uint64_t* d_ctr = nullptr;
   uint64_t* h_ctr = nullptr;  // pinned
@@ -77,7 +80,7 @@ mbis_status build_items(mbis_batch* b) {
       if (c->ids[p] == kQ) q = c->mean[p];
     }
     const double live = (double)live_bins(mc, q > 0 ? q : 1.0, c->f_lo, c->df, c->n_bins);
-    const int32_t tiles = (int32_t)((b->ns[i] + kMixedThreads - 1) / kMixedThreads);
+    const int32_t tiles = (int32_t)((b->ns[i] + b->tile - 1) / b->tile);
     for (int32_t t = 0; t < tiles; ++t) g[c->ff_phase ? 0 : 1].push_back({live, {i, t}});
   }
   std::vector<BatchItem> list;
@@ -86,16 +89,17 @@ mbis_status build_items(mbis_batch* b) {
     for (const Cost& c : v) list.push_back(c.item);
   }
   b->n_ff = (int32_t)g[0].size();
-  if ((int32_t)list.size() != b->n_items) return berr(MBIS_E_STATE, "mbis_batch: work list size changed");
+  if ((int64_t)list.size() > b->items_cap) return berr(MBIS_E_STATE, "mbis_batch: work list too long");
+  b->n_items = (int32_t)list.size();
   B_TRY(cudaMemcpy(b->d_items, list.data(), sizeof(BatchItem) * list.size(), cudaMemcpyHostToDevice));
   return MBIS_OK;
 }
 
 cudaError_t launch_items(mbis_batch* b, cudaStream_t s) {
-  cudaError_t e = launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_ff, b->d_next, b->grid, true, s);
+  cudaError_t e = launch_loglike_mixed_batch(b->d_args, b->d_items, b->n_ff, b->d_next, b->grid, true, b->tile, s);
   if (e == cudaSuccess)
     e = launch_loglike_mixed_batch(b->d_args, b->d_items + b->n_ff, b->n_items - b->n_ff, b->d_next + 1, b->grid,
-                                   false, s);
+                                   false, b->tile, s);
   return e;
 }
 
@@ -235,16 +239,16 @@ mbis_status mbis_batch_create(int32_t n_ctx, mbis_ctx* const* ctxs, const int64_
       C_TRY(cudaMalloc(&b->hist[i], sizeof(int32_t) * order_keys(c->n_bins, kFoldOrderGran)));
     }
     b->hargs[i] = batch_args(b, i);
-    total_tiles += (n + kMixedThreads - 1) / kMixedThreads;
+    total_tiles += (n + 63) / 64;  // the work list at the smallest tile the autotuner tries
   }
   if (total_tiles > INT32_MAX) {
     berr(MBIS_E_INVALID, "mbis_batch_create: more than 2^31 sample tiles");
     return fail(MBIS_E_INVALID);
   }
-  b->n_items = (int32_t)total_tiles;
+  b->items_cap = total_tiles;
   C_TRY(cudaMalloc(&b->d_args, sizeof(LikeArgs) * n_ctx));
   C_TRY(cudaMemcpy(b->d_args, b->hargs.data(), sizeof(LikeArgs) * n_ctx, cudaMemcpyHostToDevice));
-  C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)b->n_items));
+  C_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)b->items_cap));
   C_TRY(cudaMalloc(&b->d_next, 2 * sizeof(int32_t)));
   C_TRY(cudaMalloc(&b->d_ctr, sizeof(uint64_t) * n_ctx));
   C_TRY(cudaMallocHost(&b->h_ctr, sizeof(uint64_t) * n_ctx));
@@ -328,42 +332,76 @@ mbis_status mbis_batch_copy_out(mbis_batch* b, int32_t i, double* theta_host, do
 mbis_status mbis_batch_autotune(mbis_batch* b, int32_t* grid_out, float* ms_out) {
   if (!b) return berr(MBIS_E_INVALID, "mbis_batch_autotune: null batch");
   if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
-  // fill the sample buffers once
+  // fill the sample buffers once (and their sample order)
   for (int i = 0; i < b->n; ++i) b->h_ctr[i] = 0;
   B_TRY(cudaGraphLaunch(b->exec, b->stream));
   B_TRY(cudaStreamSynchronize(b->stream));
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int cand[] = {2, 4, 6, kBatchCtasPerSm};
   cudaEvent_t e0, e1;
   B_TRY(cudaEventCreate(&e0));
   B_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_grid = sms * kBatchCtasPerSm;
-  for (int c : cand) {
-    b->grid = sms * c;
-    float t = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
-      B_TRY(cudaEventRecord(e0, b->stream));
-      B_TRY(launch_items(b, b->stream));
-      B_TRY(cudaEventRecord(e1, b->stream));
-      B_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) t += ms;  // first repetition warms up
-    }
-    if (t < best) {
-      best = t;
-      best_grid = b->grid;
+  int best_grid = sms * kBatchCtasPerSm, best_tile = kMixedThreads;
+  // the tile shape (samples per CTA) and the persistent grid (CTAs per SM, up to what the
+  // shape's registers and shared memory allow)
+  for (const int tile : {64, kMixedThreads, 256}) {
+    b->tile = tile;
+    if (const mbis_status st = build_items(b); st != MBIS_OK) return st;
+    const int cmax = batch_ctas_per_sm(tile);
+    for (const int c : {cmax / 2, (3 * cmax) / 4, cmax}) {
+      if (c < 1) continue;
+      b->grid = sms * c;
+      float t = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        B_TRY(cudaEventRecord(e0, b->stream));
+        B_TRY(launch_items(b, b->stream));
+        B_TRY(cudaEventRecord(e1, b->stream));
+        B_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t += ms;  // first repetition warms up
+      }
+      if (t < best) {
+        best = t;
+        best_grid = b->grid;
+        best_tile = tile;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->tile = best_tile;
   b->grid = best_grid;
+  if (const mbis_status st = build_items(b); st != MBIS_OK) return st;
   if (grid_out) *grid_out = best_grid;
   if (ms_out) *ms_out = best / 2.0f;
   return capture(b);
+}
+
+mbis_status mbis_batch_set_shape(mbis_batch* b, int32_t samples_per_cta, int32_t ctas_per_sm) {
+  if (!b) return berr(MBIS_E_INVALID, "mbis_batch_set_shape: null batch");
+  if (samples_per_cta != 64 && samples_per_cta != kMixedThreads && samples_per_cta != 256)
+    return berr(MBIS_E_INVALID, "mbis_batch_set_shape: samples per CTA must be 64, 128 or 256");
+  if (ctas_per_sm < 1 || ctas_per_sm > batch_ctas_per_sm(samples_per_cta))
+    return berr(MBIS_E_INVALID, "mbis_batch_set_shape: CTAs per SM out of range for this tile");
+  if (const mbis_status st = refresh(b); st != MBIS_OK) return st;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  B_TRY(cudaStreamSynchronize(b->stream));
+  b->tile = samples_per_cta;
+  b->grid = sms * ctas_per_sm;
+  if (const mbis_status st = build_items(b); st != MBIS_OK) return st;
+  return capture(b);
+}
+
+mbis_status mbis_batch_shape(const mbis_batch* b, int32_t* samples_per_cta, int32_t* grid) {
+  if (!b) return berr(MBIS_E_INVALID, "mbis_batch_shape: null batch");
+  if (samples_per_cta) *samples_per_cta = b->tile;
+  if (grid) *grid = b->grid;
+  return MBIS_OK;
 }
 
 }  // extern "C"

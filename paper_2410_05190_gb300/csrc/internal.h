@@ -170,8 +170,10 @@ cudaError_t launch_draw(const DrawArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_fp64(const LikeArgs& a, cudaStream_t s);
 cudaError_t launch_loglike_mixed(const LikeArgs& a, cudaStream_t s);
 // items of events that all enter anchor blocks in float-float (ff) or all in FP64
+// tile: samples per CTA (64, 128 or 256); the grid's CTAs per SM at most batch_ctas_per_sm(tile)
 cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
-                                      int32_t grid, bool ff, cudaStream_t s);
+                                      int32_t grid, bool ff, int32_t tile, cudaStream_t s);
+int32_t batch_ctas_per_sm(int32_t tile);
 
 // two-pass weight reduction; partials / counter / result are device scratch
 struct ReduceScratch {

@@ -44,14 +44,16 @@ struct BlockState {
 };
 
 // Enter anchor block blk: FP64 linear phase -> fixed point, FP32 remainder coefficients.
-// pc / cf are this thread's coefficient columns in shared memory (stride kMixedThreads).
+// pc / cf are this thread's coefficient columns in shared memory (stride T, the samples of
+// a tile).
+template <int T>
 __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan, int blk, const double* pc,
                                             const float* cf, BlockState& st) {
   const AnchorBlock& B = plan[blk];
-  double x = pc[kNumBasis * kMixedThreads], y = 0.0;  // cst
+  double x = pc[kNumBasis * T], y = 0.0;  // cst
 #pragma unroll
   for (int j = 0; j < kNumBasis; ++j) {
-    const double Cj = pc[j * kMixedThreads];
+    const double Cj = pc[j * T];
     x = fma(Cj, B.B[j], x);
     y = fma(Cj, B.dB[j], y);
   }
@@ -68,7 +70,7 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
   for (int m = 0; m <= kFoldRemDeg; ++m) {
     float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j * kMixedThreads], B.E[j][m], s);
+    for (int j = 0; j < kNumBasis - 1; ++j) s = fmaf(cf[j * T], B.E[j][m], s);
     st.c[m] = s;
   }
   st.c[0] += (float)(r0 - w0 * r1);
@@ -81,11 +83,12 @@ __device__ __forceinline__ void enter_block(const AnchorBlock* __restrict__ plan
 }
 
 // The same entry in float-float arithmetic (events whose phase terms stay below
-// kFloatFloatMaxTurns; no FP64).  pf is this thread's column (stride kMixedThreads): C_j hi
-// at row j, cst hi at row kNumBasis, C_j lo at row kNumBasis + 1 + j, cst lo at the last.
+// kFloatFloatMaxTurns; no FP64).  pf is this thread's column (stride T): C_j hi at row j,
+// cst hi at row kNumBasis, C_j lo at row kNumBasis + 1 + j, cst lo at the last.
+template <int T>
 __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ plan, int blk, const float* pf,
                                                BlockState& st) {
-  constexpr int S = kMixedThreads, L = kNumBasis + 1;
+  constexpr int S = T, L = kNumBasis + 1;
   const AnchorBlock& B = plan[blk];
   float xh = pf[kNumBasis * S], xl = pf[(L + kNumBasis) * S], yh = 0.f, yl = 0.f;
 #pragma unroll
@@ -118,13 +121,14 @@ __device__ __forceinline__ void enter_block_ff(const AnchorBlock* __restrict__ p
 
 __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_float((a >> 9) | 0x3f800000u); }
 
-// Shared memory of one CTA (declared once per kernel, so the persistent launch's two
-// instantiations of fold_tile share it).
+// Shared memory of one CTA of T threads (declared once per kernel, so the persistent
+// launch's two instantiations of fold_tile share it).
+template <int T>
 struct FoldSmem {
   __align__(128) float4 sC[kNbuf][kChunk / 2];
   __align__(8) uint64_t bar[kNbuf];
-  double sPC[(kNumBasis + 1) * kMixedThreads];  // C_j and cst per thread (float pairs when kFF)
-  float sCF[(kNumBasis - 1) * kMixedThreads];   // FP32 copies of C_0..C_7 (FP64 entry only)
+  double sPC[(kNumBasis + 1) * T];  // C_j and cst per thread (float pairs when kFF)
+  float sCF[(kNumBasis - 1) * T];   // FP32 copies of C_0..C_7 (FP64 entry only)
   int s_kmax;
 };
 
@@ -138,12 +142,13 @@ __device__ __forceinline__ double fold_loglike(const LikeArgs& a, double A, int3
   return log_distance_marginal_mixed(hypot(zr, zi), H, a.dist, a.glf);
 }
 
-// One tile of 128 samples of one event.  `first` is false when the CTA has already run a
-// tile (persistent launch): the mbarriers are then invalidated and initialised afresh.
-// piece / split: this CTA sums the parts [n_parts piece / split, n_parts (piece + 1) / split)
-// of the tile's bins; with split > 1 it writes their sums for the epilogue kernel.
-template <bool kFF>
-__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first, FoldSmem& sm, int piece = 0,
+// One tile of T samples of one event (one per thread).  `first` is false when the CTA has
+// already run a tile (persistent launch): the mbarriers are then invalidated and initialised
+// afresh.  piece / split: this CTA sums the parts [n_parts piece / split, n_parts (piece + 1)
+// / split) of the tile's bins; with split > 1 it writes their sums for the epilogue kernel.
+// A sample's arithmetic does not depend on T or on its tile-mates.
+template <bool kFF, int T>
+__device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool first, FoldSmem<T>& sm, int piece = 0,
                                           int split = 1) {
   float4 (&sC)[kNbuf][kChunk / 2] = sm.sC;
   uint64_t* bar = sm.bar;
@@ -151,7 +156,7 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
   float* sCF = sm.sCF;
   int& s_kmax = sm.s_kmax;
   const int tid = threadIdx.x;
-  const int64_t slot = tile * kMixedThreads + tid;
+  const int64_t slot = tile * T + tid;
   const bool active = slot < a.n;
   const int64_t s = active && a.perm != nullptr ? (int64_t)a.perm[slot] : slot;
 
@@ -183,18 +188,18 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
 #pragma unroll
       for (int j = 0; j < kNumBasis; ++j) {
         const float h = (float)pc.C[j];
-        pf[j * kMixedThreads] = h;
-        pf[(kNumBasis + 1 + j) * kMixedThreads] = (float)(pc.C[j] - (double)h);
+        pf[j * T] = h;
+        pf[(kNumBasis + 1 + j) * T] = (float)(pc.C[j] - (double)h);
       }
       const float h = (float)pc.cst;
-      pf[kNumBasis * kMixedThreads] = h;
-      pf[(2 * kNumBasis + 1) * kMixedThreads] = (float)(pc.cst - (double)h);
+      pf[kNumBasis * T] = h;
+      pf[(2 * kNumBasis + 1) * T] = (float)(pc.cst - (double)h);
     } else {
 #pragma unroll
-      for (int j = 0; j < kNumBasis; ++j) sPC[j * kMixedThreads + tid] = pc.C[j];
-      sPC[kNumBasis * kMixedThreads + tid] = pc.cst;
+      for (int j = 0; j < kNumBasis; ++j) sPC[j * T + tid] = pc.C[j];
+      sPC[kNumBasis * T + tid] = pc.cst;
 #pragma unroll
-      for (int j = 0; j < kNumBasis - 1; ++j) sCF[j * kMixedThreads + tid] = (float)pc.C[j];
+      for (int j = 0; j < kNumBasis - 1; ++j) sCF[j * T + tid] = (float)pc.C[j];
     }
   }
   const double* my_pc = sPC + tid;
@@ -266,9 +271,9 @@ __device__ __forceinline__ void fold_tile(const LikeArgs& a, int64_t tile, bool 
         ++blk;
         if (k < kcut) {
           if constexpr (kFF)
-            enter_block_ff(a.plan, blk, my_pf, st);
+            enter_block_ff<T>(a.plan, blk, my_pf, st);
           else
-            enter_block(a.plan, blk, my_pc, my_cf, st);
+            enter_block<T>(a.plan, blk, my_pc, my_cf, st);
           // a range that starts inside the block: the state at bin k, exactly as a sweep
           // from the block's first bin reaches it (integer turn counter, integer offset)
           const int32_t adv = k - a.plan[blk].k0;
@@ -412,23 +417,24 @@ __global__ void fold_epilogue_kernel(LikeArgs a) {
 
 template <bool kFF>
 __global__ void __launch_bounds__(kMixedThreads, 8) loglike_mixed_fold_kernel(LikeArgs a) {
-  __shared__ FoldSmem sm;
+  __shared__ FoldSmem<kMixedThreads> sm;
   const int split = a.split > 1 ? a.split : 1;
-  fold_tile<kFF>(a, blockIdx.x / split, true, sm, (int)(blockIdx.x % split), split);
+  fold_tile<kFF, kMixedThreads>(a, blockIdx.x / split, true, sm, (int)(blockIdx.x % split), split);
 }
 
 // Persistent launch over the tiles of many events: each CTA takes (event, tile) items from a
 // device counter until the list is exhausted.  The host orders the list longest first, so
 // uneven events (2k-128k bins, 2^14-2^20 samples) balance across the SMs.  One launch
 // takes the events of one block-entry arithmetic (kFF), so each keeps its own registers.
-// At most 7 CTAs per SM: 72 registers hold the persistent loop's state without the spills
-// that the 64-register bound of 8 CTAs caused (6% faster on the uneven batch).
-template <bool kFF>
-__global__ void __launch_bounds__(kMixedThreads, kBatchCtasPerSm) loglike_mixed_batch_kernel(const LikeArgs* __restrict__ args,
-                                                                               const BatchItem* __restrict__ items,
-                                                                               int32_t n_items, int32_t* next) {
+// Tiles of T samples with at most C CTAs per SM (the autotuner picks among (64, 14),
+// (128, 7) and (256, 3)): 72-85 registers hold the persistent loop's state without the
+// spills that a 64-register bound caused (6% faster on the uneven batch at T = 128).
+template <bool kFF, int T, int C>
+__global__ void __launch_bounds__(T, C) loglike_mixed_batch_kernel(const LikeArgs* __restrict__ args,
+                                                                   const BatchItem* __restrict__ items, int32_t n_items,
+                                                                   int32_t* next) {
   __shared__ int s_item;
-  __shared__ FoldSmem sm;
+  __shared__ FoldSmem<T> sm;
   bool first = true;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(kMixedThreads, kBatchCtasPerSm) loglike_mixed_
     __syncthreads();
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    fold_tile<kFF>(args[item.ev], item.tile, first, sm);
+    fold_tile<kFF, T>(args[item.ev], item.tile, first, sm);
     first = false;
     __syncthreads();
   }
@@ -445,15 +451,43 @@ __global__ void __launch_bounds__(kMixedThreads, kBatchCtasPerSm) loglike_mixed_
 
 }  // namespace
 
+int32_t batch_ctas_per_sm(int32_t tile) {
+  switch (tile) {
+    case 64: return 14;
+    case 256: return 3;
+    default: return kBatchCtasPerSm;
+  }
+}
+
 cudaError_t launch_loglike_mixed_batch(const LikeArgs* args, const BatchItem* items, int32_t n_items, int32_t* next,
-                                      int32_t grid, bool ff, cudaStream_t s) {
+                                      int32_t grid, bool ff, int32_t tile, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  if (ff)
-    loglike_mixed_batch_kernel<true><<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
-  else
-    loglike_mixed_batch_kernel<false><<<grid, kMixedThreads, 0, s>>>(args, items, n_items, next);
+  switch (tile) {
+    case 64:
+      if (ff)
+        loglike_mixed_batch_kernel<true, 64, 14><<<grid, 64, 0, s>>>(args, items, n_items, next);
+      else
+        loglike_mixed_batch_kernel<false, 64, 14><<<grid, 64, 0, s>>>(args, items, n_items, next);
+      break;
+    case 256:
+      if (ff)
+        loglike_mixed_batch_kernel<true, 256, 3><<<grid, 256, 0, s>>>(args, items, n_items, next);
+      else
+        loglike_mixed_batch_kernel<false, 256, 3><<<grid, 256, 0, s>>>(args, items, n_items, next);
+      break;
+    case kMixedThreads:
+      if (ff)
+        loglike_mixed_batch_kernel<true, kMixedThreads, kBatchCtasPerSm><<<grid, kMixedThreads, 0, s>>>(args, items,
+                                                                                                      n_items, next);
+      else
+        loglike_mixed_batch_kernel<false, kMixedThreads, kBatchCtasPerSm><<<grid, kMixedThreads, 0, s>>>(args, items,
+                                                                                                       n_items, next);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -167,7 +167,9 @@ def test_batch_autotune_keeps_results(m, torch, small):
         before = m.mbis_batch_step(b, 3, len(evs))
         grid, ms = m.mbis_batch_autotune(b)
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        assert grid % sms == 0 and grid // sms in (2, 4, 6, 7)
+        tile, grid2 = m.mbis_batch_shape(b)
+        assert grid2 == grid and tile in (64, 128, 256)
+        assert grid % sms == 0 and 1 <= grid // sms <= {64: 14, 128: 7, 256: 3}[tile]
         assert ms > 0.0
         after = m.mbis_batch_step(b, 3, len(evs))
         assert after == before
@@ -197,6 +199,28 @@ def test_batch_rejects_unsupported_contexts(m, torch, small):
             m.mbis_batch_create([evs[0]["ctx"], ctx], [128, 128], [1, 2])
     finally:
         m.mbis_destroy(ctx)
+
+
+@pytest.mark.parametrize("tile,ctas", [(64, 14), (256, 3), (64, 5)])
+def test_batch_tile_shapes_keep_results(m, torch, small, tile, ctas):
+    """Every tile shape the autotuner tries gives the same log L and summaries, bit for bit:
+    a sample's arithmetic does not depend on how many samples share its CTA."""
+    evs = small
+    b = m.mbis_batch_create([e["ctx"] for e in evs], [e["w"].n_samples for e in evs],
+                            [e["spec"].draw_seed for e in evs])
+    try:
+        ref = m.mbis_batch_step(b, 4, len(evs))
+        lls = [m.mbis_batch_copy_out(b, i, len(e["prop"]["ids"]), e["w"].n_samples)[1] for i, e in enumerate(evs)]
+        m.mbis_batch_set_shape(b, tile, ctas)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert m.mbis_batch_shape(b) == (tile, sms * ctas)
+        assert m.mbis_batch_step(b, 4, len(evs)) == ref
+        for i, e in enumerate(evs):
+            assert np.array_equal(m.mbis_batch_copy_out(b, i, len(e["prop"]["ids"]), e["w"].n_samples)[1], lls[i])
+        with pytest.raises(m.MbisError):
+            m.mbis_batch_set_shape(b, 96, 2)
+    finally:
+        m.mbis_batch_destroy(b)
 
 
 def test_batch_full_size_events(m, torch):
