@@ -45,7 +45,7 @@ N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one loglike_mixed_fold_kernel launch at this
 # workload (2^20 samples), from a full ncu capture of the current kernel version (bench leg
 # `--steps 1 --warmup 3`); not measured inside this run
-FOLD_TRAFFIC_BYTES = 44_097_792 + 264_192
+FOLD_TRAFFIC_BYTES = 44_049_664 + 122_880
 FOLD_TRAFFIC_SOURCE = ("ncu --set full capture of one launch of this kernel version at this workload "
                        "(dram__bytes_read.sum + dram__bytes_write.sum); not measured in this run")
 SFU_PEAK_NOTE = ("peak = 152 SM x 16 MUFU results/clk (nominal; sine/cosine measured at 15.1 per SM per clock "
