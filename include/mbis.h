@@ -562,8 +562,8 @@ mbis_status mbis_fisher(mbis_ctx* ctx, const double* theta, int32_t P, const int
 typedef struct {
   double scale;         /* width scale s: the proposal is N(theta0, s^2 Gamma^-1) (> 0) */
   double box_sigmas;    /* prior box of Mc, q and t_c: theta0 +- box_sigmas s sigma (> 0) */
-  double chi_max;       /* prior of chi1z, chi2z: [-chi_max, chi_max] (0 < chi_max < 1) */
-  double dmin_mpc, dmax_mpc;  /* prior range of a sampled d_L (0 < dmin < dmax) */
+  double chi_max;       /* prior of chi1z, chi2z: [-chi_max, chi_max] (0 < chi_max < 1 when a spin is sampled) */
+  double dmin_mpc, dmax_mpc;  /* prior range of a sampled d_L (0 < dmin < dmax when d_L is sampled) */
 } mbis_proposal_options;
 
 /* The Gaussian proposal of Sec. II A from a Fisher matrix: the metric of the inner product

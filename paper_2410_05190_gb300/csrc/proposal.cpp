@@ -84,9 +84,7 @@ mbis_status mbis_proposal_from_fisher(int32_t P, const int32_t* ids, int32_t n_m
   if (!ids || !gamma || !theta0 || !o || !mean_out || !chol_out || !lo_out || !hi_out || (n_marg > 0 && !marg_ids))
     return bad(std::string(fn) + "null argument");
   if (P < 1 || n_marg < 0 || P + n_marg > kMaxDim) return bad(std::string(fn) + "need 1 <= P and P + n_marg <= 11");
-  if (!(o->scale > 0.0) || !(o->box_sigmas > 0.0) || !(o->chi_max > 0.0 && o->chi_max < 1.0) ||
-      !(o->dmax_mpc > o->dmin_mpc) || !(o->dmin_mpc > 0.0))
-    return bad(std::string(fn) + "need scale > 0, box_sigmas > 0, 0 < chi_max < 1, 0 < dmin < dmax");
+  if (!(o->scale > 0.0) || !(o->box_sigmas > 0.0)) return bad(std::string(fn) + "need scale > 0, box_sigmas > 0");
   bool seen[kNumSlots] = {};
   const int N = P + n_marg;
   for (int i = 0; i < N; ++i) {
@@ -94,6 +92,16 @@ mbis_status mbis_proposal_from_fisher(int32_t P, const int32_t* ids, int32_t n_m
     if (id < 0 || id >= kNumSlots || seen[id]) return bad(std::string(fn) + "slot ids must be distinct and < 11");
     seen[id] = true;
   }
+  // the spin and distance bounds matter only where those slots are sampled
+  bool spin = false, dist = false;
+  for (int p = 0; p < P; ++p) {
+    spin = spin || ids[p] == kChi1 || ids[p] == kChi2;
+    dist = dist || ids[p] == kDl;
+  }
+  if (spin && !(o->chi_max > 0.0 && o->chi_max < 1.0))
+    return bad(std::string(fn) + "a sampled spin needs 0 < chi_max < 1");
+  if (dist && !(o->dmin_mpc > 0.0 && o->dmax_mpc > o->dmin_mpc))
+    return bad(std::string(fn) + "a sampled distance needs 0 < dmin < dmax");
   for (int i = 0; i < N * N; ++i)
     if (!std::isfinite(gamma[i])) return bad(std::string(fn) + "non-finite Fisher matrix entry");
 

@@ -84,5 +84,21 @@ def test_bad_inputs_are_rejected(m):
         m.mbis_proposal_from_fisher([workloads.MC], [workloads.MC], np.eye(2), th)
     with pytest.raises(m.MbisError):           # non-finite entry
         m.mbis_proposal_from_fisher([workloads.MC], [], np.array([[np.nan]]), th)
-    with pytest.raises(m.MbisError):           # bad option
-        m.mbis_proposal_from_fisher([workloads.MC], [], np.eye(1), th, chi_max=1.0)
+    with pytest.raises(m.MbisError):           # bad option: a sampled spin with chi_max = 1
+        m.mbis_proposal_from_fisher([workloads.CHI1], [], np.eye(1), th, chi_max=1.0)
+    with pytest.raises(m.MbisError):           # bad option: a sampled distance with dmin = 0
+        m.mbis_proposal_from_fisher([workloads.DL], [], np.eye(1), th, dmin=0.0)
+    with pytest.raises(m.MbisError):           # bad option: scale 0
+        m.mbis_proposal_from_fisher([workloads.MC], [], np.eye(1), th, scale=0.0)
+
+
+def test_unsampled_spin_and_distance_bounds_are_not_checked(m):
+    """A non-spinning proposal over (Mc, q) needs no spin or distance range: chi_max = 0 and
+    an empty distance range are accepted and change nothing."""
+    th = np.zeros(11)
+    th[workloads.MC], th[workloads.Q] = 20.0, 1.2
+    G = np.array([[4.0e4, 1.0e2], [1.0e2, 9.0]])
+    a = m.mbis_proposal_from_fisher([workloads.MC, workloads.Q], [], G, th, chi_max=0.0, dmin=0.0, dmax=0.0)
+    b = m.mbis_proposal_from_fisher([workloads.MC, workloads.Q], [], G, th, chi_max=0.9)
+    for k in ("mean", "chol", "lo", "hi"):
+        np.testing.assert_array_equal(a[k], b[k])
