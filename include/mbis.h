@@ -606,6 +606,15 @@ mbis_status mbis_fisher_proposal(mbis_ctx* ctx, const double* theta0, int32_t P,
  * next mbis_reduce) instead of a hang.  Returns MBIS_E_INVALID or MBIS_E_CUDA on failure. */
 mbis_status mbis_debug_wait_timeout(uint64_t limit_ns, int32_t* status_out, uint64_t* waited_ns_out);
 
+/* Self-test of the float-float sine and cosine that the time-marginalised kernel's
+ * per-sample set-up uses for the sky and orientation angles (not in the paper): for n
+ * angles x (device, FP64) writes sin x and cos x (device, FP64, nullable each) as that
+ * kernel computes them (a Cody-Waite reduction by pi/2 and the Taylor series in float-float
+ * arithmetic: absolute error below ~1e-13 for |x| < 8 pi, growing as |x| 1e-16 beyond it,
+ * from the FP64 pi/2 of the reduction; angles with |x| >= 2^20 take the library's FP64
+ * sincos).  Errors: MBIS_E_INVALID (n < 0, null x with n > 0), MBIS_E_CUDA. */
+mbis_status mbis_debug_ff_sincos(int64_t n, const double* x, double* sin_out, double* cos_out, void* cuda_stream);
+
 /* Library build/version string. */
 const char* mbis_version(void);
 

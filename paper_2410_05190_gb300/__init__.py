@@ -147,6 +147,7 @@ def _load():
         "mbis_server_poll": [p, p, i32, p],
         "mbis_server_stats_get": [p, p],
         "mbis_debug_wait_timeout": [u64, p, p],
+        "mbis_debug_ff_sincos": [i64, p, p, p, p],
         "mbis_credible_levels": [i64, i32, p, p, p, p, p],
         "mbis_rb_setup": [p, p, i32, p],
         "mbis_rb_loglike": [p, i64, p, p, p],
@@ -445,6 +446,11 @@ def mbis_debug_wait_timeout(limit_ns):
     st, ns = C.c_int32(), C.c_uint64()
     _check(_lib.mbis_debug_wait_timeout(int(limit_ns), C.byref(st), C.byref(ns)))
     return st.value, ns.value
+
+
+def mbis_debug_ff_sincos(n, x, sin_out=None, cos_out=None, stream=None):
+    """The time kernel's float-float sine and cosine of n device angles (a self-test)."""
+    _check(_lib.mbis_debug_ff_sincos(int(n), _dev(x), _dev(sin_out), _dev(cos_out), _stream(stream)))
 
 
 NOALLOC_MAX_SAMPLES = 16777216

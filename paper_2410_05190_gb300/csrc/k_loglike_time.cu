@@ -227,10 +227,12 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
     // the response argument enters the phase at FP32 accuracy.
     double sp = 0.0, cp = 1.0, sd = 0.0, cd = 1.0, ss = 0.0, cs = 1.0, ci = 1.0;
     if (valid) {
-      sincos(par[kRa] - a.gmst, &sp, &cp);
-      sincos(par[kDec], &sd, &cd);
-      sincos(par[kPsi], &ss, &cs);
-      ci = cos(par[kIota]);
+      // float-float sines and cosines (~1e-13): the FP64 pipe is the set-up's bottleneck
+      double si;
+      ff_sincos_d(par[kRa] - a.gmst, sp, cp);
+      ff_sincos_d(par[kDec], sd, cd);
+      ff_sincos_d(par[kPsi], ss, cs);
+      ff_sincos_d(par[kIota], si, ci);
     }
 #pragma unroll
     for (int d = 0; d < nrow; ++d) {
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
         const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
         p2 = p_re * p_re + p_im * p_im;
         const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
-        pm = (float)sqrt(p2);
+        pm = sqrtf((float)p2);  // |P_d| enters in FP32
         const double arg_turns = (double)atan2f((float)p_im, (float)p_re) * (1.0 / kTwoPi);
         off = frac64(a.f_lo * dt - arg_turns);
         stp = frac64(a.df * dt);

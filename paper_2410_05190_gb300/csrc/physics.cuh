@@ -27,6 +27,7 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kTwoPi = 6.283185307179586476925286766559005768;
 constexpr double kTsun = 4.925490947641267e-6;             // G Msun / c^3, s (IAU 2015)
 constexpr double kClight = 299792458.0;                    // m / s
+constexpr double kInvClight = 1.0 / kClight;               // a product, not an FP64 division, per delay
 constexpr double kMpcSeconds = 3.0856775814913673e22 / 299792458.0;  // 1 Mpc / c, s
 constexpr double kEulerGamma = 0.577215664901532860606512090082;
 constexpr int kNumBasis = 9;
@@ -298,13 +299,13 @@ MBIS_HD void antenna_trig(const double* x, const double* y, double sp, double cp
 }
 
 MBIS_HD double delay_trig(const double* r, double sp, double cp, double sd, double cd) {
-  return -(r[0] * cd * cp + r[1] * cd * sp + r[2] * sd) / kClight;
+  return -(r[0] * cd * cp + r[1] * cd * sp + r[2] * sd) * kInvClight;
 }
 
 // arrival-time offset relative to the geocentre, -r . n / c
 MBIS_HD double geocentre_delay(const double* r, double ra, double dec, double gmst) {
   const double ph = ra - gmst, cd = cos(dec);
-  return -(r[0] * cd * cos(ph) + r[1] * cd * sin(ph) + r[2] * sin(dec)) / kClight;
+  return -(r[0] * cd * cos(ph) + r[1] * cd * sin(ph) + r[2] * sin(dec)) * kInvClight;
 }
 
 }  // namespace mbis
