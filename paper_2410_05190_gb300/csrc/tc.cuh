@@ -160,10 +160,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// FP32 -> TF32 rounded to nearest, ties away from zero (the rounding of cvt.rna.tf32.f32):
+// half a unit of the 13 dropped bits added to the magnitude, then those bits cleared -- two
+// integer operations; a carry into the exponent is the round-up to the next binade.  For
+// finite x.
 __device__ __forceinline__ float tf32_round(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
 }  // namespace tc
