@@ -322,12 +322,12 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 16) {
       uint32_t r[16], q[16];
-      tc::tmem_ld16(tq + c0, r);
       if (first) {
+        tc::tmem_ld16(tq + c0, r);
 #pragma unroll
         for (int i = 0; i < 16; ++i) q[i] = 0u;
       } else {
-        tc::tmem_ld16(tq + kRunCol + c0, q);
+        tc::tmem_ld16x2(tq + c0, r, tq + kRunCol + c0, q);  // block sums and running sums, one wait
       }
 #pragma unroll
       for (int i = 0; i < 16; i += 2) {  // running sum + block sum, two lanes of f32x2
