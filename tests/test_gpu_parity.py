@@ -331,6 +331,72 @@ def test_ess_loop_equals_manual_batches_and_refit_raises_efficiency(m, torch, ti
         m.mbis_destroy(ctx)
 
 
+def _oracle_ess_loop(ev, th, prop, seed, batch, target, max_samples, refine, refine_scale):
+    """The ESS-target loop on the oracle (Eqs. 5-6; the refit of the proposal from weighted
+    samples, Sec. III A): batch b draws the Philox counters [b batch, (b + 1) batch) from the
+    current Gaussian; each of the first `refine` batches refits the mean and covariance from
+    its normalised weights (when its own ESS is at least 2P + 1), with the width scale
+    refine_scale, and does not enter the estimate; the later batches are reduced together
+    until the ESS reaches the target.  Returns (summary, draws, draws in the estimate)."""
+    ids = prop["ids"]
+    P = len(ids)
+    mean, chol, scale = np.array(prop["mean"], dtype=float), np.array(prop["chol"], dtype=float).reshape(P, P), \
+        prop["scale"]
+    refits, b, drawn = refine, 0, 0
+    kept = ([], [], [])
+    summary = None
+    while drawn < max_samples:
+        nb = min(batch, max_samples - drawn)
+        theta, lq = oracle.draw(seed, b * batch, nb, ids, mean, chol, scale)
+        lp = oracle.log_prior(ids, prop["lo"], prop["hi"], prop["flags"], theta)
+        inside = np.isfinite(lp)
+        ll = np.zeros(nb)
+        ll[inside] = oracle.loglike_batch(ev, oracle.full_params(ids, theta[:, inside], th))
+        drawn += nb
+        b += 1
+        if refits > 0:
+            refits -= 1
+            red = oracle.reduce(ll, lp, lq, want_weights=True)
+            if red["ess"] >= 2 * P + 1:
+                mean, cov = oracle.weighted_moments(ids, theta, red["weights"], mean)
+                chol = np.linalg.cholesky(cov)
+                scale = refine_scale if refine_scale > 0 else scale
+            kept = ([], [], [])
+            continue
+        for k, x in enumerate((ll, lp, lq)):
+            kept[k].append(x)
+        summary = oracle.reduce(*(np.concatenate(x) for x in kept))
+        if summary["ess"] >= target:
+            break
+    return summary, drawn, sum(len(x) for x in kept[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_refitted_ess_loop_replayed_by_the_oracle(m, torch, tiny, precision):
+    """a7 end to end: the loop with two refits on the device, and the same sequence of
+    draws, likelihoods, weights, refits and merged estimates replayed by the oracle from its
+    own arithmetic -- the same draw counts, and the final ESS and log Z to 1e-6 (FP64 path)
+    or 1e-3 (mixed path) relative."""
+    w, spec, ev, th, prop = tiny
+    ctx = gpu_context(m, ev, w, spec, th, m.FP64 if precision == "fp64" else m.MIXED)
+    try:
+        set_metric(m, ctx, prop)
+        P, batch, target = len(prop["ids"]), 4096, 400.0
+        bufs = [torch.empty((P, batch), dtype=torch.float64, device="cuda")] + \
+               [torch.empty(batch, dtype=torch.float64, device="cuda") for _ in range(4)]
+        got, nd, nu = m.mbis_run_to_ess(ctx, *bufs, ess_target=target, batch=batch, max_samples=64 * batch,
+                                        seed=spec.draw_seed, refine=2, refine_scale=1.2)
+        ref, nd_o, nu_o = _oracle_ess_loop(ev, th, prop, spec.draw_seed, batch, target, 64 * batch, 2, 1.2)
+        tol = 1e-6 if precision == "fp64" else 1e-3
+        print(f"  device: ESS {got['ess']:.3f} log Z {got['log_z']:.6f} drawn {nd} used {nu}; "
+              f"oracle: ESS {ref['ess']:.3f} log Z {ref['log_z']:.6f} drawn {nd_o} used {nu_o}")
+        assert (nd, nu) == (nd_o, nu_o) and nu > 0 and got["ess"] >= target
+        assert abs(got["ess"] / ref["ess"] - 1) <= tol, (got["ess"], ref["ess"])
+        assert abs(got["log_z"] - ref["log_z"]) <= tol * max(1.0, abs(ref["log_z"])), (got["log_z"], ref["log_z"])
+    finally:
+        m.mbis_destroy(ctx)
+
+
 def test_ess_loop_pools_refit_batches_up_to_the_cap(m, torch, tiny):
     """a7 with refit_min_ess: a refit batch short of it pools with the next ones; with a
     floor that no pool reaches, each refit takes 16 batches; with no floor (0) the loop is
