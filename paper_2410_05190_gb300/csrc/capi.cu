@@ -289,11 +289,19 @@ LikeArgs make_like_args(const mbis_ctx* c, int64_t n, const double* theta, doubl
   a.tfold = c->d_tfold;
   a.cdet64 = c->d_cdet64;
   a.tdet = c->d_tdet;
+  auto split = [](double v, float (&out)[2]) {
+    out[0] = (float)v;
+    out[1] = (float)(v - (double)out[0]);
+  };
   for (int d = 0; d < c->n_det; ++d)
     for (int i = 0; i < 3; ++i) {
       a.det_vertex[d][i] = c->dets[d].vertex_m[i];
       a.det_x[d][i] = c->dets[d].xarm[i];
       a.det_y[d][i] = c->dets[d].yarm[i];
+      split(c->dets[d].xarm[i], a.det_xf[d][i]);
+      split(c->dets[d].yarm[i], a.det_yf[d][i]);
+      split(-c->f_lo * c->dets[d].vertex_m[i] * kInvClight, a.det_offf[d][i]);
+      split(-c->df * c->dets[d].vertex_m[i] * kInvClight, a.det_stpf[d][i]);
     }
   a.gmst = c->gmst;
   a.twiddle = c->d_twiddle;

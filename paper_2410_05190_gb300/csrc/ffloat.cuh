@@ -139,16 +139,38 @@ __device__ __forceinline__ void ff_sincos(double x, FF& s_out, FF& c_out) {
   c_out = k == 0 ? cs : (k == 1 ? msn : (k == 2 ? mcs : sn));
 }
 
-// The same as FP64 values (an angle beyond the reduction's range takes the library's sincos)
-__device__ __forceinline__ void ff_sincos_d(double x, double& s, double& c) {
+// Any FP64 angle: an angle beyond the reduction's range takes the library's sincos
+__device__ __forceinline__ void ff_sincos_any(double x, FF& s, FF& c) {
   if (fabs(x) < 1048576.0) {
-    FF fs, fc;
-    ff_sincos(x, fs, fc);
-    s = ff_to_double(fs);
-    c = ff_to_double(fc);
+    ff_sincos(x, s, c);
   } else {
-    sincos(x, &s, &c);
+    double sd, cd;
+    sincos(x, &sd, &cd);
+    s = ff_from_double(sd);
+    c = ff_from_double(cd);
   }
+}
+
+// The same as FP64 values
+__device__ __forceinline__ void ff_sincos_d(double x, double& s, double& c) {
+  FF fs, fc;
+  ff_sincos_any(x, fs, fc);
+  s = ff_to_double(fs);
+  c = ff_to_double(fc);
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
+
+// frac(h + l) as a 64-bit fixed-point turn count (|h| < 256 turns): the integer parts of
+// h 2^32 and l 2^32 give the upper word modulo 2^32, their fractional parts (exact) the
+// lower word, rounded at 2^-56 turns; a negative lower word borrows from the upper one.
+__device__ __forceinline__ uint64_t ff_frac64(FF v) {
+  const float xh = __fmul_rn(v.h, 4294967296.0f), xl = __fmul_rn(v.l, 4294967296.0f);
+  const float rh = rintf(xh), rl = rintf(xl);
+  const float f = __fadd_rn(__fsub_rn(xh, rh), __fsub_rn(xl, rl));  // in [-1, 1] units of 2^-32
+  const uint32_t hi = (uint32_t)(unsigned long long)__float2ll_rn(rh) + (uint32_t)__float2int_rn(rl);
+  return ((uint64_t)hi << 32) + (uint64_t)__float2ll_rn(__fmul_rn(f, 4294967296.0f));
 }
 
 }  // namespace mbis

@@ -82,6 +82,10 @@ struct LikeArgs {
   const double2* cdet64;      // [n_det][n_bins] (non-fold)
   const double* tdet;         // [n_det][n_bins + 1]
   double det_vertex[kMaxDet][3], det_x[kMaxDet][3], det_y[kMaxDet][3];
+  // the same as float pairs (hi, lo) for the float-float sky set-up of the time kernel: the
+  // arms, and -f_lo r / c and -df r / c (turns at the first bin and per bin, per unit of
+  // the source direction)
+  float det_xf[kMaxDet][3][2], det_yf[kMaxDet][3][2], det_offf[kMaxDet][3][2], det_stpf[kMaxDet][3][2];
   double gmst;
   const double2* twiddle;     // TIME: [n_bins][n_tshift] (cos, sin) of 2 pi f_k tau_j
   // mixed tables

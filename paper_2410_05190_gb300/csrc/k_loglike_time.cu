@@ -138,15 +138,6 @@ __device__ __forceinline__ float mantissa_turn(uint32_t a) { return __uint_as_fl
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// turns t -> 64-bit fixed point of frac(t)
-__device__ __forceinline__ uint64_t frac64(double t) {
-  const double x = (t - floor(t)) * 4294967296.0;  // [0, 2^32)
-  const double xh = floor(x);
-  const uint64_t hi = (uint64_t)xh;
-  const uint64_t lo = (uint64_t)__double2ull_rn((x - xh) * 4294967296.0);  // 2^32 carries into hi
-  return (hi << 32) + lo;
-}
-
 // kFF: anchor blocks entered in float-float (events whose phase terms stay below
 // kFloatFloatMaxTurns), otherwise in FP64.  kRows: detector rows of the table (1 when the
 // detectors are folded), a compile-time count so the detectors' chains interleave.
@@ -223,32 +214,49 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
   } else if (!a.fold) {
     // Detector d enters as |P_d| c_dk e^{-i (Psi_k + 2 pi f_k dt_d - arg P_d)}: the argument
     // of the response and the delay share one 64-bit fixed-point turn counter (off, stp per
-    // bin).  FP64 for the delays (2 pi f dt to ~1e-7 rad) and for |P|^2 (H scales with it);
-    // the response argument enters the phase at FP32 accuracy.
-    double sp = 0.0, cp = 1.0, sd = 0.0, cd = 1.0, ss = 0.0, cs = 1.0, ci = 1.0;
+    // bin); the response argument enters the phase at FP32 accuracy.  Float-float throughout (~1e-14 relative; the FP64 pipe runs at a small fraction of
+    // FP32): the angles' sines and cosines, the wave axes X, Y and the direction n once per
+    // sample, then per detector F+ and Fx, |P|^2 (to FP64 for H), the response argument
+    // (FP32 atan2) and the delay terms f_lo dt and df dt from the host's -f r / c.
+    FF sp{0.f, 0.f}, cp{1.f, 0.f}, sd{0.f, 0.f}, cd{1.f, 0.f}, ss{0.f, 0.f}, cs{1.f, 0.f}, ci{1.f, 0.f};
     if (valid) {
-      // float-float sines and cosines (~1e-13): the FP64 pipe is the set-up's bottleneck
-      double si;
-      ff_sincos_d(par[kRa] - a.gmst, sp, cp);
-      ff_sincos_d(par[kDec], sd, cd);
-      ff_sincos_d(par[kPsi], ss, cs);
-      ff_sincos_d(par[kIota], si, ci);
+      FF si;
+      ff_sincos_any(par[kRa] - a.gmst, sp, cp);
+      ff_sincos_any(par[kDec], sd, cd);
+      ff_sincos_any(par[kPsi], ss, cs);
+      ff_sincos_any(par[kIota], si, ci);
     }
+    const FF cpsd = ff_mul(cp, sd), spsd = ff_mul(sp, sd);
+    const FF X[3] = {ff_sub(ff_mul(sp, cs), ff_mul(ss, cpsd)), ff_neg(ff_add(ff_mul(cp, cs), ff_mul(ss, spsd))),
+                     ff_mul(ss, cd)};
+    const FF Y[3] = {ff_neg(ff_add(ff_mul(sp, ss), ff_mul(cs, cpsd))), ff_sub(ff_mul(cp, ss), ff_mul(cs, spsd)),
+                     ff_mul(cs, cd)};
+    const FF nv[3] = {ff_mul(cd, cp), ff_mul(cd, sp), sd};
+    const FF cplus = ff_mul(FF{0.5f, 0.f}, ff_add_f(ff_mul(ci, ci), 1.0f));  // (1 + cos^2 iota) / 2
+    auto dot = [&](const float (&r)[3][2], const FF (&v)[3]) {
+      FF t = ff_mul(FF{r[0][0], r[0][1]}, v[0]);
+      t = ff_add(t, ff_mul(FF{r[1][0], r[1][1]}, v[1]));
+      return ff_add(t, ff_mul(FF{r[2][0], r[2][1]}, v[2]));
+    };
 #pragma unroll
     for (int d = 0; d < nrow; ++d) {
       float pm = 0.f;
       uint64_t off = 0, stp = 0;
       double p2 = 0.0;
       if (valid) {
-        double fp, fc;
-        antenna_trig(a.det_x[d], a.det_y[d], sp, cp, sd, cd, ss, cs, &fp, &fc);
-        const double p_re = fp * 0.5 * (1.0 + ci * ci), p_im = -fc * ci;
-        p2 = p_re * p_re + p_im * p_im;
-        const double dt = delay_trig(a.det_vertex[d], sp, cp, sd, cd);
-        pm = sqrtf((float)p2);  // |P_d| enters in FP32
-        const double arg_turns = (double)atan2f((float)p_im, (float)p_re) * (1.0 / kTwoPi);
-        off = frac64(a.f_lo * dt - arg_turns);
-        stp = frac64(a.df * dt);
+        const FF xX = dot(a.det_xf[d], X), xY = dot(a.det_xf[d], Y), yX = dot(a.det_yf[d], X),
+                 yY = dot(a.det_yf[d], Y);
+        const FF fp = ff_mul(FF{0.5f, 0.f}, ff_add(ff_sub(ff_mul(xX, xX), ff_mul(xY, xY)),
+                                                   ff_sub(ff_mul(yY, yY), ff_mul(yX, yX))));
+        const FF fc = ff_sub(ff_mul(xX, xY), ff_mul(yX, yY));
+        const FF p_re = ff_mul(fp, cplus), p_im = ff_neg(ff_mul(fc, ci));
+        const FF q2 = ff_add(ff_mul(p_re, p_re), ff_mul(p_im, p_im));
+        p2 = ff_to_double(q2);
+        pm = sqrtf(q2.h);  // |P_d| enters in FP32
+        constexpr FFConst kInv2Pi(1.0 / kTwoPi);
+        const FF arg_turns = ff_mul(FF{atan2f(p_im.h, p_re.h), 0.f}, FF{kInv2Pi.h, kInv2Pi.l});
+        off = ff_frac64(ff_sub(dot(a.det_offf[d], nv), arg_turns));
+        stp = ff_frac64(dot(a.det_stpf[d], nv));
       }
       x_pm[d * kSamples + si] = pm;
       x_off[d * kSamples + si] = off;
