@@ -7,7 +7,7 @@
 //
 // The second line is a real contraction [samples x 2K] . [2K x 128 shifts].  A CTA owns a
 // tile of 128 samples and runs two threads per sample (256 threads); two CTAs share an SM,
-// so that one's FP64 set-up overlaps the other's blocks.  Per K-block of 16 bins:
+// so that one's per-sample set-up overlaps the other's blocks.  Per K-block of 16 bins:
 //   * each thread computes its sample's a_k for one half of the block (8 bins), two bins at
 //     a time in f32x2 (mixed-precision phase as in the folded kernel: anchors entered in
 //     float-float when the event's phase terms allow it, FP64 otherwise; 32-bit fixed-point
@@ -32,6 +32,7 @@
 #include "marg.cuh"
 #include "anchor.cuh"
 #include "ffloat.cuh"
+#include "setup_ff.cuh"
 #include "tc.cuh"
 
 namespace mbis {
@@ -180,35 +181,32 @@ __global__ void __launch_bounds__(kTT, kCtasPerSm) loglike_mixed_time_kernel(Lik
   double* x_p2 = reinterpret_cast<double*>(x_stp + kMaxDet * kSamples);
   double amp = 0.0;
   if (half == 0) {
-    // phase coefficients, amplitude and cut
-    PhaseCoeffs pc;
+    // phase coefficients, amplitude and cut (float-float set-up)
+    SampleSetupFF ss;
 #pragma unroll
-    for (int j = 0; j < kNumBasis; ++j) pc.C[j] = 0.0;
-    pc.cst = 0.0;
-    int32_t kcut = 0;
-    if (valid) {
-      const SampleSetup ss = sample_setup(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic],
-                                          par[kDl], a.f_lo, a.df, a.n_bins);
-      pc = ss.pc;
-      kcut = ss.kcut;
-      amp = ss.amp;
-    }
+    for (int j = 0; j < kNumBasis; ++j) ss.C[j] = FF{0.f, 0.f};
+    ss.cst = FF{0.f, 0.f};
+    ss.kcut = 0;
+    ss.amp = 0.0;
+    if (valid)
+      ss = sample_setup_ff(par[kMc], par[kQ], par[kChi1], par[kChi2], par[kTc], par[kPhic], par[kDl], a.f_lo, a.df,
+                           a.n_bins);
+    const int32_t kcut = ss.kcut;
+    amp = ss.amp;
     if constexpr (kFF) {
       float* pf = reinterpret_cast<float*>(sm + kOffC) + si;
 #pragma unroll
       for (int j = 0; j < kNumBasis; ++j) {
-        const float h = (float)pc.C[j];
-        pf[j * kSamples] = h;
-        pf[(kNumBasis + j) * kSamples] = (float)(pc.C[j] - (double)h);
+        pf[j * kSamples] = ss.C[j].h;
+        pf[(kNumBasis + j) * kSamples] = ss.C[j].l;
       }
-      const float h = (float)pc.cst;
-      pf[2 * kNumBasis * kSamples] = h;
-      pf[(2 * kNumBasis + 1) * kSamples] = (float)(pc.cst - (double)h);
+      pf[2 * kNumBasis * kSamples] = ss.cst.h;
+      pf[(2 * kNumBasis + 1) * kSamples] = ss.cst.l;
     } else {
       double* pd = reinterpret_cast<double*>(sm + kOffC) + si;
 #pragma unroll
-      for (int j = 0; j < kNumBasis; ++j) pd[j * kSamples] = pc.C[j];
-      pd[kNumBasis * kSamples] = pc.cst;
+      for (int j = 0; j < kNumBasis; ++j) pd[j * kSamples] = ff_to_double(ss.C[j]);
+      pd[kNumBasis * kSamples] = ff_to_double(ss.cst);
     }
     s_kcut[si] = kcut;
   } else if (!a.fold) {
