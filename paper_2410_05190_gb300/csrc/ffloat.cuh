@@ -1,6 +1,7 @@
-// ffloat.cuh -- float-float ("double-single") helpers for the anchor-block entry of the
-// mixed-precision kernels, for events whose phase terms stay below kFloatFloatMaxTurns, and
-// for their running sums of FP32 partial sums.
+// ffloat.cuh -- float-float ("double-single") helpers: the anchor-block entry of the
+// mixed-precision kernels (events whose phase terms stay below kFloatFloatMaxTurns), their
+// running sums of FP32 partial sums, and the per-sample set-up of the time-marginalised
+// kernel (pair arithmetic, sine and cosine, a 64-bit turn fraction).
 #pragma once
 #include <cstdint>
 
