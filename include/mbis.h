@@ -615,6 +615,15 @@ mbis_status mbis_debug_wait_timeout(uint64_t limit_ns, int32_t* status_out, uint
  * sincos).  Errors: MBIS_E_INVALID (n < 0, null x with n > 0), MBIS_E_CUDA. */
 mbis_status mbis_debug_ff_sincos(int64_t n, const double* x, double* sin_out, double* cos_out, void* cuda_stream);
 
+/* Self-test of the time-marginalised kernel's float-float per-sample set-up (not in the
+ * paper): for n parameter sets params (device, [7][n]: Mc, q, chi1, chi2, t_c, phi_c, d_L)
+ * on the grid (f_lo, df, n_bins), out (device, [2][12][n]) receives the FP64 set-up of the
+ * mixed kernels (block 0) and the float-float one (block 1): the phase coefficients C_0..C_8
+ * (turns), the constant, the amplitude at d_L and the ISCO cut (as a double).
+ * Errors: MBIS_E_INVALID, MBIS_E_CUDA. */
+mbis_status mbis_debug_setup_pair(int64_t n, const double* params, double f_lo, double df, int32_t n_bins,
+                                  double* out, void* cuda_stream);
+
 /* Library build/version string. */
 const char* mbis_version(void);
 

@@ -148,6 +148,7 @@ def _load():
         "mbis_server_stats_get": [p, p],
         "mbis_debug_wait_timeout": [u64, p, p],
         "mbis_debug_ff_sincos": [i64, p, p, p, p],
+        "mbis_debug_setup_pair": [i64, p, d, d, i32, p, p],
         "mbis_credible_levels": [i64, i32, p, p, p, p, p],
         "mbis_rb_setup": [p, p, i32, p],
         "mbis_rb_loglike": [p, i64, p, p, p],
@@ -451,6 +452,12 @@ def mbis_debug_wait_timeout(limit_ns):
 def mbis_debug_ff_sincos(n, x, sin_out=None, cos_out=None, stream=None):
     """The time kernel's float-float sine and cosine of n device angles (a self-test)."""
     _check(_lib.mbis_debug_ff_sincos(int(n), _dev(x), _dev(sin_out), _dev(cos_out), _stream(stream)))
+
+
+def mbis_debug_setup_pair(n, params, f_lo, df, n_bins, out, stream=None):
+    """FP64 and float-float per-sample set-up side by side (a self-test; out [2][12][n])."""
+    _check(_lib.mbis_debug_setup_pair(int(n), _dev(params), float(f_lo), float(df), int(n_bins), _dev(out),
+                                      _stream(stream)))
 
 
 NOALLOC_MAX_SAMPLES = 16777216
